@@ -1,0 +1,381 @@
+"""Benchmark of the explicit ensemble wall update on GB300.
+
+Workload: the idealised aneurysm tube (200,000 nodes, 399,200 linear triangles,
+S = 64 realisations per GPU, pulsatile pressure plus axial shear), one context per
+precision form. One benchmark "step" is one pass of the whole hot path over a chunk
+of time steps: ens_step(chunk) (traction, internal force, fused update for every time
+step) followed by the ensemble statistics of the new state.
+
+Prints one JSON line (rank 0). value = sample-steps/s of the headline form over all
+ranks; every rank runs its own S-sample ensemble (weak scaling, no data-path
+collective). --impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HEADLINE = "fp32_force"
+FORMS = ["fp32_force", "kahan32", "fp64"]
+METRIC = "ensemble sample-steps/s and HBM GB/s fraction, FP32 vs FP64 form, at rel-L2 <=1e-5"
+# Algorithmic bytes per node-sample-step of each form (u read + write, v read + write,
+# (E h) of the ~2 incident elements, inverse mass), before the per-node terms.
+BYTES_NS = {"fp64": 120.0, "fp32_force": 108.0, "kahan32": 84.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk", type=int, default=200, help="time steps per benchmark step")
+    ap.add_argument("--workload", default="aneurysm")
+    ap.add_argument("--samples", type=int, default=64)
+    ap.add_argument("--forms", default=",".join(FORMS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 arithmetic peak derived from unit counts and clock: 152 SMs x 2 binary64 FMA per
+# SM per clock (measured DFMA throughput on this part matches) x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def step_kernel_traffic(form):
+    """DRAM bytes per step-kernel launch from a committed ncu capture, if the kernel
+    source it was taken on is unchanged (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    src = os.path.join(ROOT, "paper_2101_09059_gb300", "csrc", "ens_step.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = d.get(form)
+    if not ent or ent.get("source_sha") != sha:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def run_reference(args, world, rank):
+    """CPU arm: the FP64 oracle on the host cores, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    case = synth.make_case(args.workload, S=args.samples, n_steps=1 + args.chunk * (args.warmup + args.steps), seed=0)
+    mod = oracle.Model(case)
+    up, uc = mod.start()
+    # each oracle "step" is a bounded sample: `sub` time steps of all S samples
+    t0 = time.perf_counter()
+    mod.steps(up, uc, 0, 1)
+    one = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.steps + args.warmup)   # whole run within a few minutes
+    sub = max(1, min(args.chunk, int(budget / max(one, 1e-6))))
+    pos = 1
+    for _ in range(args.warmup):
+        mod.steps(up, uc, pos, sub)
+        pos += sub
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mod.steps(up, uc, pos, sub)
+        pos += sub
+    dt = time.perf_counter() - t0
+    value = args.samples * sub * args.steps / dt
+    cores = oracle.num_threads()
+    m = case["mesh"]
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sample-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} tube, {m.n_nodes} nodes, {m.n_elems} triangles, S={args.samples}",
+                   "time_steps_per_step": sub},
+        "cpu_baseline": {"value": value, "unit": "sample-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sub} time steps x {args.samples} samples per step of the {m.n_nodes}-node mesh"},
+        "e2e": {"value": value, "unit": "sample-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def cpu_baseline(case, S, budget_s=15.0):
+    import oracle
+    mod = oracle.Model(case)
+    up, uc = mod.start()
+    t0 = time.perf_counter()
+    mod.steps(up, uc, 0, 1)
+    one = time.perf_counter() - t0
+    n = max(2, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    mod.steps(up, uc, 1, n)
+    dt = time.perf_counter() - t0
+    return {"value": S * n / dt, "unit": "sample-steps/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} time steps x {S} samples of the same {case['mesh'].n_nodes}-node workload"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.load()
+    forms = [f for f in args.forms.split(",") if f]
+    K, W, C = args.steps, args.warmup, args.chunk
+    n_steps = C * (W + K)
+    case = synth.make_case(args.workload, S=args.samples, n_steps=n_steps, seed=rank)
+    m = case["mesh"]
+    N, S = m.n_nodes, args.samples
+    stream = torch.cuda.current_stream(dev)
+    results, finals = {}, {}
+    hbm_peak, peak_kind = peaks()
+    for form in forms:
+        e = pkg.Ensemble.from_case(case, precision=form, stream=stream, device=local)
+        info = e.info()
+        mean = torch.empty((N, 3), dtype=torch.float64, device=dev)
+        var = torch.empty_like(mean)
+        for _ in range(W):
+            e.step(C)
+            e.stats_device(mean, var)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(K):
+                e.step(C)
+                e.stats_device(mean, var)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        barrier(world)
+        ms = ev0.elapsed_time(ev1)
+        ms_max = max_over_ranks(ms, world)
+        per_launch_s = ms / 1e3 / (K * C)
+        alg_bytes = info["bytes_per_step"]
+        res = {
+            "value": sum_over_ranks(S * C * K / (ms_max / 1e3), world),
+            "ms_per_step": ms_max / K,
+            "kernel_us": per_launch_s * 1e6,
+            "achieved_gbs": alg_bytes / per_launch_s / 1e9,
+            "hbm_frac": alg_bytes / per_launch_s / 1e9 / hbm_peak,
+            "clocks": clk.summary(),
+            "gpu_launches": K * (C + 2),
+        }
+        if form == "fp64":
+            nnz = info["nnz"]
+            flops = N * S * (48.0 * nnz / N + 3 * (2 * case["modes"].shape[0] + 7))
+            res["achieved_tflops"] = flops / per_launch_s / 1e12
+            res["fp64_frac"] = res["achieved_tflops"] / FP64_PEAK_TFLOPS
+        finals[form] = e.displacement()
+        results[form] = res
+        e.close()
+        del mean, var
+        torch.cuda.synchronize()
+    if "fp64" in finals:
+        ref = finals["fp64"]
+        for f in forms:
+            results[f]["rel_l2_vs_fp64_gpu"] = float(np.linalg.norm(finals[f] - ref) / np.linalg.norm(ref))
+
+    head = HEADLINE if HEADLINE in results else forms[0]
+    h = results[head]
+
+    # end to end through the public API with host buffers: every step streams this
+    # chunk's load amplitudes from pinned host memory and reads the statistics back
+    e2e = None
+    if not args.no_e2e:
+        e = pkg.Ensemble.from_case(case, precision=head, stream=stream, device=local)
+        amp_host = torch.from_numpy(np.ascontiguousarray(case["amp"])).pin_memory().numpy()
+        for w in range(W):
+            e.set_amplitudes(w * C, amp_host[w * C:(w + 1) * C])
+            e.step(C)
+            e.stats()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for k in range(K):
+            r0 = (W + k) * C
+            e.set_amplitudes(r0, amp_host[r0:r0 + C])
+            e.step(C)
+            e.stats()
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+        barrier(world)
+        e.close()
+        e2e = {"value": sum_over_ranks(S * C * K / t_e2e, world), "unit": "sample-steps/s",
+               "h2d_bytes_per_step": int(C * case["amp"].shape[1] * 8),
+               "d2h_bytes_per_step": int(2 * N * 3 * 8 + 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, S)
+
+    traffic = step_kernel_traffic(head)
+    info_bytes = BYTES_NS[head] * N * S + m.n_elems * 64.0 + N * (12.0 + 24.0 * case["modes"].shape[0])
+    achieved = info_bytes / (h["kernel_us"] * 1e-6) / 1e9
+    out = {
+        "metric": METRIC,
+        "value": h["value"],
+        "unit": "sample-steps/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": h["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 forces / f64 state" if head == "fp32_force" else ("f64" if head == "fp64" else "f32 (compensated)"),
+        "data": "synthetic",
+        "config": {
+            "workload": f"{args.workload} tube, {N} nodes, {m.n_elems} triangles, S={S} per GPU, "
+                        f"pulsatile pressure + axial shear",
+            "form": head, "time_steps_per_step": C, "dt_s": case["dt"],
+            "l2": "inputs larger than L2 (state and coefficients > 129 MB per form)",
+            "parallelism": f"sample-sharded x{world}",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": f"step_kernel<{head}>",
+                     "algorithmic_bytes_per_launch": info_bytes},
+        "clocks": h["clocks"],
+        "gpu_launches": h["gpu_launches"],
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "forms": results,
+        "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

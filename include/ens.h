@@ -1,0 +1,213 @@
+/*
+ * ens.h — C ABI of the GB300 explicit ensemble solver for the segregated vessel-wall
+ * model of Li & Schiavazzi, "An ensemble solver for segregated cardiovascular FSI"
+ * (arXiv 2101.09059).
+ *
+ * What is solved (Section 2.2.1 and Section 2.3, Eq. dynamicsCD): a small-strain,
+ * linear, 3-dof-per-node shell of linear triangles (membrane plus transverse shear),
+ * lumped mass M and mass-proportional damping C = alpha M, advanced by central
+ * differences
+ *     (M + dt/2 C) u_{n+1} = dt^2 f_n - (dt^2 K - 2 M) u_n - (M - dt/2 C) u_{n-1}
+ * for S realisations at once. Each realisation s has its own nodal elastic modulus E_s
+ * and thickness h_s (Section 2.1 random fields); every realisation sees the same wall
+ * traction history f_n (one-way coupling, Section 2.2.3). The library evaluates the
+ * equivalent velocity form v_{n+1/2} = ((1 - beta) v_{n-1/2} + dt a_n) / (1 + beta),
+ * u_{n+1} = u_n + dt v_{n+1/2}, beta = alpha dt / 2, a_n = M^-1 (f_n - K_s u_n), with
+ * K_s never stored (assembly-free, Section 2.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Units are the caller's; the shipped workloads use SI.
+ *  - Every call returns ENS_OK (0) or a negative ENS_ERR_* code; ens_last_error gives
+ *    the message of the last failing call on that context. No C++ exception crosses
+ *    the ABI.
+ *  - Host input arrays belong to the caller and are copied before the call returns.
+ *    Output arrays are caller-allocated.
+ *  - Device work runs on the stream given at creation. Calls that return host data
+ *    synchronise that stream; ens_step synchronises it once at the end to report
+ *    non-finite values.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef ENS_H
+#define ENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------- */
+#define ENS_OK 0
+#define ENS_ERR_INVALID_ARG (-1) /* bad pointer, size, layout or parameter            */
+#define ENS_ERR_ALLOC (-2)       /* device allocation failed                           */
+#define ENS_ERR_CUDA (-3)        /* a CUDA runtime call failed (message has the name)  */
+#define ENS_ERR_UNSTABLE_DT (-4) /* dt is above the central-difference stability limit */
+#define ENS_ERR_NONFINITE (-5)   /* a displacement became Inf or NaN                   */
+#define ENS_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up                 */
+#define ENS_ERR_RANGE (-7)       /* stepping past the end of the traction table        */
+#define ENS_ERR_STATE (-8)       /* call not valid in the current state                */
+
+/* ---- precision forms ------------------------------------------------------------
+ * ENS_FP64       : every operation in IEEE binary64.
+ * ENS_FP32_FORCE : element forces K_s u in binary32 from a binary32 copy of u; the
+ *                  displacement and velocity state and their update stay binary64.
+ * ENS_KAHAN32    : forces in binary32; the displacement is a compensated pair of
+ *                  binary32 values (hi + lo) updated with an error-free sum, the
+ *                  velocity is binary32.                                              */
+typedef enum { ENS_FP64 = 0, ENS_FP32_FORCE = 1, ENS_KAHAN32 = 2 } ens_precision;
+
+/* ---- displacement layouts for the getters ---------------------------------------- */
+#define ENS_LAYOUT_SNC 0 /* out[s][node][dof]  */
+#define ENS_LAYOUT_NCS 1 /* out[node][dof][s]  */
+
+typedef struct ens_ctx ens_ctx;
+
+/* Surface mesh of linear triangles (Section 2.2.1). Corner order fixes the outward
+ * normal (X2 - X1) x (X3 - X1). fixed: per dof, 1 = held at zero ("fully fixed"
+ * restraints of Section 3); NULL means nothing is fixed. Node ids in tri must be in
+ * [0, n_nodes). Elements of zero area are rejected with ENS_ERR_INVALID_ARG.        */
+typedef struct {
+    int32_t n_nodes;
+    int32_t n_elems;
+    const double *xyz;    /* host [n_nodes][3]            */
+    const int32_t *tri;   /* host [n_elems][3]            */
+    const uint8_t *fixed; /* host [n_nodes][3] or NULL    */
+} ens_mesh;
+
+/* Material and integration constants.
+ * rho    : density (lumped mass m_i = sum over elements of rho A_e hbar_e / 3).
+ * nu     : Poisson ratio of the constitutive matrix C (Section 2.2.1), 0 <= nu < 1.
+ * kshear : transverse shear factor k (5/6 in the paper).
+ * alpha  : mass-proportional damping C = alpha M, >= 0.
+ * dt     : time step, > 0. ens_create returns ENS_ERR_UNSTABLE_DT when dt exceeds
+ *          2 / omega_lower, where omega_lower^2 is an element-local Rayleigh quotient
+ *          of M^-1 K_s (a lower bound of the top eigenvalue, so such a dt certainly
+ *          diverges). omega_upper (element eigenvalue bound) is reported by ens_info:
+ *          dt <= 2 / omega_upper is guaranteed stable.
+ * precision : an ens_precision value. flags : must be 0.                            */
+typedef struct {
+    double rho;
+    double nu;
+    double kshear;
+    double alpha;
+    double dt;
+    int32_t precision;
+    int32_t flags;
+} ens_params;
+
+/* Optional device allocator. alloc returns a device pointer of at least `bytes`
+ * bytes (aligned to 256 bytes) usable on `stream`, or NULL on failure; release frees
+ * it. NULL allocator: cudaMalloc / cudaFree.                                        */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*release)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} ens_allocator;
+
+/* Sizes and the traffic model of one context (read-only report).                    */
+typedef struct {
+    int32_t n_nodes, n_elems, n_samples, n_samples_padded;
+    int32_t precision, n_modes;
+    int64_t n_steps_table; /* rows of the traction amplitude table              */
+    int64_t step;          /* index n of the current state u_n                  */
+    int64_t nnz;           /* node-to-element incidences (3 n_elems)            */
+    double dt;
+    double omega_lower;     /* lower bound of the top angular frequency         */
+    double omega_upper;     /* upper bound of the top angular frequency         */
+    double bytes_per_step;  /* algorithmic HBM bytes of one step                */
+    double device_bytes;    /* device memory held by the context                */
+} ens_info_t;
+
+/* Create a context: copies the mesh, builds the node-to-element incidence lists,
+ * computes on the device the element matrices per unit E*h (Section 2.2.1: B, C,
+ * k_e = sum_gp B^T C B A_e zeta w), the three-point Gauss products (E*h)_e,s and the
+ * lumped masses (Section 2.3), and sets the state to rest (u_0 = v_0 = 0).
+ * S       : ensemble width, >= 1.
+ * E_node, h_node : host [n_nodes][S] nodal modulus and thickness of every
+ *           realisation (sample index innermost), all > 0.
+ * stream  : cudaStream_t to run on (NULL = legacy default stream).
+ * alloc   : device allocator or NULL.
+ * out     : receives the context; on failure *out is NULL and the code is returned
+ *           (use ens_error_string for the text).                                   */
+int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const double *h_node,
+               const ens_params *params, void *stream, const ens_allocator *alloc,
+               ens_ctx **out);
+
+/* Wall traction history in separable form f_n = sum_j amp[n][j] * modes[j]
+ * (Section 2.2.3: the nodal force passed from the fluid to the structure; identical
+ * for every realisation). modes: host [J][n_nodes][3]; amp: host [n_steps][J].
+ * 1 <= J <= 16. All values finite (and within the binary32 range for the binary32
+ * forms). Replaces any previous table; the state is kept.                            */
+int ens_set_traction(ens_ctx *ctx, int32_t J, const double *modes, int64_t n_steps,
+                     const double *amp);
+
+/* Overwrite rows [first_row, first_row + n_rows) of the current amplitude table with
+ * amp (host [n_rows][J], J of the last ens_set_traction): the way a coupled fluid
+ * solver streams new load amplitudes while the structure advances (Section 2.2.3).
+ * The copy is ordered on the context stream before later steps; the host buffer may
+ * be reused when the call returns. ENS_ERR_RANGE if the rows fall outside the table. */
+int ens_set_amplitudes(ens_ctx *ctx, int64_t first_row, int64_t n_rows, const double *amp);
+
+/* Advance every realisation n >= 0 steps of Eq. (dynamicsCD) from the current step
+ * index; step k uses load row amp[k]. The first step after creation or ens_reset
+ * applies the Taylor start u_{-1} = u_0 - dt v_0 + dt^2/2 a_0. Returns ENS_ERR_RANGE
+ * (nothing is run) if the table has fewer than index + n rows, ENS_ERR_NONFINITE if a
+ * displacement became Inf/NaN during these steps.                                    */
+int ens_step(ens_ctx *ctx, int64_t n);
+
+/* Back to rest: u = v = 0, step index 0.                                             */
+int ens_reset(ens_ctx *ctx);
+
+/* Current displacements u_n as binary64. out: host array of S * n_nodes * 3 values in
+ * the given ENS_LAYOUT_*.                                                             */
+int ens_get_displacement(ens_ctx *ctx, double *out, int32_t layout);
+
+/* Same into device memory (binary64, caller-allocated, same sizes and layouts).      */
+int ens_get_displacement_device(ens_ctx *ctx, double *out_dev, int32_t layout);
+
+/* Ensemble mean and sample variance (divisor S - 1, 0 when S = 1) of u_n per dof
+ * (the ensemble means and bands of Section 3). mean, var: host [n_nodes][3].         */
+int ens_stats(ens_ctx *ctx, double *mean, double *var);
+
+/* Same into device memory (binary64 [n_nodes][3] each); runs asynchronously.        */
+int ens_stats_device(ens_ctx *ctx, double *mean_dev, double *var_dev);
+
+/* Internal force K_s u_s of every realisation for a given displacement field
+ * (Section 2.4 assembly-free product; the term dt^2 K u_n of Eq. dynamicsCD without
+ * dt^2), computed by the same device path and precision as ens_step. u, f: host
+ * [n_nodes][3][S] binary64. The context state is not changed.                       */
+int ens_internal_force(ens_ctx *ctx, const double *u, double *f);
+
+/* Per-realisation coefficients as binary64 (Section 2.2.1 Gauss rule, Section 2.3
+ * lumped mass): eh host [n_elems][S] = sum_gp w E zeta, minv host [n_nodes][S] =
+ * 1 / m. Either pointer may be NULL.                                                 */
+int ens_get_coefficients(ens_ctx *ctx, double *eh, double *minv);
+
+/* Element matrices per unit E*h in the global frame (Section 2.2.1), binary64, as the
+ * device computed them: kelem host [n_elems][9][9].                                  */
+int ens_get_element_matrices(ens_ctx *ctx, double *kelem);
+
+/* Checkpoint. ens_state_size gives the byte size; ens_get_state writes the state
+ * (step index, start flag, u, v in the context's precision) to a host buffer;
+ * ens_set_state restores one written by a context of identical sizes and precision. */
+int ens_state_size(const ens_ctx *ctx, size_t *bytes);
+int ens_get_state(ens_ctx *ctx, void *buf, size_t bytes);
+int ens_set_state(ens_ctx *ctx, const void *buf, size_t bytes);
+
+/* Sizes, step index and traffic model.                                               */
+int ens_info(const ens_ctx *ctx, ens_info_t *info);
+
+/* Message of the last failing call on ctx ("" if none); ens_error_string names a
+ * code. Both return static or context-owned storage.                                  */
+const char *ens_last_error(const ens_ctx *ctx);
+const char *ens_error_string(int code);
+
+/* Release every device and host resource of the context (NULL is a no-op).          */
+void ens_destroy(ens_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ENS_H */

@@ -1,0 +1,8 @@
+"""GB300 explicit ensemble solver for the segregated vessel-wall model
+(Li & Schiavazzi, arXiv 2101.09059): C ABI in include/ens.h, CUDA kernels in csrc/,
+and a thin Python binding."""
+from ._lib import build, load, declared_functions
+from .ensemble import Ensemble, EnsError, FP64, FP32_FORCE, KAHAN32, PRECISIONS
+
+__all__ = ["build", "load", "declared_functions", "Ensemble", "EnsError", "FP64", "FP32_FORCE",
+           "KAHAN32", "PRECISIONS"]

@@ -1,0 +1,798 @@
+// Host side of the C ABI declared in include/ens.h: argument checking, the node ->
+// element incidence lists, device memory, and the launch sequence of every call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ens.h"
+#include "ens_internal.cuh"
+
+using namespace ens;
+
+struct ens_ctx {
+    int32_t N = 0, E = 0, S = 0, Sp = 0, Q = 0, form = 0, J = 0;
+    int64_t nnz = 0, n_amp = 0, step = 0;
+    bool started = false;
+    int cur = 0;
+    double rho = 0, nu = 0, ks = 0, alpha = 0, dt = 0, w_lo = 0, w_hi = 0;
+    cudaStream_t stream = nullptr;
+    ens_allocator al{};
+    bool custom_alloc = false;
+    std::string err;
+    size_t held_bytes = 0;
+    std::vector<std::pair<void *, size_t>> bufs;
+
+    // device data
+    int32_t *rowptr = nullptr;
+    int4 *ent = nullptr;
+    uint8_t *fix = nullptr;
+    double *xyz_d = nullptr;
+    int32_t *tri_d = nullptr;
+    int32_t *ec2ent_d = nullptr;
+    void *kc = nullptr, *eh = nullptr, *minv = nullptr, *modes = nullptr, *amp = nullptr;
+    void *ug[2] = {nullptr, nullptr};
+    double *u64 = nullptr, *v64 = nullptr;
+    float *ulo = nullptr, *v32 = nullptr;
+    int *flags = nullptr;
+    int64_t *step_ctr = nullptr;
+    double *stat_mean = nullptr, *stat_var = nullptr;
+    double *export_buf = nullptr;
+    int *h_flags = nullptr;  // pinned
+};
+
+namespace {
+
+const char *code_name(int code) {
+    switch (code) {
+    case ENS_OK: return "ok";
+    case ENS_ERR_INVALID_ARG: return "invalid argument";
+    case ENS_ERR_ALLOC: return "device allocation failed";
+    case ENS_ERR_CUDA: return "CUDA runtime error";
+    case ENS_ERR_UNSTABLE_DT: return "time step above the stability limit";
+    case ENS_ERR_NONFINITE: return "non-finite displacement";
+    case ENS_ERR_TIMEOUT: return "device wait timed out";
+    case ENS_ERR_RANGE: return "step index past the end of the traction table";
+    case ENS_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown status";
+    }
+}
+
+int fail(ens_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = std::string(code_name(code)) + ": " + buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(c, ENS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+void *dev_alloc(ens_ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (c->custom_alloc) {
+        p = c->al.alloc(bytes, (void *)c->stream, c->al.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        c->bufs.emplace_back(p, bytes);
+        c->held_bytes += bytes;
+    }
+    return p;
+}
+
+void dev_free(ens_ctx *c, void *p) {
+    if (!p) return;
+    for (size_t k = 0; k < c->bufs.size(); k++) {
+        if (c->bufs[k].first == p) {
+            size_t bytes = c->bufs[k].second;
+            if (c->custom_alloc)
+                c->al.release(p, bytes, (void *)c->stream, c->al.user);
+            else
+                cudaFree(p);
+            c->held_bytes -= bytes;
+            c->bufs.erase(c->bufs.begin() + k);
+            return;
+        }
+    }
+}
+
+#define ALLOC(ptr, type, count)                                                              \
+    do {                                                                                     \
+        ptr = (type *)dev_alloc(c, sizeof(type) * (size_t)(count));                          \
+        if (!ptr)                                                                            \
+            return fail(c, ENS_ERR_ALLOC, "%zu bytes for %s", sizeof(type) * (size_t)(count), \
+                        #ptr);                                                               \
+    } while (0)
+
+bool finite_pos(const double *x, size_t n) {
+    for (size_t k = 0; k < n; k++)
+        if (!(std::isfinite(x[k]) && x[k] > 0.0)) return false;
+    return true;
+}
+
+bool finite_all(const double *x, size_t n) {
+    for (size_t k = 0; k < n; k++)
+        if (!std::isfinite(x[k])) return false;
+    return true;
+}
+
+size_t elem_size(int form) { return form == kFP64 ? 8 : 4; }
+
+// Algorithmic HBM bytes of one step: per node-sample the state traffic of the form
+// (u read + write, v read + write, (E h) of the E/N incident elements, 1/m), plus the
+// sample-independent geometry, incidence lists and traction patterns.
+double bytes_per_step(const ens_ctx *c) {
+    double per_ns = c->form == kFP64 ? 120.0 : (c->form == kFP32Force ? 108.0 : 84.0);
+    double ns = (double)c->N * c->S * per_ns;
+    double fixed = (double)c->E * 64.0 + (double)c->N * (12.0 + 24.0 * (c->J > 0 ? c->J : 1));
+    return ns + fixed;
+}
+
+template <typename R>
+StepArgs<R> make_args(ens_ctx *c) {
+    StepArgs<R> a{};
+    a.fv.rowptr = c->rowptr;
+    a.fv.ent = c->ent;
+    a.fv.kc = (const R *)c->kc;
+    a.fv.eh = (const R *)c->eh;
+    a.fv.N = c->N;
+    a.fv.Sp = c->Sp;
+    a.fv.Q = c->Q;
+    a.u64 = c->u64;
+    a.v64 = c->v64;
+    a.ulo = c->ulo;
+    a.v32 = c->v32;
+    a.minv = (const R *)c->minv;
+    a.fix = c->fix;
+    a.modes = (const R *)c->modes;
+    a.amp = (const R *)c->amp;
+    a.step_ctr = c->step_ctr;
+    a.J = c->J;
+    a.dt = c->dt;
+    a.flags = c->flags;
+    return a;
+}
+
+int run_steps(ens_ctx *c, int64_t n) {
+    const double beta = 0.5 * c->alpha * c->dt;
+    for (int64_t k = 0; k < n; k++) {
+        double c1, c2;
+        if (!c->started && k == 0) {  // Taylor start: v_{1/2} = (1 - beta) v_0 + dt/2 a_0
+            c1 = 1.0 - beta;
+            c2 = 0.5 * c->dt;
+        } else {
+            c1 = (1.0 - beta) / (1.0 + beta);
+            c2 = c->dt / (1.0 + beta);
+        }
+        cudaError_t e;
+        if (c->form == kFP64) {
+            StepArgs<double> a = make_args<double>(c);
+            a.ug_cur = (const double *)c->ug[c->cur];
+            a.ug_next = (double *)c->ug[c->cur ^ 1];
+            a.k_off = (int32_t)k;
+            a.c1 = c1;
+            a.c2 = c2;
+            e = launch_step<double>(c->form, a, false, c->stream);
+        } else {
+            StepArgs<float> a = make_args<float>(c);
+            a.ug_cur = (const float *)c->ug[c->cur];
+            a.ug_next = (float *)c->ug[c->cur ^ 1];
+            a.k_off = (int32_t)k;
+            a.c1 = c1;
+            a.c2 = c2;
+            e = launch_step<float>(c->form, a, false, c->stream);
+        }
+        if (e != cudaSuccess) return fail(c, ENS_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+        c->cur ^= 1;
+    }
+    return ENS_OK;
+}
+
+const void *state_main(const ens_ctx *c) {
+    if (c->form == kFP32Force) return c->u64;
+    return c->ug[c->cur];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ens_error_string(int code) { return code_name(code); }
+
+const char *ens_last_error(const ens_ctx *c) { return c ? c->err.c_str() : ""; }
+
+void ens_destroy(ens_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    while (!c->bufs.empty()) dev_free(c, c->bufs.back().first);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    delete c;
+}
+
+int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const double *h_node,
+               const ens_params *p, void *stream, const ens_allocator *alloc, ens_ctx **out) {
+    if (!out) return ENS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mesh || !p || !E_node || !h_node || !mesh->xyz || !mesh->tri) return ENS_ERR_INVALID_ARG;
+    const int32_t N = mesh->n_nodes, E = mesh->n_elems;
+    if (N < 3 || E < 1 || S < 1) return ENS_ERR_INVALID_ARG;
+    if ((int64_t)N * 3 * (((int64_t)S + 3) / 4 * 4) > (int64_t)INT32_MAX * 4) return ENS_ERR_INVALID_ARG;
+    if (!(p->rho > 0.0) || !(p->nu >= 0.0 && p->nu < 1.0) || !(p->kshear > 0.0) ||
+        !(p->alpha >= 0.0) || !(p->dt > 0.0) || !std::isfinite(p->rho) ||
+        !std::isfinite(p->kshear) || !std::isfinite(p->alpha) || !std::isfinite(p->dt) ||
+        p->precision < 0 || p->precision > 2 || p->flags != 0)
+        return ENS_ERR_INVALID_ARG;
+    if (alloc && (!alloc->alloc || !alloc->release)) return ENS_ERR_INVALID_ARG;
+    if (!finite_all(mesh->xyz, 3 * (size_t)N)) return ENS_ERR_INVALID_ARG;
+    if (!finite_pos(E_node, (size_t)N * S) || !finite_pos(h_node, (size_t)N * S))
+        return ENS_ERR_INVALID_ARG;
+
+    ens_ctx *c = new (std::nothrow) ens_ctx();
+    if (!c) return ENS_ERR_ALLOC;
+    c->N = N;
+    c->E = E;
+    c->S = S;
+    c->Sp = (S + 3) / 4 * 4;
+    c->form = p->precision;
+    c->Q = c->Sp / (c->form == kFP64 ? Vw<double>::V : Vw<float>::V);
+    c->rho = p->rho;
+    c->nu = p->nu;
+    c->ks = p->kshear;
+    c->alpha = p->alpha;
+    c->dt = p->dt;
+    c->stream = (cudaStream_t)stream;
+    if (alloc) {
+        c->al = *alloc;
+        c->custom_alloc = true;
+    }
+    int rc = [&]() -> int {
+        // ---- incidence lists (host) ----------------------------------------------
+        std::vector<int32_t> cnt(N + 1, 0);
+        for (int64_t e = 0; e < E; e++) {
+            const int32_t *t = mesh->tri + 3 * e;
+            for (int j = 0; j < 3; j++)
+                if (t[j] < 0 || t[j] >= N)
+                    return fail(c, ENS_ERR_INVALID_ARG, "element %lld has node id %d outside [0, %d)",
+                                (long long)e, t[j], N);
+            if (t[0] == t[1] || t[1] == t[2] || t[0] == t[2])
+                return fail(c, ENS_ERR_INVALID_ARG, "element %lld repeats a node", (long long)e);
+            for (int j = 0; j < 3; j++) cnt[t[j] + 1]++;
+        }
+        for (int32_t i = 0; i < N; i++) {
+            if (cnt[i + 1] == 0)
+                return fail(c, ENS_ERR_INVALID_ARG, "node %d belongs to no element (zero mass)", i);
+            cnt[i + 1] += cnt[i];
+        }
+        c->nnz = 3 * (int64_t)E;
+        std::vector<int32_t> rowptr(cnt), fillp(cnt.begin(), cnt.end() - 1);
+        std::vector<int4> ent(c->nnz);
+        std::vector<int32_t> ec2ent(3 * (size_t)E);
+        for (int32_t e = 0; e < E; e++) {
+            const int32_t *t = mesh->tri + 3 * (int64_t)e;
+            for (int cc = 0; cc < 3; cc++) {
+                int32_t i = t[cc];
+                int32_t pos = fillp[i]++;
+                ent[pos] = make_int4(e, t[(cc + 1) % 3], t[(cc + 2) % 3], cc);
+                ec2ent[3 * (size_t)e + cc] = pos;
+            }
+        }
+        std::vector<uint8_t> fixb(N, 0);
+        if (mesh->fixed)
+            for (int32_t i = 0; i < N; i++)
+                for (int d = 0; d < 3; d++)
+                    if (mesh->fixed[3 * (int64_t)i + d]) fixb[i] |= (uint8_t)(1u << d);
+
+        // ---- device copies of the inputs -------------------------------------------
+        const int64_t NSp = (int64_t)N * c->Sp;
+        ALLOC(c->rowptr, int32_t, N + 1);
+        ALLOC(c->ent, int4, c->nnz);
+        ALLOC(c->fix, uint8_t, N);
+        ALLOC(c->xyz_d, double, 3 * (int64_t)N);
+        ALLOC(c->tri_d, int32_t, 3 * (int64_t)E);
+        ALLOC(c->ec2ent_d, int32_t, 3 * (int64_t)E);
+        ALLOC(c->flags, int, 4);
+        ALLOC(c->step_ctr, int64_t, 1);
+        CK(cudaMallocHost((void **)&c->h_flags, 4 * sizeof(int)));
+        CK(cudaMemcpyAsync(c->rowptr, rowptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ent, ent.data(), sizeof(int4) * c->nnz, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->fix, fixb.data(), N, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->xyz_d, mesh->xyz, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->tri_d, mesh->tri, sizeof(int32_t) * 3 * (int64_t)E, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->ec2ent_d, ec2ent.data(), sizeof(int32_t) * 3 * (int64_t)E, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->stream));
+        CK(cudaMemsetAsync(c->step_ctr, 0, sizeof(int64_t), c->stream));
+
+        // padded nodal fields: padding samples repeat sample 0 (finite, never reported)
+        std::vector<double> Ep((size_t)NSp), hp((size_t)NSp);
+        for (int64_t i = 0; i < N; i++)
+            for (int32_t s = 0; s < c->Sp; s++) {
+                int32_t src = s < S ? s : 0;
+                Ep[i * c->Sp + s] = E_node[i * S + src];
+                hp[i * c->Sp + s] = h_node[i * S + src];
+            }
+        double *En_d, *hn_d, *kc64, *area, *laml, *lamh, *xsq, *eh64, *m64, *w2lo, *w2hi;
+        int *bad;
+        ALLOC(En_d, double, NSp);
+        ALLOC(hn_d, double, NSp);
+        ALLOC(kc64, double, 18 * c->nnz);
+        ALLOC(area, double, E);
+        ALLOC(laml, double, E);
+        ALLOC(lamh, double, E);
+        ALLOC(xsq, double, 3 * (int64_t)E);
+        ALLOC(eh64, double, (int64_t)E * c->Sp);
+        ALLOC(m64, double, NSp);
+        ALLOC(w2lo, double, E);
+        ALLOC(w2hi, double, E);
+        ALLOC(bad, int, 1);
+        CK(cudaMemcpyAsync(En_d, Ep.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(hn_d, hp.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
+        const int big = 0x7fffffff;
+        CK(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+
+        // ---- set-up kernels ----------------------------------------------------------
+        CK(launch_setup_elements(c->xyz_d, c->tri_d, c->ec2ent_d, E, c->nu, c->ks, kc64, area,
+                                 laml, lamh, xsq, nullptr, bad, c->stream));
+        CK(launch_setup_eh(c->tri_d, En_d, hn_d, E, c->Sp, eh64, c->stream));
+        CK(launch_setup_mass(c->rowptr, c->ent, area, hn_d, N, c->Sp, c->rho, m64, c->stream));
+        CK(launch_setup_stability(c->tri_d, eh64, m64, area, hn_d, laml, lamh, xsq, E, S, c->Sp,
+                                  c->rho, w2lo, w2hi, c->stream));
+        const size_t es = elem_size(c->form);
+        const int to_f = c->form != kFP64;
+        c->kc = dev_alloc(c, es * (size_t)c->nnz * (to_f ? 20 : 18));
+        c->minv = dev_alloc(c, es * (size_t)NSp);
+        if (!c->kc || !c->minv) return fail(c, ENS_ERR_ALLOC, "coefficient buffers");
+        CK(launch_pack_kc(kc64, c->nnz, c->kc, to_f, c->stream));
+        CK(launch_convert(m64, NSp, c->minv, to_f, 1, c->stream));
+        if (to_f) {
+            c->eh = dev_alloc(c, es * (size_t)E * c->Sp);
+            if (!c->eh) return fail(c, ENS_ERR_ALLOC, "eh buffer");
+            CK(launch_convert(eh64, (int64_t)E * c->Sp, c->eh, 1, 0, c->stream));
+        } else {
+            c->eh = eh64;
+        }
+        int hbad = 0;
+        std::vector<double> h_lo(E), h_hi(E);
+        CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(h_lo.data(), w2lo, sizeof(double) * E, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(h_hi.data(), w2hi, sizeof(double) * E, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaGetLastError());
+        dev_free(c, En_d);
+        dev_free(c, hn_d);
+        dev_free(c, kc64);
+        dev_free(c, area);
+        dev_free(c, laml);
+        dev_free(c, lamh);
+        dev_free(c, xsq);
+        dev_free(c, m64);
+        dev_free(c, w2lo);
+        dev_free(c, w2hi);
+        dev_free(c, bad);
+        if (to_f) dev_free(c, eh64);
+        if (hbad != big)
+            return fail(c, ENS_ERR_INVALID_ARG, "element %d has zero or non-finite area", hbad);
+        double lo = 0.0, hi = 0.0;
+        for (int32_t e = 0; e < E; e++) {
+            lo = std::fmax(lo, h_lo[e]);
+            hi = std::fmax(hi, h_hi[e]);
+        }
+        c->w_lo = std::sqrt(lo);
+        c->w_hi = std::sqrt(hi);
+        if (c->dt * c->w_lo > 2.0)
+            return fail(c, ENS_ERR_UNSTABLE_DT,
+                        "dt = %.6g s exceeds 2 / omega = %.6g s (omega >= %.6g rad/s)", c->dt,
+                        2.0 / c->w_lo, c->w_lo);
+
+        // ---- state at rest -------------------------------------------------------------
+        const size_t srow = sizeof(float) * (size_t)N * 3 * c->Sp;
+        if (c->form == kFP64) {
+            c->ug[0] = dev_alloc(c, 2 * srow);
+            c->ug[1] = dev_alloc(c, 2 * srow);
+            ALLOC(c->v64, double, (int64_t)N * 3 * c->Sp);
+        } else if (c->form == kFP32Force) {
+            c->ug[0] = dev_alloc(c, srow);
+            c->ug[1] = dev_alloc(c, srow);
+            ALLOC(c->u64, double, (int64_t)N * 3 * c->Sp);
+            ALLOC(c->v64, double, (int64_t)N * 3 * c->Sp);
+        } else {
+            c->ug[0] = dev_alloc(c, srow);
+            c->ug[1] = dev_alloc(c, srow);
+            ALLOC(c->ulo, float, (int64_t)N * 3 * c->Sp);
+            ALLOC(c->v32, float, (int64_t)N * 3 * c->Sp);
+        }
+        if (!c->ug[0] || !c->ug[1]) return fail(c, ENS_ERR_ALLOC, "state buffers");
+        ALLOC(c->stat_mean, double, 3 * (int64_t)N);
+        ALLOC(c->stat_var, double, 3 * (int64_t)N);
+        return ens_reset(c);
+    }();
+    if (rc != ENS_OK) {
+        ens_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return ENS_OK;
+}
+
+int ens_reset(ens_ctx *c) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    const size_t n = (size_t)c->N * 3 * c->Sp;
+    const size_t es = c->form == kFP64 ? 8 : 4;
+    CK(cudaMemsetAsync(c->ug[0], 0, es * n, c->stream));
+    CK(cudaMemsetAsync(c->ug[1], 0, es * n, c->stream));
+    if (c->u64) CK(cudaMemsetAsync(c->u64, 0, 8 * n, c->stream));
+    if (c->v64) CK(cudaMemsetAsync(c->v64, 0, 8 * n, c->stream));
+    if (c->ulo) CK(cudaMemsetAsync(c->ulo, 0, 4 * n, c->stream));
+    if (c->v32) CK(cudaMemsetAsync(c->v32, 0, 4 * n, c->stream));
+    CK(cudaMemsetAsync(c->step_ctr, 0, sizeof(int64_t), c->stream));
+    CK(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->cur = 0;
+    c->step = 0;
+    c->started = false;
+    return ENS_OK;
+}
+
+int ens_set_traction(ens_ctx *c, int32_t J, const double *modes, int64_t n_steps,
+                     const double *amp) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (J < 1 || J > kMaxModes || !modes || !amp || n_steps < 1)
+        return fail(c, ENS_ERR_INVALID_ARG, "J = %d (1..%d), n_steps = %lld", J, kMaxModes,
+                    (long long)n_steps);
+    const size_t nm = (size_t)J * c->N * 3, na = (size_t)n_steps * J;
+    if (!finite_all(modes, nm) || !finite_all(amp, na))
+        return fail(c, ENS_ERR_INVALID_ARG, "non-finite traction values");
+    if (c->form != kFP64) {
+        for (size_t k = 0; k < nm; k++)
+            if (std::fabs(modes[k]) > 3.0e38)
+                return fail(c, ENS_ERR_INVALID_ARG, "traction pattern outside the binary32 range");
+        for (size_t k = 0; k < na; k++)
+            if (std::fabs(amp[k]) > 3.0e38)
+                return fail(c, ENS_ERR_INVALID_ARG, "traction amplitude outside the binary32 range");
+    }
+    const size_t es = elem_size(c->form);
+    CK(cudaStreamSynchronize(c->stream));
+    dev_free(c, c->modes);
+    dev_free(c, c->amp);
+    c->modes = c->amp = nullptr;
+    c->J = 0;
+    c->modes = dev_alloc(c, es * nm);
+    c->amp = dev_alloc(c, es * na);
+    if (!c->modes || !c->amp) return fail(c, ENS_ERR_ALLOC, "traction buffers");
+    if (c->form == kFP64) {
+        CK(cudaMemcpyAsync(c->modes, modes, 8 * nm, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->amp, amp, 8 * na, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> fm(nm), fa(na);
+        for (size_t k = 0; k < nm; k++) fm[k] = (float)modes[k];
+        for (size_t k = 0; k < na; k++) fa[k] = (float)amp[k];
+        CK(cudaMemcpyAsync(c->modes, fm.data(), 4 * nm, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->amp, fa.data(), 4 * na, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    c->J = J;
+    c->n_amp = n_steps;
+    return ENS_OK;
+}
+
+int ens_set_amplitudes(ens_ctx *c, int64_t first_row, int64_t n_rows, const double *amp) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (c->J == 0) return fail(c, ENS_ERR_STATE, "no traction table (call ens_set_traction)");
+    if (!amp || n_rows < 0) return fail(c, ENS_ERR_INVALID_ARG, "null amplitudes or n_rows < 0");
+    if (first_row < 0 || first_row + n_rows > c->n_amp)
+        return fail(c, ENS_ERR_RANGE, "rows [%lld, %lld) outside the %lld-row table",
+                    (long long)first_row, (long long)(first_row + n_rows), (long long)c->n_amp);
+    const size_t na = (size_t)n_rows * c->J;
+    if (!finite_all(amp, na)) return fail(c, ENS_ERR_INVALID_ARG, "non-finite amplitudes");
+    if (na == 0) return ENS_OK;
+    if (c->form == kFP64) {
+        CK(cudaMemcpyAsync((double *)c->amp + first_row * c->J, amp, 8 * na,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> fa(na);
+        for (size_t k = 0; k < na; k++) {
+            if (std::fabs(amp[k]) > 3.0e38)
+                return fail(c, ENS_ERR_INVALID_ARG, "amplitude outside the binary32 range");
+            fa[k] = (float)amp[k];
+        }
+        CK(cudaMemcpyAsync((float *)c->amp + first_row * c->J, fa.data(), 4 * na,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return ENS_OK;
+}
+
+int ens_step(ens_ctx *c, int64_t n) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (n < 0) return fail(c, ENS_ERR_INVALID_ARG, "n = %lld", (long long)n);
+    if (c->J == 0) return fail(c, ENS_ERR_STATE, "no traction table (call ens_set_traction)");
+    if (c->step + n > c->n_amp)
+        return fail(c, ENS_ERR_RANGE, "step %lld + %lld > %lld table rows", (long long)c->step,
+                    (long long)n, (long long)c->n_amp);
+    if (n == 0) return ENS_OK;
+    if (n > INT32_MAX) return fail(c, ENS_ERR_INVALID_ARG, "n too large for one call");
+    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+    int rc = run_steps(c, n);
+    if (rc != ENS_OK) return rc;
+    CK(launch_advance(c->step_ctr, n, c->stream));
+    CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->step += n;
+    c->started = true;
+    if (c->h_flags[0])
+        return fail(c, ENS_ERR_NONFINITE, "displacement became Inf/NaN before step %lld",
+                    (long long)c->step);
+    return ENS_OK;
+}
+
+int ens_get_displacement_device(ens_ctx *c, double *out, int32_t layout) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!out || (layout != ENS_LAYOUT_SNC && layout != ENS_LAYOUT_NCS))
+        return fail(c, ENS_ERR_INVALID_ARG, "output pointer or layout");
+    CK(launch_export(c->form, state_main(c), c->ulo, c->N, c->S, c->Sp, out, layout, c->stream));
+    return ENS_OK;
+}
+
+int ens_get_displacement(ens_ctx *c, double *out, int32_t layout) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!out || (layout != ENS_LAYOUT_SNC && layout != ENS_LAYOUT_NCS))
+        return fail(c, ENS_ERR_INVALID_ARG, "output pointer or layout");
+    const size_t n = (size_t)c->N * 3 * c->S;
+    if (!c->export_buf) {
+        c->export_buf = (double *)dev_alloc(c, 8 * n);
+        if (!c->export_buf) return fail(c, ENS_ERR_ALLOC, "export buffer");
+    }
+    int rc = ens_get_displacement_device(c, c->export_buf, layout);
+    if (rc != ENS_OK) return rc;
+    CK(cudaMemcpyAsync(out, c->export_buf, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ENS_OK;
+}
+
+int ens_stats_device(ens_ctx *c, double *mean, double *var) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!mean || !var) return fail(c, ENS_ERR_INVALID_ARG, "null output");
+    CK(launch_stats(c->form, state_main(c), c->ulo, c->N, c->S, c->Sp, mean, var, c->stream));
+    return ENS_OK;
+}
+
+int ens_stats(ens_ctx *c, double *mean, double *var) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!mean || !var) return fail(c, ENS_ERR_INVALID_ARG, "null output");
+    int rc = ens_stats_device(c, c->stat_mean, c->stat_var);
+    if (rc != ENS_OK) return rc;
+    const size_t n = 3 * (size_t)c->N;
+    CK(cudaMemcpyAsync(mean, c->stat_mean, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(var, c->stat_var, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ENS_OK;
+}
+
+int ens_internal_force(ens_ctx *c, const double *u, double *f) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!u || !f) return fail(c, ENS_ERR_INVALID_ARG, "null array");
+    const size_t n = (size_t)c->N * 3 * c->S, np = (size_t)c->N * 3 * c->Sp;
+    if (!finite_all(u, n)) return fail(c, ENS_ERR_INVALID_ARG, "non-finite displacement");
+    const size_t es = elem_size(c->form);
+    double *in_d = (double *)dev_alloc(c, 8 * n);
+    void *ug = dev_alloc(c, es * np);
+    double *f_d = (double *)dev_alloc(c, 8 * np);
+    int rc = ENS_OK;
+    if (!in_d || !ug || !f_d) rc = fail(c, ENS_ERR_ALLOC, "force buffers");
+    cudaError_t e = cudaSuccess;
+    if (rc == ENS_OK) {
+        e = cudaMemcpyAsync(in_d, u, 8 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_import(c->form, in_d, c->N, c->S, c->Sp, ug, nullptr, nullptr, c->stream);
+        if (e == cudaSuccess) {
+            if (c->form == kFP64) {
+                StepArgs<double> a = make_args<double>(c);
+                a.ug_cur = (const double *)ug;
+                a.force_out = f_d;
+                e = launch_step<double>(c->form, a, true, c->stream);
+            } else {
+                StepArgs<float> a = make_args<float>(c);
+                a.ug_cur = (const float *)ug;
+                a.force_out = f_d;
+                e = launch_step<float>(c->form, a, true, c->stream);
+            }
+        }
+        std::vector<double> fp;
+        if (e == cudaSuccess) {
+            fp.resize(np);
+            e = cudaMemcpyAsync(fp.data(), f_d, 8 * np, cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) {
+            for (size_t row = 0; row < (size_t)c->N * 3; row++)
+                memcpy(f + row * c->S, fp.data() + row * c->Sp, 8 * (size_t)c->S);
+        } else {
+            rc = fail(c, ENS_ERR_CUDA, "internal force: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, in_d);
+    dev_free(c, ug);
+    dev_free(c, f_d);
+    return rc;
+}
+
+int ens_get_coefficients(ens_ctx *c, double *eh, double *minv) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    const int to_f = c->form != kFP64;
+    auto fetch = [&](const void *src, int64_t rows, double *dst) -> int {
+        const size_t np = (size_t)rows * c->Sp;
+        std::vector<double> tmp(np);
+        if (to_f) {
+            std::vector<float> t32(np);
+            CK(cudaMemcpyAsync(t32.data(), src, 4 * np, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (size_t k = 0; k < np; k++) tmp[k] = (double)t32[k];
+        } else {
+            CK(cudaMemcpyAsync(tmp.data(), src, 8 * np, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+        for (int64_t r = 0; r < rows; r++)
+            memcpy(dst + r * c->S, tmp.data() + r * c->Sp, 8 * (size_t)c->S);
+        return ENS_OK;
+    };
+    if (eh) {
+        int rc = fetch(c->eh, c->E, eh);
+        if (rc != ENS_OK) return rc;
+    }
+    if (minv) {
+        int rc = fetch(c->minv, c->N, minv);
+        if (rc != ENS_OK) return rc;
+    }
+    return ENS_OK;
+}
+
+int ens_get_element_matrices(ens_ctx *c, double *kelem) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!kelem) return fail(c, ENS_ERR_INVALID_ARG, "null output");
+    double *kf = (double *)dev_alloc(c, 8 * 81 * (size_t)c->E);
+    double *area = (double *)dev_alloc(c, 8 * (size_t)c->E);
+    int *bad = (int *)dev_alloc(c, sizeof(int));
+    int rc = ENS_OK;
+    if (!kf || !area || !bad) rc = fail(c, ENS_ERR_ALLOC, "element matrix buffer");
+    if (rc == ENS_OK) {
+        cudaError_t e = launch_setup_elements(c->xyz_d, c->tri_d, c->ec2ent_d, c->E, c->nu, c->ks,
+                                              nullptr, area, nullptr, nullptr, nullptr, kf, bad,
+                                              c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(kelem, kf, 8 * 81 * (size_t)c->E, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = fail(c, ENS_ERR_CUDA, "element matrices: %s", cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, kf);
+    dev_free(c, area);
+    dev_free(c, bad);
+    return rc;
+}
+
+namespace {
+struct StateHeader {
+    uint64_t magic;
+    int32_t N, E, S, Sp, form, started;
+    int64_t step;
+    int64_t reserved[3];
+};
+const uint64_t kMagic = 0x31534e4557435345ull;  // "ESCWENS1"
+
+size_t state_bytes(const ens_ctx *c) {
+    const size_t n = (size_t)c->N * 3 * c->Sp;
+    size_t b = sizeof(StateHeader);
+    if (c->form == kFP64) b += 16 * n;                // u, v
+    else if (c->form == kFP32Force) b += 20 * n;      // u64, v64, u32 copy
+    else b += 12 * n;                                 // hi, lo, v
+    return b;
+}
+}  // namespace
+
+int ens_state_size(const ens_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return ENS_ERR_INVALID_ARG;
+    *bytes = state_bytes(c);
+    return ENS_OK;
+}
+
+int ens_get_state(ens_ctx *c, void *buf, size_t bytes) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!buf || bytes < state_bytes(c)) return fail(c, ENS_ERR_INVALID_ARG, "buffer too small");
+    StateHeader h{kMagic, c->N, c->E, c->S, c->Sp, c->form, c->started ? 1 : 0, c->step, {0, 0, 0}};
+    memcpy(buf, &h, sizeof(h));
+    char *p = (char *)buf + sizeof(h);
+    const size_t n = (size_t)c->N * 3 * c->Sp;
+    auto get = [&](const void *src, size_t b) -> int {
+        CK(cudaMemcpyAsync(p, src, b, cudaMemcpyDeviceToHost, c->stream));
+        p += b;
+        return ENS_OK;
+    };
+    int rc;
+    if (c->form == kFP64) {
+        if ((rc = get(c->ug[c->cur], 8 * n)) || (rc = get(c->v64, 8 * n))) return rc;
+    } else if (c->form == kFP32Force) {
+        if ((rc = get(c->u64, 8 * n)) || (rc = get(c->v64, 8 * n)) || (rc = get(c->ug[c->cur], 4 * n)))
+            return rc;
+    } else {
+        if ((rc = get(c->ug[c->cur], 4 * n)) || (rc = get(c->ulo, 4 * n)) || (rc = get(c->v32, 4 * n)))
+            return rc;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return ENS_OK;
+}
+
+int ens_set_state(ens_ctx *c, const void *buf, size_t bytes) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!buf || bytes < state_bytes(c)) return fail(c, ENS_ERR_INVALID_ARG, "buffer too small");
+    StateHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != kMagic || h.N != c->N || h.E != c->E || h.S != c->S || h.Sp != c->Sp ||
+        h.form != c->form || h.step < 0)
+        return fail(c, ENS_ERR_INVALID_ARG, "state written by a different context layout");
+    const char *p = (const char *)buf + sizeof(h);
+    const size_t n = (size_t)c->N * 3 * c->Sp;
+    CK(cudaStreamSynchronize(c->stream));
+    auto put = [&](void *dst, size_t b) -> int {
+        CK(cudaMemcpyAsync(dst, p, b, cudaMemcpyHostToDevice, c->stream));
+        p += b;
+        return ENS_OK;
+    };
+    c->cur = 0;
+    int rc;
+    if (c->form == kFP64) {
+        if ((rc = put(c->ug[0], 8 * n)) || (rc = put(c->v64, 8 * n))) return rc;
+    } else if (c->form == kFP32Force) {
+        if ((rc = put(c->u64, 8 * n)) || (rc = put(c->v64, 8 * n)) || (rc = put(c->ug[0], 4 * n)))
+            return rc;
+    } else {
+        if ((rc = put(c->ug[0], 4 * n)) || (rc = put(c->ulo, 4 * n)) || (rc = put(c->v32, 4 * n)))
+            return rc;
+    }
+    int64_t st = h.step;
+    CK(cudaMemcpyAsync(c->step_ctr, &st, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->step = h.step;
+    c->started = h.started != 0;
+    return ENS_OK;
+}
+
+int ens_info(const ens_ctx *c, ens_info_t *info) {
+    if (!c || !info) return ENS_ERR_INVALID_ARG;
+    ens_info_t r{};
+    r.n_nodes = c->N;
+    r.n_elems = c->E;
+    r.n_samples = c->S;
+    r.n_samples_padded = c->Sp;
+    r.precision = c->form;
+    r.n_modes = c->J;
+    r.n_steps_table = c->n_amp;
+    r.step = c->step;
+    r.nnz = c->nnz;
+    r.dt = c->dt;
+    r.omega_lower = c->w_lo;
+    r.omega_upper = c->w_hi;
+    r.bytes_per_step = bytes_per_step(c);
+    r.device_bytes = (double)c->held_bytes;
+    *info = r;
+    return ENS_OK;
+}
+
+}  // extern "C"

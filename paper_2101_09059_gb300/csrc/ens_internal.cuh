@@ -1,0 +1,101 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+//
+// Device data layout (sample index innermost, padded to Sp = round_up(S, 4) so every
+// row of a per-sample array starts on a 16-byte boundary for float4 / double2 access):
+//   u, v state            [N][3][Sp]     (precision-dependent, see StepArgs below)
+//   per-element (E h)     [E][Sp]
+//   inverse lumped mass   [N][Sp]
+//   node -> element CSR   rowptr [N+1], ent [nnz] = {element, node a, node b, corner}
+//                         where a, b are the element's other corners in cyclic order
+//   coupling blocks       kc [nnz][KC]: the 3 x 3 blocks K_{c,a}, K_{c,b} (row-major) of
+//                         the element matrix per unit E h, rows of the entry's corner c
+//   traction patterns     [J][N][3], amplitudes [n_steps][J]
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ens {
+
+constexpr int kBlock = 256;       // threads per block of the node kernels
+constexpr int kMaxModes = 16;     // traction patterns per context
+
+// Coupling-block storage per incidence: 18 values, padded to a 16-byte multiple.
+template <typename R> struct Kc;
+template <> struct Kc<double> { static constexpr int stride = 18; };  // 144 B
+template <> struct Kc<float> { static constexpr int stride = 20; };   // 80 B
+
+// Samples per thread: one 16-byte vector.
+template <typename R> struct Vw;
+template <> struct Vw<double> { static constexpr int V = 2; };
+template <> struct Vw<float> { static constexpr int V = 4; };
+
+enum Form : int { kFP64 = 0, kFP32Force = 1, kKahan32 = 2 };
+
+// Everything the internal-force gather reads (shared by all forms).
+template <typename R>
+struct ForceView {
+    const int32_t *rowptr;  // [N+1]
+    const int4 *ent;        // [nnz]
+    const R *kc;            // [nnz][Kc<R>::stride]
+    const R *eh;            // [E][Sp]
+    int32_t N, Sp, Q;       // Q = Sp / V threads per node
+};
+
+// Arguments of one step (or one force evaluation) for every form.
+//   kFP64      : ug = u (double, ping-pong), v (double, in place)
+//   kFP32Force : ug = binary32 copy of u (ping-pong), u64 / v64 binary64 (in place)
+//   kKahan32   : ug = hi part of u (ping-pong), ulo (in place), v32 (in place)
+template <typename R>
+struct StepArgs {
+    ForceView<R> fv;
+    const R *ug_cur;  // gathered displacement at step n
+    R *ug_next;       // written: displacement at step n + 1 (gather precision)
+    double *u64;      // kFP32Force state
+    double *v64;      // kFP64 / kFP32Force velocity
+    float *ulo;       // kKahan32 low part
+    float *v32;       // kKahan32 velocity
+    const R *minv;    // [N][Sp]
+    const uint8_t *fix;  // [N] bit d set = dof d fixed
+    const R *modes;   // [J][N][3]
+    const R *amp;     // [n_amp][J]
+    const int64_t *step_ctr;  // device step index of u_n at the start of the chunk
+    int32_t k_off;    // this launch advances step (*step_ctr + k_off)
+    int32_t J;
+    double c1, c2, dt;  // v_new = c1 v + c2 a ; u_new = u + dt v_new
+    double *force_out;  // force-only mode: [N][3][Sp] binary64
+    int *flags;         // [0] = non-finite seen
+};
+
+// Launchers (ens_step.cu).
+template <typename R>
+cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s);
+cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s);
+cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
+                         int32_t Sp, double *mean, double *var, cudaStream_t s);
+cudaError_t launch_export(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
+                          int32_t Sp, double *out, int layout, cudaStream_t s);
+cudaError_t launch_import(int form, const double *in_ncs, int32_t N, int32_t S, int32_t Sp,
+                          void *ug, double *u64, float *ulo, cudaStream_t s);
+
+// Setup launchers (ens_setup.cu).
+cudaError_t launch_setup_elements(const double *xyz, const int32_t *tri, const int32_t *ec2ent,
+                                  int32_t E, double nu, double kshear, double *kc64,
+                                  double *area, double *lam_lo, double *lam_hi, double *xsq,
+                                  double *kfull, int *bad, cudaStream_t s);
+cudaError_t launch_setup_eh(const int32_t *tri, const double *E_node, const double *h_node,
+                            int32_t E, int32_t Sp, double *eh64, cudaStream_t s);
+cudaError_t launch_setup_mass(const int32_t *rowptr, const int4 *ent, const double *area,
+                              const double *h_node, int32_t N, int32_t Sp, double rho,
+                              double *m64, cudaStream_t s);
+cudaError_t launch_setup_stability(const int32_t *tri, const double *eh64, const double *m64,
+                                   const double *area, const double *h_node,
+                                   const double *lam_lo, const double *lam_hi,
+                                   const double *xsq, int32_t E, int32_t S, int32_t Sp,
+                                   double rho, double *w2lo, double *w2hi, cudaStream_t s);
+cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
+                           cudaStream_t s);
+cudaError_t launch_convert(const double *in, int64_t n, void *out, int to_float, int invert,
+                           cudaStream_t s);
+
+}  // namespace ens

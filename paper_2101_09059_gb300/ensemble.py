@@ -1,0 +1,213 @@
+"""Python binding of the ensemble solver's C ABI (argument marshalling only).
+
+Every computation runs in libens.so (CUDA, sm_103a). PyTorch provides the device
+memory (its caching allocator is handed to the library as the allocator hook) and the
+stream the library launches on. Host arrays are numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32_force": FP32_FORCE, "kahan32": KAHAN32}
+LAYOUT_SNC, LAYOUT_NCS = 0, 1
+
+
+class EnsError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"[{code}] {message}")
+        self.code = code
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class _TorchAllocator:
+    """Adapter giving the library PyTorch's caching allocator on one device."""
+
+    def __init__(self, device: int):
+        torch = _torch()
+        self.device = device
+        self.sizes = {}
+
+        def alloc(nbytes, stream, user):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), device=device,
+                                                       stream=int(stream or 0))
+                return int(p)
+            except Exception:  # an exception may not cross into C
+                return None
+
+        def release(ptr, nbytes, stream, user):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self._alloc = _lib.ALLOC_FN(alloc)
+        self._release = _lib.RELEASE_FN(release)
+        self.struct = _lib.ens_allocator(self._alloc, self._release, None)
+
+
+def _check(L, ctx, rc):
+    if rc != 0:
+        msg = L.ens_last_error(ctx).decode() if ctx else ""
+        if not msg:
+            msg = L.ens_error_string(rc).decode()
+        raise EnsError(rc, msg)
+
+
+class Ensemble:
+    """S realisations of the wall model advanced together on one GPU.
+
+    xyz [N][3], tri [E][3], fixed [N][3] (uint8), E_node / h_node [N][S] (float64),
+    material constants and dt as in ens_params; precision: "fp64", "fp32_force",
+    "kahan32" or the ENS_* value. stream: a torch.cuda.Stream (default: current).
+    """
+
+    def __init__(self, xyz, tri, fixed, E_node, h_node, *, rho, nu, kshear, alpha, dt,
+                 precision="fp64", stream=None, torch_allocator: bool = True, device: int = 0):
+        torch = _torch()
+        self._L = _lib.load()
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32)
+        self.fixed = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+        E_node = np.ascontiguousarray(E_node, dtype=np.float64)
+        h_node = np.ascontiguousarray(h_node, dtype=np.float64)
+        self.N, self.E = self.xyz.shape[0], self.tri.shape[0]
+        self.S = int(E_node.shape[1])
+        self.precision = PRECISIONS.get(precision, precision)
+        self.device = device
+        with torch.cuda.device(device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self._allocator = _TorchAllocator(device) if torch_allocator else None
+        mesh = _lib.ens_mesh(self.N, self.E, self.xyz.ctypes.data, self.tri.ctypes.data,
+                             None if self.fixed is None else self.fixed.ctypes.data)
+        params = _lib.ens_params(rho, nu, kshear, alpha, dt, int(self.precision), 0)
+        out = ctypes.c_void_p()
+        alloc_p = ctypes.byref(self._allocator.struct) if self._allocator else None
+        with torch.cuda.device(device):
+            rc = self._L.ens_create(ctypes.byref(mesh), self.S, _ptr(E_node), _ptr(h_node),
+                                    ctypes.byref(params), ctypes.c_void_p(self.stream.cuda_stream),
+                                    alloc_p, ctypes.byref(out))
+        if rc != 0:
+            raise EnsError(rc, self._L.ens_error_string(rc).decode())
+        self._ctx = out
+
+    @classmethod
+    def from_case(cls, case, precision="fp64", **kw):
+        """Build from a workload dict with keys mesh, E, h, rho, nu, kshear, alpha, dt,
+        modes, amp (the traction table is set too)."""
+        m = case["mesh"]
+        ens = cls(m.xyz, m.tri, m.fixed, case["E"], case["h"], rho=case["rho"], nu=case["nu"],
+                  kshear=case["kshear"], alpha=case["alpha"], dt=case["dt"], precision=precision,
+                  **kw)
+        ens.set_traction(case["modes"], case["amp"])
+        return ens
+
+    # -- life cycle ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.ens_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _call(self, name, *args):
+        _check(self._L, self._ctx, getattr(self._L, name)(self._ctx, *args))
+
+    # -- ABI calls ------------------------------------------------------------------
+    def set_traction(self, modes, amp):
+        modes = np.ascontiguousarray(modes, dtype=np.float64)
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        if modes.ndim != 3 or modes.shape[1:] != (self.N, 3) or amp.ndim != 2 or amp.shape[1] != modes.shape[0]:
+            raise ValueError("modes must be [J][N][3] and amp [n_steps][J]")
+        self._call("ens_set_traction", modes.shape[0], _ptr(modes), amp.shape[0], _ptr(amp))
+
+    def set_amplitudes(self, first_row: int, amp):
+        amp = np.ascontiguousarray(amp, dtype=np.float64)
+        self._call("ens_set_amplitudes", int(first_row), amp.shape[0], _ptr(amp))
+
+    def step(self, n: int = 1):
+        self._call("ens_step", int(n))
+
+    def reset(self):
+        self._call("ens_reset")
+
+    def displacement(self, layout: str = "snc") -> np.ndarray:
+        lay = LAYOUT_SNC if layout == "snc" else LAYOUT_NCS
+        shape = (self.S, self.N, 3) if lay == LAYOUT_SNC else (self.N, 3, self.S)
+        out = np.empty(shape, dtype=np.float64)
+        self._call("ens_get_displacement", _ptr(out), lay)
+        return out
+
+    def displacement_device(self, out, layout: str = "snc"):
+        """Write u_n into a float64 CUDA tensor (asynchronous on the context stream)."""
+        lay = LAYOUT_SNC if layout == "snc" else LAYOUT_NCS
+        assert out.is_cuda and out.dtype == _torch().float64 and out.numel() == self.S * self.N * 3
+        self._call("ens_get_displacement_device", ctypes.c_void_p(out.data_ptr()), lay)
+        return out
+
+    def stats(self):
+        mean = np.empty((self.N, 3))
+        var = np.empty((self.N, 3))
+        self._call("ens_stats", _ptr(mean), _ptr(var))
+        return mean, var
+
+    def stats_device(self, mean, var):
+        self._call("ens_stats_device", ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()))
+        return mean, var
+
+    def internal_force(self, u_ncs) -> np.ndarray:
+        u = np.ascontiguousarray(u_ncs, dtype=np.float64)
+        assert u.shape == (self.N, 3, self.S)
+        f = np.empty_like(u)
+        self._call("ens_internal_force", _ptr(u), _ptr(f))
+        return f
+
+    def coefficients(self):
+        eh = np.empty((self.E, self.S))
+        minv = np.empty((self.N, self.S))
+        self._call("ens_get_coefficients", _ptr(eh), _ptr(minv))
+        return eh, minv
+
+    def element_matrices(self) -> np.ndarray:
+        k = np.empty((self.E, 9, 9))
+        self._call("ens_get_element_matrices", _ptr(k))
+        return k
+
+    def get_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        self._call("ens_state_size", ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        self._call("ens_get_state", buf, n.value)
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._call("ens_set_state", buf, len(blob))
+
+    def info(self) -> dict:
+        i = _lib.ens_info_t()
+        self._call("ens_info", ctypes.byref(i))
+        return {name: getattr(i, name) for name, _ in i._fields_}

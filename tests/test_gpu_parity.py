@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances (relative L2 over all dofs and samples unless stated):
+  * FP64 form, element matrices and Gauss products: 1e-13 / 1e-14 (both sides evaluate
+    the same closed forms in binary64 with different operation orders).
+  * FP64 form, trajectories: 1e-10. Both integrate the same recursion in binary64; the
+    device sums K_{c,a} du_a + K_{c,b} du_b (translation-free offsets) and steps the
+    velocity form, the oracle sums the full element matrix and steps the two-displacement
+    form. Their per-step rounding differs by a few ulps of |K| |u|, which is up to R / h_e
+    (about 10 to 100) times |K u|; damping bounds the accumulation to about 1 / (alpha dt)
+    steps. 1e-10 leaves a margin of about two orders over that estimate.
+  * FP32 forms: 1e-5 (the accuracy target of the binary32 force paths).
+  * Statistics: 1e-12 relative to the largest |mean| / variance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2101_09059_gb300 as ens  # noqa: E402
+
+TOL = {"fp64": 1e-10, "fp32_force": 1e-5, "kahan32": 1e-5}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ens.load()
+
+
+def _oracle_run(case, n, samples=None):
+    mod = oracle.Model(case, samples=samples)
+    u, _ = mod.run(n)
+    return u  # [S][N][3]
+
+
+SMALL = [("one_triangle", 1), ("one_triangle", 3), ("plate", 5), ("tube_small", 8),
+         ("tube_small", 33)]
+
+
+def test_element_matrices_match_oracle():
+    case = synth.make_case("tube_small", S=2)
+    e = ens.Ensemble.from_case(case, precision="fp64")
+    k = e.element_matrices()
+    Kg, _ = oracle.element_matrices(case["mesh"].xyz, case["mesh"].tri, case["nu"], case["kshear"])
+    assert rel_l2(k, Kg) < 1e-13
+    assert np.abs(k - Kg).max() < 1e-13 * np.abs(Kg).max()
+    e.close()
+
+
+@pytest.mark.parametrize("name,S", SMALL)
+def test_coefficients_match_oracle(name, S):
+    case = synth.make_case(name, S=S)
+    e = ens.Ensemble.from_case(case, precision="fp64")
+    eh, minv = e.coefficients()
+    mod = oracle.Model(case)
+    assert np.abs(eh - mod.eh_se.T).max() <= 1e-14 * np.abs(mod.eh_se).max()
+    assert np.abs(minv - 1.0 / mod.m_sn.T).max() <= 1e-14 * np.abs(1.0 / mod.m_sn).max()
+    e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+@pytest.mark.parametrize("name,S", SMALL)
+def test_internal_force_matches_oracle(name, S, precision):
+    case = synth.make_case(name, S=S)
+    e = ens.Ensemble.from_case(case, precision=precision)
+    mod = oracle.Model(case)
+    rng = np.random.default_rng(7)
+    # a smooth large displacement plus a small random part: the realistic regime
+    u = np.empty((mod.S, mod.N, 3))
+    u[:] = 1e-3 * case["mesh"].xyz[None, :, :] / np.abs(case["mesh"].xyz).max()
+    u += 1e-5 * rng.standard_normal(u.shape)
+    f_ref = mod.internal_force(u)
+    f = e.internal_force(np.ascontiguousarray(u.transpose(1, 2, 0)))
+    err = rel_l2(f.transpose(2, 0, 1), f_ref)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert err < tol, err
+    e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+@pytest.mark.parametrize("name,S", SMALL)
+def test_trajectory_small_meshes(name, S, precision):
+    case = synth.make_case(name, S=S)
+    n = case["n_steps"]
+    ref = _oracle_run(case, n)
+    e = ens.Ensemble.from_case(case, precision=precision)
+    e.step(n // 2)
+    e.step(n - n // 2)
+    u = e.displacement("snc")
+    assert rel_l2(u, ref) < TOL[precision]
+    e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+def test_tube_40x40_full_run(case_tiny, precision):
+    n = case_tiny["n_steps"]
+    ref = _oracle_run(case_tiny, n)
+    e = ens.Ensemble.from_case(case_tiny, precision=precision)
+    for _ in range(4):
+        e.step(n // 4)
+    u = e.displacement("snc")
+    err = rel_l2(u, ref)
+    print(f"tube_40x40 {precision}: rel-L2 {err:.3e}")
+    assert err < TOL[precision]
+    per_sample = [rel_l2(u[s], ref[s]) for s in range(u.shape[0])]
+    assert max(per_sample) < 10 * TOL[precision]
+    mean, var = e.stats()
+    m_ref, v_ref = oracle.stats(ref)
+    if precision == "fp64":
+        assert np.abs(mean - m_ref).max() <= 1e-9 * np.abs(m_ref).max()
+    # statistics of the device state must equal the two-pass statistics of that state
+    m2, v2 = oracle.stats(u)
+    assert np.abs(mean - m2).max() <= 1e-12 * np.abs(m2).max()
+    assert np.abs(var - v2).max() <= 1e-12 * np.abs(v2).max()
+    e.close()
+
+
+def test_determinism_permutation_and_single_member(case_tiny):
+    n = 300
+    e1 = ens.Ensemble.from_case(case_tiny, precision="kahan32")
+    e1.step(n)
+    u1 = e1.displacement()
+    e1.reset()
+    e1.step(n)
+    assert np.array_equal(u1, e1.displacement())
+    e1.close()
+    perm = np.array([5, 2, 7, 0, 1, 6, 3, 4])
+    cp = dict(case_tiny, E=case_tiny["E"][:, perm], h=case_tiny["h"][:, perm])
+    e2 = ens.Ensemble.from_case(cp, precision="kahan32")
+    e2.step(n)
+    assert np.array_equal(e2.displacement(), u1[perm])
+    e2.close()
+    c1 = dict(case_tiny, E=case_tiny["E"][:, [6]], h=case_tiny["h"][:, [6]], S=1)
+    e3 = ens.Ensemble.from_case(c1, precision="kahan32")
+    e3.step(n)
+    assert np.array_equal(e3.displacement()[0], u1[6])
+    e3.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "kahan32", "fp32_force"])
+def test_checkpoint_restart_is_bitwise(case_tiny, precision):
+    e = ens.Ensemble.from_case(case_tiny, precision=precision)
+    e.step(200)
+    blob = e.get_state()
+    e.step(200)
+    u_a = e.displacement()
+    e2 = ens.Ensemble.from_case(case_tiny, precision=precision)
+    e2.set_state(blob)
+    assert e2.info()["step"] == 200
+    e2.step(200)
+    assert np.array_equal(e2.displacement(), u_a)
+    e.close()
+    e2.close()
+
+
+def test_error_paths(case_tiny):
+    e = ens.Ensemble(case_tiny["mesh"].xyz, case_tiny["mesh"].tri, case_tiny["mesh"].fixed,
+                     case_tiny["E"], case_tiny["h"], rho=case_tiny["rho"], nu=case_tiny["nu"],
+                     kshear=case_tiny["kshear"], alpha=case_tiny["alpha"], dt=case_tiny["dt"])
+    with pytest.raises(ens.EnsError) as ei:
+        e.step(1)
+    assert ei.value.code == -8          # no traction table
+    e.set_traction(case_tiny["modes"], case_tiny["amp"][:10])
+    with pytest.raises(ens.EnsError) as ei:
+        e.step(11)
+    assert ei.value.code == -7          # past the table
+    e.step(10)
+    e.close()
+    f32 = ens.Ensemble.from_case(case_tiny, precision="kahan32")
+    with pytest.raises(ens.EnsError) as ei:
+        f32.set_traction(case_tiny["modes"], np.full((5, 1), 1e300))
+    assert ei.value.code == -1          # amplitude outside the binary32 range
+    f32.close()
+    with pytest.raises(ens.EnsError) as ei:
+        ens.Ensemble.from_case(dict(case_tiny, dt=20 * case_tiny["dt"]))
+    assert ei.value.code == -4          # certainly unstable step
+
+
+def _true_omega(case):
+    from oracle import assembled
+    import scipy.linalg as sla
+    mod = oracle.Model(case)
+    w = 0.0
+    for s in range(mod.S):
+        K = assembled.assemble(mod, s).toarray()
+        M = assembled.lumped_mass_vector(mod, s)
+        free = np.flatnonzero(mod.fixed == 0)
+        lam = sla.eigh(K[np.ix_(free, free)], np.diag(M[free]), eigvals_only=True)
+        w = max(w, float(np.sqrt(lam.max())))
+    return w
+
+
+def test_unstable_step_is_reported_as_nonfinite():
+    """dt 20 % above the true limit 2 / omega_max (undamped) passes the element-local
+    check at creation, then the top mode grows by |lambda| ~ 3 per step until Inf."""
+    case = synth.make_case("tube_small", S=2, n_steps=2000, alpha=0.0)
+    dt = 2.4 / _true_omega(case)
+    e = ens.Ensemble.from_case(dict(case, dt=dt), precision="fp64")
+    assert e.info()["omega_lower"] * dt < 2.0
+    with pytest.raises(ens.EnsError) as ei:
+        e.step(2000)
+    assert ei.value.code == -5
+    e.close()
+
+
+def test_stability_bounds_bracket_true_frequency():
+    case = synth.make_case("tube_small", S=2)
+    e = ens.Ensemble.from_case(case)
+    info = e.info()
+    w_true = _true_omega(case)
+    assert info["omega_lower"] <= w_true * (1 + 1e-9)
+    assert info["omega_upper"] >= w_true * (1 - 1e-9)
+    e.close()
+
+
+def test_full_size_aneurysm_sampled_parity():
+    """The 200k-node, S = 64 aneurysm in the benchmark's launch configuration: the device
+    runs all 64 samples, the oracle two of them (samples are independent, so the subset
+    is exact), compared after 150 steps."""
+    case = synth.make_case("aneurysm", S=64, n_steps=150)
+    picks = [3, 60]
+    ref = _oracle_run(case, 150, samples=picks)
+    for precision in ("fp32_force", "kahan32", "fp64"):
+        e = ens.Ensemble.from_case(case, precision=precision)
+        e.step(150)
+        u = e.displacement()
+        for k, s in enumerate(picks):
+            err = rel_l2(u[s], ref[k])
+            print(f"aneurysm {precision} sample {s}: rel-L2 {err:.3e}")
+            assert err < TOL[precision]
+        e.close()
+
+
+def test_streamed_amplitudes_equal_full_table():
+    case = synth.make_case("tube_small", S=3, n_steps=60)
+    full = ens.Ensemble.from_case(case, precision="fp32_force")
+    full.step(60)
+    u_full = full.displacement()
+    full.close()
+    zero = dict(case, amp=np.zeros_like(case["amp"]))
+    st = ens.Ensemble.from_case(zero, precision="fp32_force")
+    for r0 in range(0, 60, 20):
+        st.set_amplitudes(r0, case["amp"][r0:r0 + 20])
+        st.step(20)
+    assert np.array_equal(st.displacement(), u_full)
+    with pytest.raises(ens.EnsError) as ei:
+        st.set_amplitudes(50, case["amp"][:20])
+    assert ei.value.code == -7
+    st.close()
