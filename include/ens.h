@@ -179,6 +179,21 @@ int ens_stats_device(ens_ctx *ctx, double *mean_dev, double *var_dev);
  * [n_nodes][3][S] binary64. The context state is not changed.                       */
 int ens_internal_force(ens_ctx *ctx, const double *u, double *f);
 
+/* The same internal force as ens_internal_force, for callers that may not allocate
+ * device memory at this point (a host framework that owns all device memory, or a
+ * loop where cudaMalloc and its implicit synchronisation are not allowed). The paper
+ * has no counterpart; this is a library service.
+ * u_dev, f_dev: device [n_nodes][3][S] binary64, caller-owned, on the context's device.
+ * Staging lives in one static device array of 32 MiB per GPU (held from library load
+ * to process exit); contexts needing more than n_nodes * 3 * Sp * (e + 8) <= 32 MiB
+ * (e = 8 for ENS_FP64, 4 otherwise) get ENS_ERR_INVALID_ARG. Nothing is allocated.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress); make
+ * that first call before any stream capture. Asynchronous on the context stream. All
+ * calls share the one array, so calls that overlap on the GPU (other streams, other
+ * contexts on the same device) race; every staged value is rewritten before it is read,
+ * so a call never sees the previous call's contents.                                 */
+int ens_internal_force_noalloc(ens_ctx *ctx, const double *u_dev, double *f_dev);
+
 /* Per-realisation coefficients as binary64 (Section 2.2.1 Gauss rule, Section 2.3
  * lumped mass): eh host [n_elems][S] = sum_gp w E zeta, minv host [n_nodes][S] =
  * 1 / m. Either pointer may be NULL.                                                 */

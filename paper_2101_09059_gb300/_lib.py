@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True):
         "ens_stats": ([vp, dp, dp], ctypes.c_int),
         "ens_stats_device": ([vp, dp, dp], ctypes.c_int),
         "ens_internal_force": ([vp, dp, dp], ctypes.c_int),
+        "ens_internal_force_noalloc": ([vp, dp, dp], ctypes.c_int),
         "ens_get_coefficients": ([vp, dp, dp], ctypes.c_int),
         "ens_get_element_matrices": ([vp, dp], ctypes.c_int),
         "ens_state_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),

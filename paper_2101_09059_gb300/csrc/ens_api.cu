@@ -796,3 +796,81 @@ int ens_info(const ens_ctx *c, ens_info_t *info) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Internal force without any allocation.
+//
+// ens_internal_force allocates three device buffers per call. Some callers cannot
+// allocate at that point: code running inside another framework's fixed memory
+// budget, real-time loops that forbid cudaMalloc (it can synchronise the device), and
+// hosts that hand this library device buffers but no allocation rights. This variant
+// stages through a file-scope device array instead. Its size is fixed below; every GPU
+// that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on device `dev`, looked up once per device with
+// that device current (in host code the symbol name is only a host-side stand-in).
+int static_scratch(ens_ctx *c, int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(c, ENS_ERR_INVALID_ARG, "device %d", dev);
+    if (g_scratch_addr[dev] == nullptr) {
+        int prev = -1;
+        CK(cudaGetDevice(&prev));
+        if (prev != dev) CK(cudaSetDevice(dev));
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (prev != dev) cudaSetDevice(prev);
+        if (e != cudaSuccess || p == nullptr)
+            return fail(c, ENS_ERR_CUDA, "cudaGetSymbolAddress(g_static_scratch): %s",
+                        cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return ENS_OK;
+}
+
+}  // namespace
+
+extern "C" int ens_internal_force_noalloc(ens_ctx *c, const double *u_dev, double *f_dev) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (!u_dev || !f_dev) return fail(c, ENS_ERR_INVALID_ARG, "null device array");
+    const size_t np = (size_t)c->N * 3 * c->Sp;
+    const size_t gbytes = ((elem_size(c->form) * np) + 255) & ~size_t(255);
+    const size_t need = gbytes + 8 * np;
+    if (need > kStaticScratchBytes)
+        return fail(c, ENS_ERR_INVALID_ARG,
+                    "needs %zu bytes of staging (N * 3 * Sp * (%zu + 8)), above the %zu-byte "
+                    "static scratch; use ens_internal_force",
+                    need, elem_size(c->form), kStaticScratchBytes);
+    cudaPointerAttributes attr{};
+    CK(cudaPointerGetAttributes(&attr, c->ug[0]));
+    void *base = nullptr;
+    int rc = static_scratch(c, attr.device, &base);
+    if (rc != ENS_OK) return rc;
+    void *ug = base;
+    double *f_pad = (double *)((char *)base + gbytes);
+    CK(launch_import(c->form, u_dev, c->N, c->S, c->Sp, ug, nullptr, nullptr, c->stream));
+    cudaError_t e;
+    if (c->form == kFP64) {
+        StepArgs<double> a = make_args<double>(c);
+        a.ug_cur = (const double *)ug;
+        a.force_out = f_pad;
+        e = launch_step<double>(c->form, a, true, c->stream);
+    } else {
+        StepArgs<float> a = make_args<float>(c);
+        a.ug_cur = (const float *)ug;
+        a.force_out = f_pad;
+        e = launch_step<float>(c->form, a, true, c->stream);
+    }
+    if (e != cudaSuccess) return fail(c, ENS_ERR_CUDA, "force launch: %s", cudaGetErrorString(e));
+    CK(cudaMemcpy2DAsync(f_dev, sizeof(double) * c->S, f_pad, sizeof(double) * c->Sp,
+                         sizeof(double) * c->S, (size_t)c->N * 3, cudaMemcpyDeviceToDevice,
+                         c->stream));
+    return ENS_OK;
+}
