@@ -287,6 +287,8 @@ def main():
             "hbm_frac": alg_bytes / per_launch_s / 1e9 / hbm_peak,
             "clocks": clk.summary(),
             "gpu_launches": K * (C + 2),
+            "kernel_variant": info["kernel_variant"],
+            "autotune_us": [round(x, 2) for x in info["variant_us"]],
         }
         if form == "fp64":
             nnz = info["nnz"]

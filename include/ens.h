@@ -57,6 +57,12 @@ extern "C" {
  *                  velocity is binary32.                                              */
 typedef enum { ENS_FP64 = 0, ENS_FP32_FORCE = 1, ENS_KAHAN32 = 2 } ens_precision;
 
+/* ---- creation flags (ens_params.flags) -------------------------------------------
+ * ENS_FLAG_NO_AUTOTUNE : keep the default launch shape instead of timing candidates.
+ * ENS_FLAG_UNSTAGED    : use the kernel without shared-memory staging.              */
+#define ENS_FLAG_NO_AUTOTUNE 1
+#define ENS_FLAG_UNSTAGED 2
+
 /* ---- displacement layouts for the getters ---------------------------------------- */
 #define ENS_LAYOUT_SNC 0 /* out[s][node][dof]  */
 #define ENS_LAYOUT_NCS 1 /* out[node][dof][s]  */
@@ -85,7 +91,9 @@ typedef struct {
  *          of M^-1 K_s (a lower bound of the top eigenvalue, so such a dt certainly
  *          diverges). omega_upper (element eigenvalue bound) is reported by ens_info:
  *          dt <= 2 / omega_upper is guaranteed stable.
- * precision : an ens_precision value. flags : must be 0.                            */
+ * precision : an ens_precision value. flags : ENS_FLAG_* bits (0 = default: the
+ *          launch shape of the step kernel is chosen by timing a few candidate shapes
+ *          on the context's own data at rest during ens_create).                      */
 typedef struct {
     double rho;
     double nu;
@@ -117,6 +125,9 @@ typedef struct {
     double omega_upper;     /* upper bound of the top angular frequency         */
     double bytes_per_step;  /* algorithmic HBM bytes of one step                */
     double device_bytes;    /* device memory held by the context                */
+    int32_t kernel_variant; /* launch shape in use: 0 unstaged, 1 staged 256x4,
+                               2 staged 256x3, 3 staged 128x6 (threads x blocks/SM) */
+    float variant_us[4];    /* autotuner's time per step of each shape (-1: n/a) */
 } ens_info_t;
 
 /* Create a context: copies the mesh, builds the node-to-element incidence lists,

@@ -105,7 +105,8 @@ class ens_info_t(ctypes.Structure):
                 ("n_steps_table", ctypes.c_int64), ("step", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("dt", ctypes.c_double), ("omega_lower", ctypes.c_double),
                 ("omega_upper", ctypes.c_double), ("bytes_per_step", ctypes.c_double),
-                ("device_bytes", ctypes.c_double)]
+                ("device_bytes", ctypes.c_double), ("kernel_variant", ctypes.c_int32),
+                ("variant_us", ctypes.c_float * 4)]
 
 
 _lib = None

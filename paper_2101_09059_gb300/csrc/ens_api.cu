@@ -42,6 +42,11 @@ struct ens_ctx {
     double *stat_mean = nullptr, *stat_var = nullptr;
     double *export_buf = nullptr;
     int *h_flags = nullptr;  // pinned
+    StagePlan plan{};     // launch shape of the step kernel
+    StagePlan plan_fo{};  // launch shape of force-only evaluations
+    int32_t variant = 0;
+    float variant_us[4] = {0, 0, 0, 0};
+    int32_t flags_in = 0;
 };
 
 namespace {
@@ -189,7 +194,7 @@ int run_steps(ens_ctx *c, int64_t n) {
             a.k_off = (int32_t)k;
             a.c1 = c1;
             a.c2 = c2;
-            e = launch_step<double>(c->form, a, false, c->stream);
+            e = launch_step<double>(c->form, a, false, c->stream, &c->plan);
         } else {
             StepArgs<float> a = make_args<float>(c);
             a.ug_cur = (const float *)c->ug[c->cur];
@@ -197,12 +202,63 @@ int run_steps(ens_ctx *c, int64_t n) {
             a.k_off = (int32_t)k;
             a.c1 = c1;
             a.c2 = c2;
-            e = launch_step<float>(c->form, a, false, c->stream);
+            e = launch_step<float>(c->form, a, false, c->stream, &c->plan);
         }
         if (e != cudaSuccess) return fail(c, ENS_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
         c->cur ^= 1;
     }
     return ENS_OK;
+}
+
+// Launch-shape autotuner: time a few steps of every candidate shape on this context's
+// own data (state at rest, no traction, so every value stays exactly zero) and keep the
+// fastest. Candidate 0 is the unstaged kernel.
+int autotune(ens_ctx *c, const StagePlan *cand, int n) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = 0.0f;
+    const StagePlan keep = c->plan;
+    const int saved_started = c->started;
+    c->started = true;
+    int rc = ENS_OK;
+    for (int k = 0; k < n && rc == ENS_OK; k++) {
+        if (k > 0 && !cand[k].staged) {
+            c->variant_us[k] = -1.0f;
+            continue;
+        }
+        c->plan = cand[k];
+        rc = run_steps(c, 2);
+        if (rc != ENS_OK) break;
+        cudaEventRecord(e0, c->stream);
+        rc = run_steps(c, 6);
+        if (rc != ENS_OK) break;
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(c, ENS_ERR_CUDA, "autotune timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->variant_us[k] = 1000.0f * ms / 6.0f;
+        if (best < 0 || ms < best_ms) {
+            best = k;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->started = saved_started;
+    c->plan = (rc == ENS_OK && best >= 0) ? cand[best] : keep;
+    c->variant = best < 0 ? 1 : best;
+    if (rc == ENS_OK) {
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->h_flags[0] & 2) return fail(c, ENS_ERR_TIMEOUT, "autotune: bounded wait gave up");
+    }
+    return rc;
 }
 
 const void *state_main(const ens_ctx *c) {
@@ -237,7 +293,8 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
     if (!(p->rho > 0.0) || !(p->nu >= 0.0 && p->nu < 1.0) || !(p->kshear > 0.0) ||
         !(p->alpha >= 0.0) || !(p->dt > 0.0) || !std::isfinite(p->rho) ||
         !std::isfinite(p->kshear) || !std::isfinite(p->alpha) || !std::isfinite(p->dt) ||
-        p->precision < 0 || p->precision > 2 || p->flags != 0)
+        p->precision < 0 || p->precision > 2 ||
+        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED)) != 0)
         return ENS_ERR_INVALID_ARG;
     if (alloc && (!alloc->alloc || !alloc->release)) return ENS_ERR_INVALID_ARG;
     if (!finite_all(mesh->xyz, 3 * (size_t)N)) return ENS_ERR_INVALID_ARG;
@@ -258,6 +315,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
     c->alpha = p->alpha;
     c->dt = p->dt;
     c->stream = (cudaStream_t)stream;
+    c->flags_in = p->flags;
     if (alloc) {
         c->al = *alloc;
         c->custom_alloc = true;
@@ -355,6 +413,14 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                                   c->rho, w2lo, w2hi, c->stream));
         const size_t es = elem_size(c->form);
         const int to_f = c->form != kFP64;
+        const int32_t kcs = to_f ? 20 : 18;
+        c->plan = make_stage_plan(rowptr.data(), N, c->Sp, c->Q, es, kcs, 256, 4);
+        c->plan_fo = c->plan;
+        if (c->flags_in & ENS_FLAG_UNSTAGED) c->plan = c->plan_fo = StagePlan{};
+        c->variant = c->plan.staged ? 1 : 0;
+        StagePlan cand[4] = {StagePlan{}, c->plan,
+                             make_stage_plan(rowptr.data(), N, c->Sp, c->Q, es, kcs, 256, 3),
+                             make_stage_plan(rowptr.data(), N, c->Sp, c->Q, es, kcs, 128, 6)};
         c->kc = dev_alloc(c, es * (size_t)c->nnz * (to_f ? 20 : 18));
         c->minv = dev_alloc(c, es * (size_t)NSp);
         if (!c->kc || !c->minv) return fail(c, ENS_ERR_ALLOC, "coefficient buffers");
@@ -420,6 +486,12 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         if (!c->ug[0] || !c->ug[1]) return fail(c, ENS_ERR_ALLOC, "state buffers");
         ALLOC(c->stat_mean, double, 3 * (int64_t)N);
         ALLOC(c->stat_var, double, 3 * (int64_t)N);
+        int rc0 = ens_reset(c);
+        if (rc0 != ENS_OK) return rc0;
+        if (!(c->flags_in & (ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED)) && c->plan.staged) {
+            rc0 = autotune(c, cand, 4);
+            if (rc0 != ENS_OK) return rc0;
+        }
         return ens_reset(c);
     }();
     if (rc != ENS_OK) {
@@ -537,7 +609,9 @@ int ens_step(ens_ctx *c, int64_t n) {
     CK(cudaStreamSynchronize(c->stream));
     c->step += n;
     c->started = true;
-    if (c->h_flags[0])
+    if (c->h_flags[0] & 2)
+        return fail(c, ENS_ERR_TIMEOUT, "a staged step gave up waiting for its bulk copies");
+    if (c->h_flags[0] & 1)
         return fail(c, ENS_ERR_NONFINITE, "displacement became Inf/NaN before step %lld",
                     (long long)c->step);
     return ENS_OK;
@@ -606,12 +680,12 @@ int ens_internal_force(ens_ctx *c, const double *u, double *f) {
                 StepArgs<double> a = make_args<double>(c);
                 a.ug_cur = (const double *)ug;
                 a.force_out = f_d;
-                e = launch_step<double>(c->form, a, true, c->stream);
+                e = launch_step<double>(c->form, a, true, c->stream, &c->plan_fo);
             } else {
                 StepArgs<float> a = make_args<float>(c);
                 a.ug_cur = (const float *)ug;
                 a.force_out = f_d;
-                e = launch_step<float>(c->form, a, true, c->stream);
+                e = launch_step<float>(c->form, a, true, c->stream, &c->plan_fo);
             }
         }
         std::vector<double> fp;
@@ -791,6 +865,8 @@ int ens_info(const ens_ctx *c, ens_info_t *info) {
     r.omega_upper = c->w_hi;
     r.bytes_per_step = bytes_per_step(c);
     r.device_bytes = (double)c->held_bytes;
+    r.kernel_variant = c->variant;
+    for (int k = 0; k < 4; k++) r.variant_us[k] = c->variant_us[k];
     *info = r;
     return ENS_OK;
 }

@@ -64,12 +64,31 @@ struct StepArgs {
     int32_t J;
     double c1, c2, dt;  // v_new = c1 v + c2 a ; u_new = u + dt v_new
     double *force_out;  // force-only mode: [N][3][Sp] binary64
-    int *flags;         // [0] = non-finite seen
+    int *flags;         // [0] bit 0: non-finite seen, bit 1: a bounded wait gave up
 };
+
+// Launch plan of the staged step kernel: each block owns `nb` consecutive nodes and
+// bulk-copies their incidence entries, coupling blocks and own displacement rows into
+// shared memory (cnt_max = most incidences of any block). staged = 0 selects the
+// unstaged kernel (samples-per-node not a power of two, or the plan exceeds smem).
+struct StagePlan {
+    int32_t staged;
+    int32_t block;   // threads per block (256 or 128)
+    int32_t nb;      // nodes per block
+    int32_t cnt_max;
+    uint32_t smem;
+    int32_t minb;    // resident blocks per SM the register budget targets (256-thread shape)
+};
+
+// Polls of a bounded mbarrier wait before the kernel reports a timeout.
+constexpr uint32_t kWaitLimit = 1u << 22;
 
 // Launchers (ens_step.cu).
 template <typename R>
-cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s);
+cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s,
+                        const StagePlan *plan = nullptr);
+StagePlan make_stage_plan(const int32_t *rowptr_host, int32_t N, int32_t Sp, int32_t Q,
+                          size_t elem_bytes, int32_t kc_stride, int32_t block, int32_t minb);
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s);
 cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s);

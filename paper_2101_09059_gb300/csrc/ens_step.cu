@@ -18,6 +18,7 @@
 //      writing u_{n+1} to the other ping-pong buffer.
 // There are no atomics in the force path: every node sums its own incidences in list
 // order, so results are bitwise reproducible.
+#include "ens_bits.cuh"
 #include "ens_internal.cuh"
 
 namespace ens {
@@ -132,6 +133,121 @@ __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__res
     }
 }
 
+// Traction of node i at step n: sum_j amp[n][j] P_j[i] (sample-independent).
+template <typename R>
+__device__ __forceinline__ void node_traction(const StepArgs<R> &a, int32_t i, int64_t n,
+                                              R (&fe)[3]) {
+    fe[0] = fe[1] = fe[2] = R(0);
+    for (int32_t j = 0; j < a.J; j++) {
+        const R am = __ldg(a.amp + n * a.J + j);
+        const R *P = a.modes + ((int64_t)j * a.fv.N + i) * 3;
+#pragma unroll
+        for (int d = 0; d < 3; d++) fe[d] = fma(am, __ldg(P + d), fe[d]);
+    }
+}
+
+// The fused update of node i, samples [s0, s0 + V): a = (f_ext - f_int) / m, then the
+// velocity form of Eq. (dynamicsCD) with the fixed-dof mask, stored per form.
+template <int FORM, typename R>
+__device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int32_t s0,
+                                            const R (&ui)[3][Vw<R>::V], const R (&f)[3][Vw<R>::V]) {
+    constexpr int V = Vw<R>::V;
+    const int64_t Sp = a.fv.Sp;
+    const int64_t n = *a.step_ctr + a.k_off;
+    R fe[3];
+    node_traction<R>(a, i, n, fe);
+    R mi[V];
+    ld_nc(a.minv + (int64_t)i * Sp + s0, mi);
+    const unsigned fx = __ldg(a.fix + i);
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const bool held = (fx >> d) & 1u;
+        const int64_t row = ((int64_t)i * 3 + d) * Sp + s0;
+        if constexpr (FORM == kFP64) {
+            double vv[V], un[V];
+            ld_cs(a.v64 + row, vv);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const double acc = (fe[d] - f[d][v]) * mi[v];
+                const double vn = held ? 0.0 : fma(a.c1, vv[v], a.c2 * acc);
+                un[v] = held ? 0.0 : fma(a.dt, vn, ui[d][v]);
+                vv[v] = vn;
+                bad |= !isfinite(un[v]);
+            }
+            st_cs(a.v64 + row, vv);
+            st_wb(a.ug_next + row, un);
+        } else if constexpr (FORM == kFP32Force) {
+            double uu[4], vv[4], h2[2];
+            ld_cs(a.u64 + row, h2);
+            uu[0] = h2[0];
+            uu[1] = h2[1];
+            ld_cs(a.u64 + row + 2, h2);
+            uu[2] = h2[0];
+            uu[3] = h2[1];
+            ld_cs(a.v64 + row, h2);
+            vv[0] = h2[0];
+            vv[1] = h2[1];
+            ld_cs(a.v64 + row + 2, h2);
+            vv[2] = h2[0];
+            vv[3] = h2[1];
+            float ug[4];
+            const float c2 = (float)a.c2;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const float acc = (fe[d] - f[d][v]) * mi[v];
+                // binary64 state update; the conversions run on the integer pipe
+                const double vn = held ? 0.0 : fma(a.c1, vv[v], f32_to_f64(c2 * acc));
+                const double un = held ? 0.0 : fma(a.dt, vn, uu[v]);
+                vv[v] = vn;
+                uu[v] = un;
+                ug[v] = f64_to_f32_rz(un);
+                bad |= !isfinite(ug[v]);
+            }
+            st_cs(a.u64 + row, {uu[0], uu[1]});
+            st_cs(a.u64 + row + 2, {uu[2], uu[3]});
+            st_cs(a.v64 + row, {vv[0], vv[1]});
+            st_cs(a.v64 + row + 2, {vv[2], vv[3]});
+            st_wb(a.ug_next + row, ug);
+        } else {  // kKahan32
+            float lo[4], vv[4], hi[4];
+            ld_cs(a.ulo + row, lo);
+            ld_cs(a.v32 + row, vv);
+            const float c1 = (float)a.c1, c2 = (float)a.c2, dt = (float)a.dt;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const float acc = (fe[d] - f[d][v]) * mi[v];
+                const float vn = held ? 0.0f : fmaf(c1, vv[v], c2 * acc);
+                // (hi, lo) += dt * vn as an error-free sum of hi and the small part.
+                const float y = fmaf(dt, vn, lo[v]);
+                const float s = ui[d][v] + y;
+                const float bb = s - ui[d][v];
+                const float err = (ui[d][v] - (s - bb)) + (y - bb);
+                hi[v] = held ? 0.0f : s;
+                lo[v] = held ? 0.0f : err;
+                vv[v] = vn;
+                bad |= !isfinite(s);
+            }
+            st_cs(a.ulo + row, lo);
+            st_cs(a.v32 + row, vv);
+            st_wb(a.ug_next + row, hi);
+        }
+    }
+    if (bad) atomicOr(a.flags, 1);
+}
+
+template <typename R>
+__device__ __forceinline__ void store_force(const StepArgs<R> &a, int32_t i, int32_t s0,
+                                            const R (&f)[3][Vw<R>::V]) {
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int v = 0; v < Vw<R>::V; v++)
+            a.force_out[((int64_t)i * 3 + d) * a.fv.Sp + s0 + v] = (double)f[d][v];
+}
+
+// Unstaged kernel: everything through the cache hierarchy (used when the staged plan
+// does not apply).
 template <int FORM, typename R, bool FORCE_ONLY>
 __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
     constexpr int V = Vw<R>::V;
@@ -141,111 +257,200 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
     if (g >= (int64_t)a.fv.N * Q) return;
     const int32_t i = (int32_t)(g / Q);
     const int32_t s0 = (int32_t)(g - (int64_t)i * Q) * V;
-
     R ui[3][V];
 #pragma unroll
     for (int d = 0; d < 3; d++) ld_nc(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
     R f[3][V];
     node_force<R>(a.fv, a.ug_cur, i, s0, ui, f);
+    if constexpr (FORCE_ONLY)
+        store_force<R>(a, i, s0, f);
+    else
+        node_update<FORM, R>(a, i, s0, ui, f);
+}
 
-    if constexpr (FORCE_ONLY) {
-#pragma unroll
-        for (int d = 0; d < 3; d++)
-#pragma unroll
-            for (int v = 0; v < V; v++)
-                a.force_out[((int64_t)i * 3 + d) * Sp + s0 + v] = (double)f[d][v];
-        return;
-    } else {
-        const int64_t n = *a.step_ctr + a.k_off;
-        R fe[3] = {R(0), R(0), R(0)};
-        for (int32_t j = 0; j < a.J; j++) {
-            const R am = __ldg(a.amp + n * a.J + j);
-            const R *P = a.modes + ((int64_t)j * a.fv.N + i) * 3;
-#pragma unroll
-            for (int d = 0; d < 3; d++) fe[d] = fma(am, __ldg(P + d), fe[d]);
-        }
-        R mi[V];
-        ld_nc(a.minv + (int64_t)i * Sp + s0, mi);
-        const unsigned fx = __ldg(a.fix + i);
-        bool bad = false;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const bool held = (fx >> d) & 1u;
-            const int64_t row = ((int64_t)i * 3 + d) * Sp + s0;
-            if constexpr (FORM == kFP64) {
-                double vv[V], un[V];
-                ld_cs(a.v64 + row, vv);
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    const double acc = (fe[d] - f[d][v]) * mi[v];
-                    const double vn = held ? 0.0 : fma(a.c1, vv[v], a.c2 * acc);
-                    un[v] = held ? 0.0 : fma(a.dt, vn, ui[d][v]);
-                    vv[v] = vn;
-                    bad |= !isfinite(un[v]);
-                }
-                st_cs(a.v64 + row, vv);
-                st_wb(a.ug_next + row, un);
+// Staged kernel. Block b owns nodes [b nb, b nb + nb). One thread issues bulk copies
+// (TMA, non-tensor) of the block's incidence entries, coupling blocks and own gathered
+// displacement rows into shared memory, completing on one mbarrier, and asks L2 for the
+// block's remaining state rows, which are only read after the force loop. Every thread
+// then needs a single global round trip per incidence (the two other corners' rows and
+// (E h)), with its own rows, the entry and the 18 coefficients coming from shared memory.
+template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs<R> a,
+                                                                  const int32_t nb_block,
+                                                                  const int32_t cnt_max) {
+    constexpr int V = Vw<R>::V;
+    constexpr int KS = Kc<R>::stride;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int4 *ent_s = reinterpret_cast<int4 *>(smem + 16);
+    R *kc_s = reinterpret_cast<R *>(ent_s + cnt_max);
+    R *ug_s = kc_s + (size_t)cnt_max * KS;
+
+    const int32_t Q = a.fv.Q;
+    const int64_t Sp = a.fv.Sp;
+    const int32_t N = a.fv.N;
+    const int32_t n0 = blockIdx.x * nb_block;
+    const int32_t nb = min(nb_block, N - n0);
+    const int32_t pb = __ldg(a.fv.rowptr + n0);
+    const int32_t cnt = __ldg(a.fv.rowptr + n0 + nb) - pb;
+    const int32_t li = threadIdx.x / Q;
+    const int32_t s0 = (threadIdx.x - li * Q) * V;
+    const bool valid = li < nb;
+    const int32_t i = n0 + li;
+    int32_t p0 = 0, p1 = 0;
+    if (valid) {
+        p0 = __ldg(a.fv.rowptr + i) - pb;
+        p1 = __ldg(a.fv.rowptr + i + 1) - pb;
+    }
+    const uint32_t row_bytes = (uint32_t)(nb * 3 * Sp * sizeof(R));
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+        const uint32_t b_ent = (uint32_t)cnt * 16u;
+        const uint32_t b_kc = (uint32_t)cnt * KS * (uint32_t)sizeof(R);
+        mbar_expect_tx(bar, b_ent + b_kc + row_bytes);
+        bulk_g2s(ent_s, a.fv.ent + pb, b_ent, bar);
+        bulk_g2s(kc_s, a.fv.kc + (size_t)pb * KS, b_kc, bar);
+        bulk_g2s(ug_s, a.ug_cur + (size_t)n0 * 3 * Sp, row_bytes, bar);
+        if constexpr (!FORCE_ONLY) {
+            const size_t r0 = (size_t)n0 * 3 * Sp;
+            bulk_prefetch_l2(a.minv + (size_t)n0 * Sp, (uint32_t)(nb * Sp * sizeof(R)));
+            if constexpr (FORM == kKahan32) {
+                bulk_prefetch_l2(a.ulo + r0, (uint32_t)(nb * 3 * Sp * 4));
+                bulk_prefetch_l2(a.v32 + r0, (uint32_t)(nb * 3 * Sp * 4));
             } else if constexpr (FORM == kFP32Force) {
-                double uu[4], vv[4];
-                double h2[2];
-                ld_cs(a.u64 + row, h2);
-                uu[0] = h2[0];
-                uu[1] = h2[1];
-                ld_cs(a.u64 + row + 2, h2);
-                uu[2] = h2[0];
-                uu[3] = h2[1];
-                ld_cs(a.v64 + row, h2);
-                vv[0] = h2[0];
-                vv[1] = h2[1];
-                ld_cs(a.v64 + row + 2, h2);
-                vv[2] = h2[0];
-                vv[3] = h2[1];
-                float ug[4];
-                const float c2 = (float)a.c2;
-#pragma unroll
-                for (int v = 0; v < 4; v++) {
-                    const float acc = (fe[d] - f[d][v]) * mi[v];
-                    const double vn = held ? 0.0 : fma(a.c1, vv[v], (double)(c2 * acc));
-                    const double un = held ? 0.0 : fma(a.dt, vn, uu[v]);
-                    vv[v] = vn;
-                    uu[v] = un;
-                    ug[v] = (float)un;
-                    bad |= !isfinite(ug[v]);
-                }
-                st_cs(a.u64 + row, {uu[0], uu[1]});
-                st_cs(a.u64 + row + 2, {uu[2], uu[3]});
-                st_cs(a.v64 + row, {vv[0], vv[1]});
-                st_cs(a.v64 + row + 2, {vv[2], vv[3]});
-                st_wb(a.ug_next + row, ug);
-            } else {  // kKahan32
-                float lo[4], vv[4], hi[4];
-                ld_cs(a.ulo + row, lo);
-                ld_cs(a.v32 + row, vv);
-                const float c1 = (float)a.c1, c2 = (float)a.c2, dt = (float)a.dt;
-#pragma unroll
-                for (int v = 0; v < 4; v++) {
-                    const float acc = (fe[d] - f[d][v]) * mi[v];
-                    const float vn = held ? 0.0f : fmaf(c1, vv[v], c2 * acc);
-                    // (hi, lo) += dt * vn as an error-free sum of hi and the small part.
-                    const float y = fmaf(dt, vn, lo[v]);
-                    const float s = ui[d][v] + y;
-                    const float bb = s - ui[d][v];
-                    const float err = (ui[d][v] - (s - bb)) + (y - bb);
-                    hi[v] = held ? 0.0f : s;
-                    lo[v] = held ? 0.0f : err;
-                    vv[v] = vn;
-                    bad |= !isfinite(s);
-                }
-                st_cs(a.ulo + row, lo);
-                st_cs(a.v32 + row, vv);
-                st_wb(a.ug_next + row, hi);
+                bulk_prefetch_l2(a.u64 + r0, (uint32_t)(nb * 3 * Sp * 8));
+                bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
+            } else {
+                bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
             }
         }
-        if (bad) atomicOr(a.flags, 1);
     }
+    __syncthreads();
+    if (!mbar_wait(bar, 0, kWaitLimit)) {
+        // Report, then give the copies in flight one more bounded wait before leaving.
+        if (threadIdx.x == 0) atomicOr(a.flags, 2);
+        mbar_wait(bar, 0, kWaitLimit);
+        return;
+    }
+    if (!valid) return;
+
+    R ui[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const R *src = ug_s + ((size_t)li * 3 + d) * Sp + s0;
+#pragma unroll
+        for (int v = 0; v < V; v++) ui[d][v] = src[v];
+    }
+    R f[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int v = 0; v < V; v++) f[d][v] = R(0);
+    const R *__restrict__ ug = a.ug_cur;
+    for (int32_t p = p0; p < p1; ++p) {
+        const int4 en = ent_s[p];
+        R ua[3][V], ub[3][V], e[V];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            ld_nc(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
+            ld_nc(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
+        }
+        ld_nc(a.fv.eh + (int64_t)en.x * Sp + s0, e);
+        const R *k = kc_s + (size_t)p * KS;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const R a0 = ua[0][v] - ui[0][v], a1 = ua[1][v] - ui[1][v], a2 = ua[2][v] - ui[2][v];
+            const R b0 = ub[0][v] - ui[0][v], b1 = ub[1][v] - ui[1][v], b2 = ub[2][v] - ui[2][v];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                R t = k[3 * d] * a0;
+                t = fma(k[3 * d + 1], a1, t);
+                t = fma(k[3 * d + 2], a2, t);
+                t = fma(k[9 + 3 * d], b0, t);
+                t = fma(k[9 + 3 * d + 1], b1, t);
+                t = fma(k[9 + 3 * d + 2], b2, t);
+                f[d][v] = fma(e[v], t, f[d][v]);
+            }
+        }
+    }
+    if constexpr (FORCE_ONLY)
+        store_force<R>(a, i, s0, f);
+    else
+        node_update<FORM, R>(a, i, s0, ui, f);
 }
 
 __global__ void advance_kernel(int64_t *ctr, int64_t n) { *ctr += n; }
+
+// Ensemble mean and sample variance per dof: 8 lanes per (node, dof) row, each lane
+// holding up to 16 of the row's samples in registers between the two passes (exact
+// two-pass formula; the shuffle tree fixes the reduction order). For wider ensembles
+// the second pass re-reads the row from cache. The binary32 pair of the compensated
+// form is widened on the integer pipe. inv_s = 1 / S, inv_s1 = 1 / (S - 1) (0 if S = 1).
+constexpr int kStatLanes = 8;
+constexpr int kStatRegs = 16;
+
+template <int FORM>
+__device__ __forceinline__ double state_value_fast(const void *u_main, const float *ulo,
+                                                   int64_t idx) {
+    if constexpr (FORM == kKahan32)
+        return f32_to_f64(((const float *)u_main)[idx]) + f32_to_f64(ulo[idx]);
+    else
+        return ((const double *)u_main)[idx];
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256) stats_kernel(const void *__restrict__ u_main,
+                                                    const float *__restrict__ ulo, int32_t N,
+                                                    int32_t S, int32_t Sp, double inv_s,
+                                                    double inv_s1, double *__restrict__ mean,
+                                                    double *__restrict__ var) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = t / kStatLanes;
+    const int g = (int)(t % kStatLanes);
+    const bool live = row < (int64_t)N * 3;
+    const int64_t base = live ? row * Sp : 0;
+    const bool in_regs = S <= kStatLanes * kStatRegs;
+    double x[kStatRegs];
+    double s = 0.0;
+    if (live) {
+        if (in_regs) {
+#pragma unroll
+            for (int k = 0; k < kStatRegs; k++) {
+                const int32_t j = g + k * kStatLanes;
+                x[k] = j < S ? state_value_fast<FORM>(u_main, ulo, base + j) : 0.0;
+                s += x[k];
+            }
+        } else {
+            for (int32_t j = g; j < S; j += kStatLanes) s += state_value_fast<FORM>(u_main, ulo, base + j);
+        }
+    }
+#pragma unroll
+    for (int o = kStatLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double mu = s * inv_s;
+    double q = 0.0;
+    if (live) {
+        if (in_regs) {
+#pragma unroll
+            for (int k = 0; k < kStatRegs; k++) {
+                const int32_t j = g + k * kStatLanes;
+                const double d = x[k] - mu;
+                q = j < S ? fma(d, d, q) : q;
+            }
+        } else {
+            for (int32_t j = g; j < S; j += kStatLanes) {
+                const double d = state_value_fast<FORM>(u_main, ulo, base + j) - mu;
+                q = fma(d, d, q);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = kStatLanes / 2; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (live && g == 0) {
+        mean[row] = mu;
+        var[row] = q * inv_s1;
+    }
+}
 
 // Value of sample s of state row `row` as binary64, for any form.
 template <int FORM>
@@ -254,34 +459,6 @@ __device__ __forceinline__ double state_value(const void *u_main, const float *u
         return (double)((const float *)u_main)[idx] + (double)ulo[idx];
     else
         return ((const double *)u_main)[idx];
-}
-
-// Ensemble mean and sample variance per dof: one warp per (node, dof) row, two passes
-// (the second re-reads the row from cache), fixed reduction order.
-template <int FORM>
-__global__ void stats_kernel(const void *__restrict__ u_main, const float *__restrict__ ulo,
-                             int32_t N, int32_t S, int32_t Sp, double *__restrict__ mean,
-                             double *__restrict__ var) {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= (int64_t)N * 3) return;
-    const int64_t base = row * Sp;
-    double s = 0.0;
-    for (int32_t k = lane; k < S; k += 32) s += state_value<FORM>(u_main, ulo, base + k);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const double mu = s / (double)S;
-    double q = 0.0;
-    for (int32_t k = lane; k < S; k += 32) {
-        const double x = state_value<FORM>(u_main, ulo, base + k) - mu;
-        q = fma(x, x, q);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    if (lane == 0) {
-        mean[row] = mu;
-        var[row] = S > 1 ? q / (double)(S - 1) : 0.0;
-    }
 }
 
 template <int FORM>
@@ -323,31 +500,76 @@ __global__ void import_kernel(const double *__restrict__ in, int32_t N, int32_t 
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-}  // namespace
-
-template <typename R>
-cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s) {
-    const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
-    if (threads == 0) return cudaSuccess;
-    const unsigned grid = blocks_for(threads, kBlock);
-    if constexpr (sizeof(R) == 8) {
-        if (force_only)
-            step_kernel<kFP64, double, true><<<grid, kBlock, 0, s>>>(a);
-        else
-            step_kernel<kFP64, double, false><<<grid, kBlock, 0, s>>>(a);
-    } else {
-        if (force_only)
-            step_kernel<kKahan32, float, true><<<grid, kBlock, 0, s>>>(a);
-        else if (form == kFP32Force)
-            step_kernel<kFP32Force, float, false><<<grid, kBlock, 0, s>>>(a);
-        else
-            step_kernel<kKahan32, float, false><<<grid, kBlock, 0, s>>>(a);
+template <int FORM, typename R, bool FO, int BLOCK, int MINB>
+cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
+    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB>;
+    if (plan->smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)plan->smem);
+        if (e != cudaSuccess) return e;
     }
+    const unsigned grid = (unsigned)((a.fv.N + plan->nb - 1) / plan->nb);
+    k<<<grid, BLOCK, plan->smem, s>>>(a, plan->nb, plan->cnt_max);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step<double>(int, const StepArgs<double> &, bool, cudaStream_t);
-template cudaError_t launch_step<float>(int, const StepArgs<float> &, bool, cudaStream_t);
+template <int FORM, typename R, bool FO>
+cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
+    const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
+    if (plan && plan->staged) {
+        if constexpr (FO) {
+            // force-only evaluations have one staged shape; other plans run unstaged
+            if (plan->block == 256 && plan->minb == 4) return launch_staged<FORM, R, FO, 256, 4>(a, s, plan);
+        } else {
+            if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 6>(a, s, plan);
+            if (plan->minb == 3) return launch_staged<FORM, R, FO, 256, 3>(a, s, plan);
+            return launch_staged<FORM, R, FO, 256, 4>(a, s, plan);
+        }
+    }
+    step_kernel<FORM, R, FO><<<blocks_for(threads, kBlock), kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s,
+                        const StagePlan *plan) {
+    if ((int64_t)a.fv.N * a.fv.Q == 0) return cudaSuccess;
+    if constexpr (sizeof(R) == 8) {
+        return force_only ? launch_one<kFP64, double, true>(a, s, plan)
+                          : launch_one<kFP64, double, false>(a, s, plan);
+    } else {
+        if (force_only) return launch_one<kKahan32, float, true>(a, s, plan);
+        if (form == kFP32Force) return launch_one<kFP32Force, float, false>(a, s, plan);
+        return launch_one<kKahan32, float, false>(a, s, plan);
+    }
+}
+
+template cudaError_t launch_step<double>(int, const StepArgs<double> &, bool, cudaStream_t,
+                                         const StagePlan *);
+template cudaError_t launch_step<float>(int, const StepArgs<float> &, bool, cudaStream_t,
+                                        const StagePlan *);
+
+StagePlan make_stage_plan(const int32_t *rowptr, int32_t N, int32_t Sp, int32_t Q,
+                          size_t es, int32_t kc_stride, int32_t block, int32_t minb) {
+    StagePlan p{0, block, 0, 0, 0, minb};
+    if (Q <= 0 || Q > block || (block % Q) != 0) return p;
+    const int32_t nb = block / Q;
+    int32_t cmax = 0;
+    for (int64_t n0 = 0; n0 < N; n0 += nb) {
+        const int64_t n1 = n0 + nb < N ? n0 + nb : N;
+        const int32_t c = rowptr[n1] - rowptr[n0];
+        cmax = c > cmax ? c : cmax;
+    }
+    const size_t bytes = 16 + (size_t)cmax * (16 + kc_stride * es) + (size_t)nb * 3 * Sp * es;
+    if (bytes > 160 * 1024) return p;
+    p.staged = 1;
+    p.nb = nb;
+    p.cnt_max = cmax;
+    p.smem = (uint32_t)((bytes + 127) / 128 * 128);
+    return p;
+}
 
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s) {
     advance_kernel<<<1, 1, 0, s>>>(step_ctr, n);
@@ -356,13 +578,14 @@ cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s) {
 
 cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s) {
-    const int64_t threads = (int64_t)N * 3 * 32;
+    const int64_t threads = (int64_t)N * 3 * kStatLanes;
     if (threads == 0) return cudaSuccess;
     const unsigned grid = blocks_for(threads, 256);
+    const double inv_s = 1.0 / (double)S, inv_s1 = S > 1 ? 1.0 / (double)(S - 1) : 0.0;
     if (form == kKahan32)
-        stats_kernel<kKahan32><<<grid, 256, 0, s>>>(u_main, ulo, N, S, Sp, mean, var);
+        stats_kernel<kKahan32><<<grid, 256, 0, s>>>(u_main, ulo, N, S, Sp, inv_s, inv_s1, mean, var);
     else
-        stats_kernel<kFP64><<<grid, 256, 0, s>>>(u_main, ulo, N, S, Sp, mean, var);
+        stats_kernel<kFP64><<<grid, 256, 0, s>>>(u_main, ulo, N, S, Sp, inv_s, inv_s1, mean, var);
     return cudaGetLastError();
 }
 

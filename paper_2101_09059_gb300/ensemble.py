@@ -13,6 +13,7 @@ import numpy as np
 from . import _lib
 
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
+FLAG_NO_AUTOTUNE, FLAG_UNSTAGED = 1, 2
 PRECISIONS = {"fp64": FP64, "fp32_force": FP32_FORCE, "kahan32": KAHAN32}
 LAYOUT_SNC, LAYOUT_NCS = 0, 1
 
@@ -76,7 +77,8 @@ class Ensemble:
     """
 
     def __init__(self, xyz, tri, fixed, E_node, h_node, *, rho, nu, kshear, alpha, dt,
-                 precision="fp64", stream=None, torch_allocator: bool = True, device: int = 0):
+                 precision="fp64", stream=None, torch_allocator: bool = True, device: int = 0,
+                 flags: int = 0):
         torch = _torch()
         self._L = _lib.load()
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
@@ -93,7 +95,7 @@ class Ensemble:
         self._allocator = _TorchAllocator(device) if torch_allocator else None
         mesh = _lib.ens_mesh(self.N, self.E, self.xyz.ctypes.data, self.tri.ctypes.data,
                              None if self.fixed is None else self.fixed.ctypes.data)
-        params = _lib.ens_params(rho, nu, kshear, alpha, dt, int(self.precision), 0)
+        params = _lib.ens_params(rho, nu, kshear, alpha, dt, int(self.precision), int(flags))
         out = ctypes.c_void_p()
         alloc_p = ctypes.byref(self._allocator.struct) if self._allocator else None
         with torch.cuda.device(device):
@@ -210,4 +212,6 @@ class Ensemble:
     def info(self) -> dict:
         i = _lib.ens_info_t()
         self._call("ens_info", ctypes.byref(i))
-        return {name: getattr(i, name) for name, _ in i._fields_}
+        out = {name: getattr(i, name) for name, _ in i._fields_}
+        out["variant_us"] = list(out["variant_us"])
+        return out

@@ -88,13 +88,14 @@ def test_internal_force_matches_oracle(name, S, precision):
     e.close()
 
 
+@pytest.mark.parametrize("flags", [0, ens.ensemble.FLAG_UNSTAGED])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
 @pytest.mark.parametrize("name,S", SMALL)
-def test_trajectory_small_meshes(name, S, precision):
+def test_trajectory_small_meshes(name, S, precision, flags):
     case = synth.make_case(name, S=S)
     n = case["n_steps"]
     ref = _oracle_run(case, n)
-    e = ens.Ensemble.from_case(case, precision=precision)
+    e = ens.Ensemble.from_case(case, precision=precision, flags=flags)
     e.step(n // 2)
     e.step(n - n // 2)
     u = e.displacement("snc")
@@ -102,11 +103,12 @@ def test_trajectory_small_meshes(name, S, precision):
     e.close()
 
 
+@pytest.mark.parametrize("flags", [0, ens.ensemble.FLAG_UNSTAGED])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
-def test_tube_40x40_full_run(case_tiny, precision):
+def test_tube_40x40_full_run(case_tiny, precision, flags):
     n = case_tiny["n_steps"]
     ref = _oracle_run(case_tiny, n)
-    e = ens.Ensemble.from_case(case_tiny, precision=precision)
+    e = ens.Ensemble.from_case(case_tiny, precision=precision, flags=flags)
     for _ in range(4):
         e.step(n // 4)
     u = e.displacement("snc")
@@ -258,3 +260,33 @@ def test_streamed_amplitudes_equal_full_table():
         st.set_amplitudes(50, case["amp"][:20])
     assert ei.value.code == -7
     st.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+@pytest.mark.parametrize("S", [4, 8, 16, 64])
+def test_every_launch_shape_is_bitwise_identical(precision, S):
+    """The staged kernels (every autotuner candidate) and the unstaged kernel evaluate the
+    same operations in the same order: their trajectories must agree bit for bit."""
+    case = synth.make_case("tube_small", S=S, n_steps=80)
+    runs = {}
+    for flags in (ens.ensemble.FLAG_UNSTAGED, ens.ensemble.FLAG_NO_AUTOTUNE, 0):
+        e = ens.Ensemble.from_case(case, precision=precision, flags=flags)
+        info = e.info()
+        e.step(80)
+        runs[flags] = (e.displacement(), info)
+        e.close()
+    base = runs[ens.ensemble.FLAG_UNSTAGED][0]
+    assert runs[ens.ensemble.FLAG_UNSTAGED][1]["kernel_variant"] == 0
+    assert runs[ens.ensemble.FLAG_NO_AUTOTUNE][1]["kernel_variant"] == 1
+    for flags, (u, info) in runs.items():
+        assert np.array_equal(u, base), (flags, info["kernel_variant"])
+    # the tuned context timed every candidate shape that applies
+    tuned = runs[0][1]["variant_us"]
+    assert tuned[0] > 0 and tuned[1] > 0
+
+
+def test_ragged_width_uses_unstaged_kernel():
+    case = synth.make_case("tube_small", S=33, n_steps=4)
+    e = ens.Ensemble.from_case(case, precision="kahan32")
+    assert e.info()["kernel_variant"] == 0
+    e.close()
