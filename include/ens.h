@@ -126,8 +126,10 @@ typedef struct {
     double bytes_per_step;  /* algorithmic HBM bytes of one step                */
     double device_bytes;    /* device memory held by the context                */
     int32_t kernel_variant; /* launch shape in use: 0 unstaged, 1 staged 256x4,
-                               2 staged 256x3, 3 staged 128x6 (threads x blocks/SM) */
-    float variant_us[4];    /* autotuner's time per step of each shape (-1: n/a) */
+                               2 staged 256x3, 3 staged 128x6, 4 staged 64x12
+                               (threads per block x blocks per SM)                */
+    float variant_us[6];    /* autotuner's time per step of each shape (-1: n/a,
+                               0: not timed)                                      */
 } ens_info_t;
 
 /* Create a context: copies the mesh, builds the node-to-element incidence lists,
@@ -224,8 +226,9 @@ int ens_set_state(ens_ctx *ctx, const void *buf, size_t bytes);
 /* Sizes, step index and traffic model.                                               */
 int ens_info(const ens_ctx *ctx, ens_info_t *info);
 
-/* Message of the last failing call on ctx ("" if none); ens_error_string names a
- * code. Both return static or context-owned storage.                                  */
+/* Message of the last failing call on ctx ("" if none); with ctx = NULL, the message
+ * of the calling thread's last failed ens_create. ens_error_string names a code. Both
+ * return static, thread-owned or context-owned storage.                               */
 const char *ens_last_error(const ens_ctx *ctx);
 const char *ens_error_string(int code);
 

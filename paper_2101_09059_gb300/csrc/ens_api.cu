@@ -13,6 +13,10 @@
 
 using namespace ens;
 
+namespace {
+constexpr int kVariants = 6;  // launch shapes the autotuner can time (see ens_info_t)
+}
+
 struct ens_ctx {
     int32_t N = 0, E = 0, S = 0, Sp = 0, Q = 0, form = 0, J = 0;
     int64_t nnz = 0, n_amp = 0, step = 0;
@@ -45,7 +49,7 @@ struct ens_ctx {
     StagePlan plan{};     // launch shape of the step kernel
     StagePlan plan_fo{};  // launch shape of force-only evaluations
     int32_t variant = 0;
-    float variant_us[4] = {0, 0, 0, 0};
+    float variant_us[kVariants] = {0, 0, 0, 0, 0, 0};
     int32_t flags_in = 0;
 };
 
@@ -177,6 +181,10 @@ StepArgs<R> make_args(ens_ctx *c) {
 
 int run_steps(ens_ctx *c, int64_t n) {
     const double beta = 0.5 * c->alpha * c->dt;
+    const cudaError_t stale = cudaGetLastError();
+    if (stale != cudaSuccess)
+        return fail(c, ENS_ERR_CUDA, "error pending before the step launches: %s",
+                    cudaGetErrorString(stale));
     for (int64_t k = 0; k < n; k++) {
         double c1, c2;
         if (!c->started && k == 0) {  // Taylor start: v_{1/2} = (1 - beta) v_0 + dt/2 a_0
@@ -204,9 +212,40 @@ int run_steps(ens_ctx *c, int64_t n) {
             a.c2 = c2;
             e = launch_step<float>(c->form, a, false, c->stream, &c->plan);
         }
-        if (e != cudaSuccess) return fail(c, ENS_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess)
+            return fail(c, ENS_ERR_CUDA, "step launch (variant staged=%d block=%d): %s [%s]",
+                        c->plan.staged, c->plan.block, cudaGetErrorString(e), last_launch_note());
         c->cur ^= 1;
     }
+    return ENS_OK;
+}
+
+// Staged launch plan for `block` threads per block (nodes per block, most incidences of
+// any block, shared-memory size). Returns an unstaged plan when the shape does not apply
+// (threads per node do not divide the block, or the staging does not fit).
+int make_stage_plan(ens_ctx *c, const std::vector<int32_t> &rowptr, int32_t block,
+                    int32_t minb, StagePlan *out) {
+    StagePlan p{};
+    p.block = block;
+    p.minb = minb;
+    *out = p;
+    const int32_t Q = c->Q, N = c->N, Sp = c->Sp;
+    if (Q <= 0 || Q > block || (block % Q) != 0) return ENS_OK;
+    const int32_t nb = block / Q;
+    const size_t es = elem_size(c->form);
+    const int32_t KS = c->form == kFP64 ? 18 : 20;
+    int32_t cmax = 0;
+    for (int64_t n0 = 0; n0 < N; n0 += nb) {
+        const int64_t n1 = std::min<int64_t>(N, n0 + nb);
+        cmax = std::max<int32_t>(cmax, rowptr[n1] - rowptr[n0]);
+    }
+    const size_t bytes = 16 + (size_t)cmax * (16 + KS * es) + (size_t)nb * 3 * Sp * es;
+    if (bytes > 160 * 1024) return ENS_OK;
+    p.staged = 1;
+    p.nb = nb;
+    p.cnt_max = cmax;
+    p.smem = (uint32_t)((bytes + 127) / 128 * 128);
+    *out = p;
     return ENS_OK;
 }
 
@@ -256,6 +295,7 @@ int autotune(ens_ctx *c, const StagePlan *cand, int n) {
         CK(cudaStreamSynchronize(c->stream));
         CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        if (c->h_flags[0] & 4) return fail(c, ENS_ERR_CUDA, "autotune: launch plan inconsistent");
         if (c->h_flags[0] & 2) return fail(c, ENS_ERR_TIMEOUT, "autotune: bounded wait gave up");
     }
     return rc;
@@ -272,7 +312,11 @@ extern "C" {
 
 const char *ens_error_string(int code) { return code_name(code); }
 
-const char *ens_last_error(const ens_ctx *c) { return c ? c->err.c_str() : ""; }
+namespace {
+thread_local std::string g_create_err;  // message of this thread's last failed ens_create
+}
+
+const char *ens_last_error(const ens_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 void ens_destroy(ens_ctx *c) {
     if (!c) return;
@@ -413,14 +457,20 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                                   c->rho, w2lo, w2hi, c->stream));
         const size_t es = elem_size(c->form);
         const int to_f = c->form != kFP64;
-        const int32_t kcs = to_f ? 20 : 18;
-        c->plan = make_stage_plan(rowptr.data(), N, c->Sp, c->Q, es, kcs, 256, 4);
-        c->plan_fo = c->plan;
-        if (c->flags_in & ENS_FLAG_UNSTAGED) c->plan = c->plan_fo = StagePlan{};
+        StagePlan cand[kVariants] = {};  // every slot unstaged until a plan is built
+        if (!(c->flags_in & ENS_FLAG_UNSTAGED)) {
+            int rcp = make_stage_plan(c, rowptr, 256, 4, &cand[1]);
+            if (rcp == ENS_OK && !(c->flags_in & ENS_FLAG_NO_AUTOTUNE)) {
+                cand[2] = cand[1];
+                cand[2].minb = 3;
+                rcp = make_stage_plan(c, rowptr, 128, 6, &cand[3]);
+                if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 64, 12, &cand[4]);
+            }
+            if (rcp != ENS_OK) return rcp;
+        }
+        c->plan = cand[1];
+        c->plan_fo = cand[1];
         c->variant = c->plan.staged ? 1 : 0;
-        StagePlan cand[4] = {StagePlan{}, c->plan,
-                             make_stage_plan(rowptr.data(), N, c->Sp, c->Q, es, kcs, 256, 3),
-                             make_stage_plan(rowptr.data(), N, c->Sp, c->Q, es, kcs, 128, 6)};
         c->kc = dev_alloc(c, es * (size_t)c->nnz * (to_f ? 20 : 18));
         c->minv = dev_alloc(c, es * (size_t)NSp);
         if (!c->kc || !c->minv) return fail(c, ENS_ERR_ALLOC, "coefficient buffers");
@@ -489,15 +539,17 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         int rc0 = ens_reset(c);
         if (rc0 != ENS_OK) return rc0;
         if (!(c->flags_in & (ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED)) && c->plan.staged) {
-            rc0 = autotune(c, cand, 4);
+            rc0 = autotune(c, cand, kVariants);
             if (rc0 != ENS_OK) return rc0;
         }
         return ens_reset(c);
     }();
     if (rc != ENS_OK) {
+        g_create_err = c->err;
         ens_destroy(c);
         return rc;
     }
+    g_create_err.clear();
     *out = c;
     return ENS_OK;
 }
@@ -609,6 +661,8 @@ int ens_step(ens_ctx *c, int64_t n) {
     CK(cudaStreamSynchronize(c->stream));
     c->step += n;
     c->started = true;
+    if (c->h_flags[0] & 4)
+        return fail(c, ENS_ERR_CUDA, "a staged block found its launch plan inconsistent");
     if (c->h_flags[0] & 2)
         return fail(c, ENS_ERR_TIMEOUT, "a staged step gave up waiting for its bulk copies");
     if (c->h_flags[0] & 1)
@@ -866,7 +920,7 @@ int ens_info(const ens_ctx *c, ens_info_t *info) {
     r.bytes_per_step = bytes_per_step(c);
     r.device_bytes = (double)c->held_bytes;
     r.kernel_variant = c->variant;
-    for (int k = 0; k < 4; k++) r.variant_us[k] = c->variant_us[k];
+    for (int k = 0; k < kVariants; k++) r.variant_us[k] = c->variant_us[k];
     *info = r;
     return ENS_OK;
 }

@@ -70,14 +70,14 @@ struct StepArgs {
 // Launch plan of the staged step kernel: each block owns `nb` consecutive nodes and
 // bulk-copies their incidence entries, coupling blocks and own displacement rows into
 // shared memory (cnt_max = most incidences of any block). staged = 0 selects the
-// unstaged kernel (samples-per-node not a power of two, or the plan exceeds smem).
+// unstaged kernel (threads per node do not divide the block, or the plan exceeds smem).
 struct StagePlan {
     int32_t staged;
-    int32_t block;   // threads per block (256 or 128)
-    int32_t nb;      // nodes per block
-    int32_t cnt_max;
-    uint32_t smem;
-    int32_t minb;    // resident blocks per SM the register budget targets (256-thread shape)
+    int32_t block;    // threads per block (256, 128 or 64)
+    int32_t nb;       // nodes per block
+    int32_t cnt_max;  // most incidences of any block
+    uint32_t smem;    // dynamic shared memory per block
+    int32_t minb;     // resident blocks per SM the register budget targets
 };
 
 // Polls of a bounded mbarrier wait before the kernel reports a timeout.
@@ -87,8 +87,8 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 template <typename R>
 cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s,
                         const StagePlan *plan = nullptr);
-StagePlan make_stage_plan(const int32_t *rowptr_host, int32_t N, int32_t Sp, int32_t Q,
-                          size_t elem_bytes, int32_t kc_stride, int32_t block, int32_t minb);
+
+const char *last_launch_note();  // detail of this thread's last failed staged launch
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s);
 cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s);

@@ -18,6 +18,8 @@
 //      writing u_{n+1} to the other ping-pong buffer.
 // There are no atomics in the force path: every node sums its own incidences in list
 // order, so results are bitwise reproducible.
+#include <cstdio>
+
 #include "ens_bits.cuh"
 #include "ens_internal.cuh"
 
@@ -276,8 +278,9 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
 // (E h)), with its own rows, the entry and the 18 coefficients coming from shared memory.
 template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs<R> a,
-                                                                  const int32_t nb_block,
-                                                                  const int32_t cnt_max) {
+                                                                  const StagePlan pl) {
+    const int32_t nb_block = pl.nb;
+    const int32_t cnt_max = pl.cnt_max;
     constexpr int V = Vw<R>::V;
     constexpr int KS = Kc<R>::stride;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -293,6 +296,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     const int32_t nb = min(nb_block, N - n0);
     const int32_t pb = __ldg(a.fv.rowptr + n0);
     const int32_t cnt = __ldg(a.fv.rowptr + n0 + nb) - pb;
+    if (cnt < 1 || cnt > cnt_max) {
+        // the plan does not describe this block: copy nothing, report, leave
+        if (threadIdx.x == 0) atomicOr(a.flags, 4);
+        return;
+    }
     const int32_t li = threadIdx.x / Q;
     const int32_t s0 = (threadIdx.x - li * Q) * V;
     const bool valid = li < nb;
@@ -500,17 +508,29 @@ __global__ void import_kernel(const double *__restrict__ in, int32_t N, int32_t 
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+thread_local char g_launch_note[160] = "";
+
+void note_launch(const char *what, int block, int minb, uint32_t smem, cudaError_t e) {
+    snprintf(g_launch_note, sizeof(g_launch_note), "%s (block %d, %d/SM, %u B shared): %s", what,
+             block, minb, smem, cudaGetErrorString(e));
+}
+
 template <int FORM, typename R, bool FO, int BLOCK, int MINB>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
     auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB>;
     if (plan->smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)plan->smem);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+            note_launch("cudaFuncSetAttribute", BLOCK, MINB, plan->smem, e);
+            return e;
+        }
     }
     const unsigned grid = (unsigned)((a.fv.N + plan->nb - 1) / plan->nb);
-    k<<<grid, BLOCK, plan->smem, s>>>(a, plan->nb, plan->cnt_max);
-    return cudaGetLastError();
+    k<<<grid, BLOCK, plan->smem, s>>>(a, *plan);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) note_launch("staged launch", BLOCK, MINB, plan->smem, e);
+    return e;
 }
 
 template <int FORM, typename R, bool FO>
@@ -522,6 +542,7 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
             if (plan->block == 256 && plan->minb == 4) return launch_staged<FORM, R, FO, 256, 4>(a, s, plan);
         } else {
             if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 6>(a, s, plan);
+            if (plan->block == 64) return launch_staged<FORM, R, FO, 64, 12>(a, s, plan);
             if (plan->minb == 3) return launch_staged<FORM, R, FO, 256, 3>(a, s, plan);
             return launch_staged<FORM, R, FO, 256, 4>(a, s, plan);
         }
@@ -532,10 +553,13 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
 
 }  // namespace
 
+const char *last_launch_note() { return g_launch_note; }
+
 template <typename R>
 cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStream_t s,
                         const StagePlan *plan) {
     if ((int64_t)a.fv.N * a.fv.Q == 0) return cudaSuccess;
+    g_launch_note[0] = 0;
     if constexpr (sizeof(R) == 8) {
         return force_only ? launch_one<kFP64, double, true>(a, s, plan)
                           : launch_one<kFP64, double, false>(a, s, plan);
@@ -550,26 +574,6 @@ template cudaError_t launch_step<double>(int, const StepArgs<double> &, bool, cu
                                          const StagePlan *);
 template cudaError_t launch_step<float>(int, const StepArgs<float> &, bool, cudaStream_t,
                                         const StagePlan *);
-
-StagePlan make_stage_plan(const int32_t *rowptr, int32_t N, int32_t Sp, int32_t Q,
-                          size_t es, int32_t kc_stride, int32_t block, int32_t minb) {
-    StagePlan p{0, block, 0, 0, 0, minb};
-    if (Q <= 0 || Q > block || (block % Q) != 0) return p;
-    const int32_t nb = block / Q;
-    int32_t cmax = 0;
-    for (int64_t n0 = 0; n0 < N; n0 += nb) {
-        const int64_t n1 = n0 + nb < N ? n0 + nb : N;
-        const int32_t c = rowptr[n1] - rowptr[n0];
-        cmax = c > cmax ? c : cmax;
-    }
-    const size_t bytes = 16 + (size_t)cmax * (16 + kc_stride * es) + (size_t)nb * 3 * Sp * es;
-    if (bytes > 160 * 1024) return p;
-    p.staged = 1;
-    p.nb = nb;
-    p.cnt_max = cmax;
-    p.smem = (uint32_t)((bytes + 127) / 128 * 128);
-    return p;
-}
 
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s) {
     advance_kernel<<<1, 1, 0, s>>>(step_ctr, n);

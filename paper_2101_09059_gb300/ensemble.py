@@ -103,7 +103,8 @@ class Ensemble:
                                     ctypes.byref(params), ctypes.c_void_p(self.stream.cuda_stream),
                                     alloc_p, ctypes.byref(out))
         if rc != 0:
-            raise EnsError(rc, self._L.ens_error_string(rc).decode())
+            msg = self._L.ens_last_error(None).decode() or self._L.ens_error_string(rc).decode()
+            raise EnsError(rc, msg)
         self._ctx = out
 
     @classmethod

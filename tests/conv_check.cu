@@ -1,0 +1,71 @@
+// Bitwise check of the integer-pipe conversions in ens_bits.cuh against the hardware
+// conversions, over edge cases and pseudo-random bit patterns. Exit code 0 = all agree.
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+#include "../paper_2101_09059_gb300/csrc/ens_bits.cuh"
+
+__global__ void conv(const float *xf, const double *xd, int n, double *o64, double *r64,
+                     float *o32, float *r32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    o64[i] = ens::f32_to_f64(xf[i]);
+    r64[i] = (double)xf[i];
+    o32[i] = ens::f64_to_f32_rz(xd[i]);
+    r32[i] = __double2float_rz(xd[i]);
+}
+
+int main() {
+    const int n = 1 << 22;
+    std::vector<float> xf(n);
+    std::vector<double> xd(n);
+    uint64_t s = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() { s ^= s << 13; s ^= s >> 7; s ^= s << 17; return s; };
+    const float ef[] = {0.0f, -0.0f, 1.0f, -1.0f, 1e-38f, 1.17549435e-38f, 1e-45f, 3.4e38f,
+                        __builtin_inff(), -__builtin_inff(), __builtin_nanf("")};
+    const double ed[] = {0.0, -0.0, 1.0, -1.0, 1e-38, 1.1754943508222875e-38, 1.1754942e-38,
+                         3.4028234663852886e38, 3.5e38, 1e-300, 5e-324, 1e300,
+                         __builtin_inf(), -__builtin_inf(), __builtin_nan("")};
+    for (int i = 0; i < n; i++) {
+        uint32_t b = (uint32_t)next();
+        uint64_t d = next();
+        memcpy(&xf[i], &b, 4);
+        memcpy(&xd[i], &d, 8);
+        if (i % 4 == 1) xd[i] = (double)xf[i] * 1.0000001;         // near float range
+        if (i % 4 == 2) xd[i] = ((double)(b % 100000) - 5e4) * 1e-9; // displacements
+    }
+    for (size_t k = 0; k < sizeof(ef) / 4; k++) xf[k] = ef[k];
+    for (size_t k = 0; k < sizeof(ed) / 8; k++) xd[k] = ed[k];
+    float *dxf, *do32, *dr32;
+    double *dxd, *do64, *dr64;
+    cudaMalloc(&dxf, 4 * n); cudaMalloc(&do32, 4 * n); cudaMalloc(&dr32, 4 * n);
+    cudaMalloc(&dxd, 8 * n); cudaMalloc(&do64, 8 * n); cudaMalloc(&dr64, 8 * n);
+    cudaMemcpy(dxf, xf.data(), 4 * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(dxd, xd.data(), 8 * n, cudaMemcpyHostToDevice);
+    conv<<<(n + 255) / 256, 256>>>(dxf, dxd, n, do64, dr64, do32, dr32);
+    std::vector<double> o64(n), r64(n);
+    std::vector<float> o32(n), r32(n);
+    cudaMemcpy(o64.data(), do64, 8 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(r64.data(), dr64, 8 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(o32.data(), do32, 4 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(r32.data(), dr32, 4 * n, cudaMemcpyDeviceToHost);
+    if (cudaGetLastError() != cudaSuccess) { printf("cuda error\n"); return 2; }
+    long bad64 = 0, bad32 = 0, flushed = 0;
+    for (int i = 0; i < n; i++) {
+        if (memcmp(&o64[i], &r64[i], 8) != 0 && !(o64[i] != o64[i] && r64[i] != r64[i])) bad64++;
+        const double ad = xd[i] < 0 ? -xd[i] : xd[i];
+        if (ad < 1.1754943508222875e-38) {   // below the binary32 normal range: signed zero
+            uint32_t ob; memcpy(&ob, &o32[i], 4);
+            uint64_t db; memcpy(&db, &xd[i], 8);
+            if ((ob & 0x7fffffffu) != 0 || (ob >> 31) != (uint32_t)(db >> 63)) bad32++;
+            flushed++;
+        } else if (memcmp(&o32[i], &r32[i], 4) != 0 && !(o32[i] != o32[i] && r32[i] != r32[i])) {
+            bad32++;
+        }
+    }
+    printf("f32->f64 mismatches %ld, f64->f32 mismatches %ld (of %d; %ld below the normal range)\n",
+           bad64, bad32, n, flushed);
+    return (bad64 || bad32) ? 1 : 0;
+}
