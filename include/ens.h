@@ -223,6 +223,48 @@ int ens_state_size(const ens_ctx *ctx, size_t *bytes);
 int ens_get_state(ens_ctx *ctx, void *buf, size_t bytes);
 int ens_set_state(ens_ctx *ctx, const void *buf, size_t bytes);
 
+/* ---- batched launches --------------------------------------------------------------
+ * Several contexts (different meshes, ensemble widths, time steps and traction tables;
+ * one precision form, one device) advanced together. This is not in the paper, whose
+ * ensembles share one mesh; it serves campaigns over uneven models.
+ * Modes: ENS_BATCH_GRAPH runs one kernel per step covering every member, with the time
+ * loop captured in a CUDA graph of 20-step chunks; ENS_BATCH_PERSISTENT runs all steps
+ * of a call in one cooperative kernel with a grid barrier between steps (bounded wait:
+ * ENS_ERR_TIMEOUT if it gives up); ENS_BATCH_AUTO times both modes at two block shapes
+ * on the members' own data during ens_batch_create (states are restored) and keeps the
+ * fastest.                                                                            */
+#define ENS_BATCH_AUTO 0
+#define ENS_BATCH_GRAPH 1
+#define ENS_BATCH_PERSISTENT 2
+
+typedef struct ens_batch ens_batch;
+
+typedef struct {
+    int32_t n_members;
+    int32_t mode;            /* ENS_BATCH_GRAPH or ENS_BATCH_PERSISTENT in use      */
+    int32_t block;           /* threads per block (256 or 128)                      */
+    int32_t graph_steps;     /* steps per captured graph                            */
+    int32_t n_tiles;         /* work tiles per step (about 1024 node-samples each)  */
+    int32_t persistent_grid; /* co-resident blocks of the persistent kernel         */
+    float mode_us[4];        /* autotuner time per step: graph 256, graph 128,
+                                persistent 256, persistent 128 (-1: not possible)   */
+    double bytes_per_step;   /* algorithmic HBM bytes of one batched step           */
+} ens_batch_info_t;
+
+/* Create a batch over n >= 1 distinct contexts (not owned; destroy the batch first).
+ * mode: ENS_BATCH_*. Errors: ENS_ERR_INVALID_ARG (mixed forms or devices, repeated
+ * members); the message is left on members[0] (ens_last_error).                        */
+int ens_batch_create(ens_ctx *const *members, int32_t n, int32_t mode, ens_batch **out);
+
+/* Advance every member n >= 0 steps (each with its own dt and load rows), exactly as n
+ * calls of ens_step on each member would. Ordered after every member's pending work;
+ * returns after the work completes. ENS_ERR_RANGE / ENS_ERR_STATE as ens_step.        */
+int ens_batch_step(ens_batch *b, int64_t n);
+
+int ens_batch_info(const ens_batch *b, ens_batch_info_t *info);
+const char *ens_batch_last_error(const ens_batch *b);
+void ens_batch_destroy(ens_batch *b);
+
 /* Sizes, step index and traffic model.                                               */
 int ens_info(const ens_ctx *ctx, ens_info_t *info);
 

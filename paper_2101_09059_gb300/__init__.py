@@ -2,7 +2,9 @@
 (Li & Schiavazzi, arXiv 2101.09059): C ABI in include/ens.h, CUDA kernels in csrc/,
 and a thin Python binding."""
 from ._lib import build, load, declared_functions
-from .ensemble import Ensemble, EnsError, FP64, FP32_FORCE, KAHAN32, PRECISIONS
+from .ensemble import (Ensemble, Batch, EnsError, FP64, FP32_FORCE, KAHAN32, PRECISIONS, BATCH_AUTO,
+                       BATCH_GRAPH, BATCH_PERSISTENT)
 
-__all__ = ["build", "load", "declared_functions", "Ensemble", "EnsError", "FP64", "FP32_FORCE",
+__all__ = ["build", "load", "declared_functions", "Ensemble", "Batch", "EnsError", "BATCH_AUTO",
+           "BATCH_GRAPH", "BATCH_PERSISTENT", "FP64", "FP32_FORCE",
            "KAHAN32", "PRECISIONS"]

@@ -109,6 +109,13 @@ class ens_info_t(ctypes.Structure):
                 ("variant_us", ctypes.c_float * 6)]
 
 
+class ens_batch_info_t(ctypes.Structure):
+    _fields_ = [("n_members", ctypes.c_int32), ("mode", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("graph_steps", ctypes.c_int32), ("n_tiles", ctypes.c_int32),
+                ("persistent_grid", ctypes.c_int32), ("mode_us", ctypes.c_float * 4),
+                ("bytes_per_step", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -145,6 +152,11 @@ def load(build_if_missing: bool = True):
         "ens_last_error": ([vp], ctypes.c_char_p),
         "ens_error_string": ([ctypes.c_int], ctypes.c_char_p),
         "ens_destroy": ([vp], None),
+        "ens_batch_create": ([ctypes.POINTER(vp), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "ens_batch_step": ([vp, i64], ctypes.c_int),
+        "ens_batch_info": ([vp, ctypes.POINTER(ens_batch_info_t)], ctypes.c_int),
+        "ens_batch_last_error": ([vp], ctypes.c_char_p),
+        "ens_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

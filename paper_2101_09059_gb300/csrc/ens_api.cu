@@ -13,45 +13,7 @@
 
 using namespace ens;
 
-namespace {
-constexpr int kVariants = 6;  // launch shapes the autotuner can time (see ens_info_t)
-}
-
-struct ens_ctx {
-    int32_t N = 0, E = 0, S = 0, Sp = 0, Q = 0, form = 0, J = 0;
-    int64_t nnz = 0, n_amp = 0, step = 0;
-    bool started = false;
-    int cur = 0;
-    double rho = 0, nu = 0, ks = 0, alpha = 0, dt = 0, w_lo = 0, w_hi = 0;
-    cudaStream_t stream = nullptr;
-    ens_allocator al{};
-    bool custom_alloc = false;
-    std::string err;
-    size_t held_bytes = 0;
-    std::vector<std::pair<void *, size_t>> bufs;
-
-    // device data
-    int32_t *rowptr = nullptr;
-    int4 *ent = nullptr;
-    uint8_t *fix = nullptr;
-    double *xyz_d = nullptr;
-    int32_t *tri_d = nullptr;
-    int32_t *ec2ent_d = nullptr;
-    void *kc = nullptr, *eh = nullptr, *minv = nullptr, *modes = nullptr, *amp = nullptr;
-    void *ug[2] = {nullptr, nullptr};
-    double *u64 = nullptr, *v64 = nullptr;
-    float *ulo = nullptr, *v32 = nullptr;
-    int *flags = nullptr;
-    int64_t *step_ctr = nullptr;
-    double *stat_mean = nullptr, *stat_var = nullptr;
-    double *export_buf = nullptr;
-    int *h_flags = nullptr;  // pinned
-    StagePlan plan{};     // launch shape of the step kernel
-    StagePlan plan_fo{};  // launch shape of force-only evaluations
-    int32_t variant = 0;
-    float variant_us[kVariants] = {0, 0, 0, 0, 0, 0};
-    int32_t flags_in = 0;
-};
+#include "ens_ctx.cuh"
 
 namespace {
 
@@ -142,7 +104,6 @@ bool finite_all(const double *x, size_t n) {
     return true;
 }
 
-size_t elem_size(int form) { return form == kFP64 ? 8 : 4; }
 
 // Algorithmic HBM bytes of one step: per node-sample the state traffic of the form
 // (u read + write, v read + write, (E h) of the E/N incident elements, 1/m), plus the
@@ -154,30 +115,6 @@ double bytes_per_step(const ens_ctx *c) {
     return ns + fixed;
 }
 
-template <typename R>
-StepArgs<R> make_args(ens_ctx *c) {
-    StepArgs<R> a{};
-    a.fv.rowptr = c->rowptr;
-    a.fv.ent = c->ent;
-    a.fv.kc = (const R *)c->kc;
-    a.fv.eh = (const R *)c->eh;
-    a.fv.N = c->N;
-    a.fv.Sp = c->Sp;
-    a.fv.Q = c->Q;
-    a.u64 = c->u64;
-    a.v64 = c->v64;
-    a.ulo = c->ulo;
-    a.v32 = c->v32;
-    a.minv = (const R *)c->minv;
-    a.fix = c->fix;
-    a.modes = (const R *)c->modes;
-    a.amp = (const R *)c->amp;
-    a.step_ctr = c->step_ctr;
-    a.J = c->J;
-    a.dt = c->dt;
-    a.flags = c->flags;
-    return a;
-}
 
 int run_steps(ens_ctx *c, int64_t n) {
     const double beta = 0.5 * c->alpha * c->dt;
@@ -308,6 +245,22 @@ const void *state_main(const ens_ctx *c) {
 
 }  // namespace
 
+namespace ens {
+int ctx_fail(ens_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = std::string(code_name(code)) + ": " + buf;
+    }
+    return code;
+}
+void *ctx_alloc(ens_ctx *c, size_t bytes) { return dev_alloc(c, bytes); }
+void ctx_free(ens_ctx *c, void *p) { dev_free(c, p); }
+}  // namespace ens
+
 extern "C" {
 
 const char *ens_error_string(int code) { return code_name(code); }
@@ -360,6 +313,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
     c->dt = p->dt;
     c->stream = (cudaStream_t)stream;
     c->flags_in = p->flags;
+    cudaGetDevice(&c->device);
     if (alloc) {
         c->al = *alloc;
         c->custom_alloc = true;

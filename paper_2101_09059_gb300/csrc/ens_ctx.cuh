@@ -1,0 +1,86 @@
+// Host-side context shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ens.h"
+#include "ens_internal.cuh"
+
+namespace ens {
+constexpr int kVariants = 6;  // launch shapes the autotuner can time (see ens_info_t)
+}
+
+struct ens_ctx {
+    int32_t device = 0;  // CUDA device the context was created on
+    int32_t N = 0, E = 0, S = 0, Sp = 0, Q = 0, form = 0, J = 0;
+    int64_t nnz = 0, n_amp = 0, step = 0;
+    bool started = false;
+    int cur = 0;
+    double rho = 0, nu = 0, ks = 0, alpha = 0, dt = 0, w_lo = 0, w_hi = 0;
+    cudaStream_t stream = nullptr;
+    ens_allocator al{};
+    bool custom_alloc = false;
+    std::string err;
+    size_t held_bytes = 0;
+    std::vector<std::pair<void *, size_t>> bufs;
+
+    // device data
+    int32_t *rowptr = nullptr;
+    int4 *ent = nullptr;
+    uint8_t *fix = nullptr;
+    double *xyz_d = nullptr;
+    int32_t *tri_d = nullptr;
+    int32_t *ec2ent_d = nullptr;
+    void *kc = nullptr, *eh = nullptr, *minv = nullptr, *modes = nullptr, *amp = nullptr;
+    void *ug[2] = {nullptr, nullptr};
+    double *u64 = nullptr, *v64 = nullptr;
+    float *ulo = nullptr, *v32 = nullptr;
+    int *flags = nullptr;
+    int64_t *step_ctr = nullptr;
+    double *stat_mean = nullptr, *stat_var = nullptr;
+    double *export_buf = nullptr;
+    int *h_flags = nullptr;  // pinned
+    ens::StagePlan plan{};     // launch shape of the step kernel
+    ens::StagePlan plan_fo{};  // launch shape of force-only evaluations
+    int32_t variant = 0;
+    float variant_us[ens::kVariants] = {0, 0, 0, 0, 0, 0};
+    int32_t flags_in = 0;
+};
+
+
+namespace ens {
+
+// Helpers defined in ens_api.cu.
+int ctx_fail(ens_ctx *c, int code, const char *fmt, ...);
+void *ctx_alloc(ens_ctx *c, size_t bytes);
+void ctx_free(ens_ctx *c, void *p);
+inline size_t elem_size(int form) { return form == kFP64 ? 8 : 4; }
+
+template <typename R>
+StepArgs<R> make_args(ens_ctx *c) {
+    StepArgs<R> a{};
+    a.fv.rowptr = c->rowptr;
+    a.fv.ent = c->ent;
+    a.fv.kc = (const R *)c->kc;
+    a.fv.eh = (const R *)c->eh;
+    a.fv.N = c->N;
+    a.fv.Sp = c->Sp;
+    a.fv.Q = c->Q;
+    a.u64 = c->u64;
+    a.v64 = c->v64;
+    a.ulo = c->ulo;
+    a.v32 = c->v32;
+    a.minv = (const R *)c->minv;
+    a.fix = c->fix;
+    a.modes = (const R *)c->modes;
+    a.amp = (const R *)c->amp;
+    a.step_ctr = c->step_ctr;
+    a.J = c->J;
+    a.dt = c->dt;
+    a.flags = c->flags;
+    return a;
+}
+
+}  // namespace ens

@@ -80,6 +80,29 @@ struct StagePlan {
     int32_t minb;     // resident blocks per SM the register budget targets
 };
 
+// One member of a batched launch (several contexts advanced by one kernel per step or
+// by one persistent kernel). Built on the host before every batched call.
+template <typename R>
+struct MemberDev {
+    ForceView<R> fv;
+    const R *ug[2];         // ping-pong gathered displacement buffers
+    double *u64, *v64;
+    float *ulo, *v32;
+    const R *minv;
+    const uint8_t *fix;
+    const R *modes, *amp;
+    int64_t *step_ctr;
+    int32_t J;
+    int32_t cur;            // buffer holding u_n at the start of the call
+    int32_t first;          // the call's first step applies the start constants
+    int32_t pad;
+    double c1, c2, dt;      // regular update constants
+    double c1s, c2s;        // start-step constants
+};
+
+// Spin iterations (each with a short sleep) of a grid-barrier wait before giving up.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
 // Polls of a bounded mbarrier wait before the kernel reports a timeout.
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -89,6 +112,17 @@ cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStr
                         const StagePlan *plan = nullptr);
 
 const char *last_launch_note();  // detail of this thread's last failed staged launch
+// Batched launches (ens_step.cu). items: {member, first node, first lane, 0} tiles.
+template <typename R>
+cudaError_t launch_batch_step(int form, int block, const MemberDev<R> *mem, const int4 *items,
+                              int32_t n_items, int32_t k_off, int *flags, cudaStream_t s);
+template <typename R>
+cudaError_t launch_batch_persistent(int form, int block, const MemberDev<R> *mem,
+                                    const int4 *items, int32_t n_items, int32_t n_steps,
+                                    unsigned *bar, int *flags, int grid, cudaStream_t s);
+template <typename R>
+int batch_persistent_grid(int form, int block);  // co-resident blocks of the persistent kernel
+cudaError_t launch_advance_many(int64_t *const *ctrs, int32_t n, int64_t by, cudaStream_t s);
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s);
 cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s);

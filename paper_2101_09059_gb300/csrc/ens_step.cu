@@ -95,7 +95,29 @@ __device__ __forceinline__ void ld_kc(const float *p, float (&k)[18]) {
 
 // Internal force of node i for samples [s0, s0 + V): f = sum over incidences of
 // (E h)_e,s (K_{c,a} (u_a - u_i) + K_{c,b} (u_b - u_i)).
-template <typename R>
+// L2-only loads for data another SM may have written earlier in the same kernel (the
+// persistent batched kernel); the read-only path is not coherent within a kernel.
+__device__ __forceinline__ void ld_cg(const double *p, double (&x)[2]) {
+    double2 t = __ldcg(reinterpret_cast<const double2 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+}
+__device__ __forceinline__ void ld_cg(const float *p, float (&x)[4]) {
+    float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+}
+template <bool COH, typename R>
+__device__ __forceinline__ void ld_state(const R *p, R (&x)[Vw<R>::V]) {
+    if constexpr (COH)
+        ld_cg(p, x);
+    else
+        ld_nc(p, x);
+}
+
+template <typename R, bool COH = false>
 __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__restrict__ ug,
                                            int32_t i, int32_t s0, const R (&ui)[3][Vw<R>::V],
                                            R (&f)[3][Vw<R>::V]) {
@@ -112,8 +134,8 @@ __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__res
         R ua[3][V], ub[3][V], e[V], k[18];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            ld_nc(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
-            ld_nc(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
+            ld_state<COH>(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
+            ld_state<COH>(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
         }
         ld_nc(w.eh + (int64_t)en.x * Sp + s0, e);
         ld_kc(w.kc + (int64_t)p * Kc<R>::stride, k);
@@ -390,6 +412,103 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
 
 __global__ void advance_kernel(int64_t *ctr, int64_t n) { *ctr += n; }
 
+__global__ void advance_many_kernel(int64_t *const *ctrs, int32_t n, int64_t by) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) *ctrs[k] += by;
+}
+
+// One tile of a batched launch: member item.x, nodes from item.y, lanes from item.z.
+// The tile holds BLOCK / Qt nodes with Qt = min(Q, BLOCK) threads per node.
+template <int FORM, typename R, int BLOCK, bool COH>
+__device__ __forceinline__ void batch_tile(const MemberDev<R> *__restrict__ mem, const int4 item,
+                                           int32_t k_off, int *flags) {
+    constexpr int V = Vw<R>::V;
+    const MemberDev<R> &m = mem[item.x];
+    const int32_t Q = m.fv.Q;
+    const int32_t Qt = Q < BLOCK ? Q : BLOCK;
+    const int32_t li = threadIdx.x / Qt;
+    const int32_t q = item.z + (threadIdx.x - li * Qt);
+    const int32_t i = item.y + li;
+    if (li >= BLOCK / Qt || i >= m.fv.N || q >= Q) return;
+    StepArgs<R> a;
+    a.fv = m.fv;
+    const int par = m.cur ^ (k_off & 1);
+    a.ug_cur = m.ug[par];
+    a.ug_next = const_cast<R *>(m.ug[par ^ 1]);
+    a.u64 = m.u64;
+    a.v64 = m.v64;
+    a.ulo = m.ulo;
+    a.v32 = m.v32;
+    a.minv = m.minv;
+    a.fix = m.fix;
+    a.modes = m.modes;
+    a.amp = m.amp;
+    a.step_ctr = m.step_ctr;
+    a.k_off = k_off;
+    a.J = m.J;
+    const bool start = m.first && k_off == 0;
+    a.c1 = start ? m.c1s : m.c1;
+    a.c2 = start ? m.c2s : m.c2;
+    a.dt = m.dt;
+    a.force_out = nullptr;
+    a.flags = flags;
+    const int32_t s0 = q * V;
+    const int64_t Sp = m.fv.Sp;
+    R ui[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++) ld_state<COH>(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
+    R f[3][V];
+    node_force<R, COH>(a.fv, a.ug_cur, i, s0, ui, f);
+    node_update<FORM, R>(a, i, s0, ui, f);
+}
+
+// Batched step: one launch advances every member one step (graph-captured in chunks).
+template <int FORM, typename R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) batch_step_kernel(const MemberDev<R> *__restrict__ mem,
+                                                           const int4 *__restrict__ items,
+                                                           int32_t k_off, int *flags) {
+    batch_tile<FORM, R, BLOCK, false>(mem, items[blockIdx.x], k_off, flags);
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Persistent batched kernel: n_steps steps in one cooperative launch. Every block keeps
+// the same tiles (round robin) for the whole launch; a grid barrier with a bounded spin
+// separates the steps. Displacement rows written by other blocks are read through L2.
+template <int FORM, typename R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) batch_persistent_kernel(
+    const MemberDev<R> *__restrict__ mem, const int4 *__restrict__ items, int32_t n_items,
+    int32_t n_steps, unsigned *bar, int *flags) {
+    __shared__ int abort_all;
+    for (int32_t k = 0; k < n_steps; k++) {
+        for (int32_t t = blockIdx.x; t < n_items; t += gridDim.x)
+            batch_tile<FORM, R, BLOCK, true>(mem, items[t], k, flags);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(bar, 1u);
+            const unsigned target = (unsigned)(k + 1) * gridDim.x;
+            bool ok = false;
+            for (uint32_t it = 0; it < kSpinLimit; ++it) {
+                if (ld_acquire(bar) >= target) {
+                    ok = true;
+                    break;
+                }
+                __nanosleep(64);
+            }
+            if (!ok) atomicOr(flags, 2);
+            abort_all = ok ? 0 : 1;
+            __threadfence();
+        }
+        __syncthreads();
+        if (abort_all) return;
+    }
+}
+
 // Ensemble mean and sample variance per dof: 8 lanes per (node, dof) row, each lane
 // holding up to 16 of the row's samples in registers between the two passes (exact
 // two-pass formula; the shuffle tree fixes the reduction order). For wider ensembles
@@ -574,6 +693,97 @@ template cudaError_t launch_step<double>(int, const StepArgs<double> &, bool, cu
                                          const StagePlan *);
 template cudaError_t launch_step<float>(int, const StepArgs<float> &, bool, cudaStream_t,
                                         const StagePlan *);
+
+template <typename R>
+cudaError_t launch_batch_step(int form, int block, const MemberDev<R> *mem, const int4 *items,
+                              int32_t n_items, int32_t k_off, int *flags, cudaStream_t s) {
+    if (n_items == 0) return cudaSuccess;
+    if constexpr (sizeof(R) == 8) {
+        if (block == 128)
+            batch_step_kernel<kFP64, double, 128><<<n_items, 128, 0, s>>>(mem, items, k_off, flags);
+        else
+            batch_step_kernel<kFP64, double, 256><<<n_items, 256, 0, s>>>(mem, items, k_off, flags);
+    } else if (form == kFP32Force) {
+        if (block == 128)
+            batch_step_kernel<kFP32Force, float, 128><<<n_items, 128, 0, s>>>(mem, items, k_off, flags);
+        else
+            batch_step_kernel<kFP32Force, float, 256><<<n_items, 256, 0, s>>>(mem, items, k_off, flags);
+    } else {
+        if (block == 128)
+            batch_step_kernel<kKahan32, float, 128><<<n_items, 128, 0, s>>>(mem, items, k_off, flags);
+        else
+            batch_step_kernel<kKahan32, float, 256><<<n_items, 256, 0, s>>>(mem, items, k_off, flags);
+    }
+    return cudaGetLastError();
+}
+
+template <int FORM, typename R, int BLOCK>
+static cudaError_t coop_launch(const MemberDev<R> *mem, const int4 *items, int32_t n_items,
+                               int32_t n_steps, unsigned *bar, int *flags, int grid, cudaStream_t s) {
+    void *args[] = {(void *)&mem, (void *)&items, (void *)&n_items, (void *)&n_steps, (void *)&bar,
+                    (void *)&flags};
+    return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel<FORM, R, BLOCK>,
+                                       dim3(grid), dim3(BLOCK), args, 0, s);
+}
+
+template <int FORM, typename R, int BLOCK>
+static int coop_grid() {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_persistent_kernel<FORM, R, BLOCK>,
+                                                      BLOCK, 0) != cudaSuccess)
+        return 0;
+    return sms * per;
+}
+
+template <typename R>
+int batch_persistent_grid(int form, int block) {
+    if constexpr (sizeof(R) == 8)
+        return block == 128 ? coop_grid<kFP64, double, 128>() : coop_grid<kFP64, double, 256>();
+    else if (form == kFP32Force)
+        return block == 128 ? coop_grid<kFP32Force, float, 128>() : coop_grid<kFP32Force, float, 256>();
+    else
+        return block == 128 ? coop_grid<kKahan32, float, 128>() : coop_grid<kKahan32, float, 256>();
+}
+
+template <typename R>
+cudaError_t launch_batch_persistent(int form, int block, const MemberDev<R> *mem,
+                                    const int4 *items, int32_t n_items, int32_t n_steps,
+                                    unsigned *bar, int *flags, int grid, cudaStream_t s) {
+    if (n_items == 0 || n_steps == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(R) == 8) {
+        return block == 128 ? coop_launch<kFP64, double, 128>(mem, items, n_items, n_steps, bar, flags, grid, s)
+                            : coop_launch<kFP64, double, 256>(mem, items, n_items, n_steps, bar, flags, grid, s);
+    } else if (form == kFP32Force) {
+        return block == 128 ? coop_launch<kFP32Force, float, 128>(mem, items, n_items, n_steps, bar, flags, grid, s)
+                            : coop_launch<kFP32Force, float, 256>(mem, items, n_items, n_steps, bar, flags, grid, s);
+    } else {
+        return block == 128 ? coop_launch<kKahan32, float, 128>(mem, items, n_items, n_steps, bar, flags, grid, s)
+                            : coop_launch<kKahan32, float, 256>(mem, items, n_items, n_steps, bar, flags, grid, s);
+    }
+}
+
+template cudaError_t launch_batch_step<double>(int, int, const MemberDev<double> *, const int4 *,
+                                               int32_t, int32_t, int *, cudaStream_t);
+template cudaError_t launch_batch_step<float>(int, int, const MemberDev<float> *, const int4 *,
+                                              int32_t, int32_t, int *, cudaStream_t);
+template cudaError_t launch_batch_persistent<double>(int, int, const MemberDev<double> *,
+                                                     const int4 *, int32_t, int32_t, unsigned *,
+                                                     int *, int, cudaStream_t);
+template cudaError_t launch_batch_persistent<float>(int, int, const MemberDev<float> *,
+                                                    const int4 *, int32_t, int32_t, unsigned *,
+                                                    int *, int, cudaStream_t);
+template int batch_persistent_grid<double>(int, int);
+template int batch_persistent_grid<float>(int, int);
+
+cudaError_t launch_advance_many(int64_t *const *ctrs, int32_t n, int64_t by, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    advance_many_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctrs, n, by);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s) {
     advance_kernel<<<1, 1, 0, s>>>(step_ctr, n);

@@ -216,3 +216,54 @@ class Ensemble:
         out = {name: getattr(i, name) for name, _ in i._fields_}
         out["variant_us"] = list(out["variant_us"])
         return out
+
+
+BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
+
+
+class Batch:
+    """Several Ensembles (uneven meshes, widths and time steps; one precision form)
+    advanced together by one batched launch per step (graph-captured) or one persistent
+    launch (ens_batch_* in the C ABI). The members must outlive the batch."""
+
+    def __init__(self, members, mode: int = BATCH_AUTO):
+        self._L = _lib.load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._ctx.value for m in self.members])
+        out = ctypes.c_void_p()
+        rc = self._L.ens_batch_create(arr, len(self.members), int(mode), ctypes.byref(out))
+        if rc != 0:
+            msg = self._L.ens_last_error(self.members[0]._ctx).decode() or self._L.ens_error_string(rc).decode()
+            raise EnsError(rc, msg)
+        self._b = out
+
+    def _check(self, rc):
+        if rc != 0:
+            raise EnsError(rc, self._L.ens_batch_last_error(self._b).decode())
+
+    def step(self, n: int = 1):
+        self._check(self._L.ens_batch_step(self._b, int(n)))
+
+    def info(self) -> dict:
+        i = _lib.ens_batch_info_t()
+        self._check(self._L.ens_batch_info(self._b, ctypes.byref(i)))
+        out = {name: getattr(i, name) for name, _ in i._fields_}
+        out["mode_us"] = list(out["mode_us"])
+        return out
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.ens_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

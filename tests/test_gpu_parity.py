@@ -290,3 +290,58 @@ def test_ragged_width_uses_unstaged_kernel():
     e = ens.Ensemble.from_case(case, precision="kahan32")
     assert e.info()["kernel_variant"] == 0
     e.close()
+
+
+def _batch_cases(sizes, widths):
+    out = []
+    for k, (n, S) in enumerate(zip(sizes, widths)):
+        c = synth.make_case(f"tube_{n}k", S=S, n_steps=90, seed=k) if n >= 1 else None
+        out.append(c)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["kahan32", "fp32_force", "fp64"])
+@pytest.mark.parametrize("mode", [ens.BATCH_GRAPH, ens.BATCH_PERSISTENT, ens.BATCH_AUTO])
+def test_batched_members_equal_individual_runs(precision, mode):
+    """Uneven members (different meshes, widths and time steps) advanced by one batched
+    launch per step or by one persistent launch give bit for bit the trajectories of
+    stepping each member on its own, across graph replays, a remainder and the start."""
+    cases = [synth.make_case("tube_small", S=3, n_steps=90, seed=1),
+             synth.make_case("tube_40x40", S=8, n_steps=90, seed=2),
+             synth.make_case("plate", S=33, n_steps=90, seed=3),
+             synth.make_case("tube_2k", S=64, n_steps=90, seed=4)]
+    solo = []
+    for c in cases:
+        e = ens.Ensemble.from_case(c, precision=precision, flags=ens.ensemble.FLAG_UNSTAGED)
+        e.step(53)
+        e.step(20)
+        solo.append(e.displacement())
+        e.close()
+    members = [ens.Ensemble.from_case(c, precision=precision) for c in cases]
+    with ens.Batch(members, mode=mode) as b:
+        info = b.info()
+        assert info["n_members"] == 4 and info["mode"] in (1, 2)
+        b.step(53)     # start step + two graph replays + a remainder of 12
+        b.step(20)
+    for m, ref in zip(members, solo):
+        assert m.info()["step"] == 73
+        assert np.array_equal(m.displacement(), ref)
+        m.close()
+
+
+def test_batched_config2_sampled_parity():
+    """The five-tube uneven batch (20k..400k nodes, S = 256..16) in one persistent/graph
+    launch: two samples of every member against the oracle after 40 steps."""
+    sizes, widths = [20, 50, 100, 200, 400], [256, 128, 64, 32, 16]
+    cases = [synth.make_case(f"tube_{n}k", S=S, n_steps=40, seed=k)
+             for k, (n, S) in enumerate(zip(sizes, widths))]
+    members = [ens.Ensemble.from_case(c, precision="kahan32") for c in cases]
+    with ens.Batch(members) as b:
+        b.step(40)
+    for c, m in zip(cases, members):
+        u = m.displacement()
+        picks = [0, c["S"] - 1]
+        ref = _oracle_run(c, 40, samples=picks)
+        for k, s in enumerate(picks):
+            assert rel_l2(u[s], ref[k]) < TOL["kahan32"]
+        m.close()
