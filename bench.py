@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--forms", default=",".join(FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-chunk", type=int, default=100)
+    ap.add_argument("--batch-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -234,6 +237,72 @@ def cpu_baseline(case, S, budget_s=15.0):
             "sample": f"{n} time steps x {S} samples of the same {case['mesh'].n_nodes}-node workload"}
 
 
+def bench_batched(args, local, stream, world):
+    """Five clamped tubes (20k, 50k, 100k, 200k, 400k nodes; S = 256, 128, 64, 32, 16; each
+    with its own CFL time step; 10 kPa step load) advanced by one batched launch per step
+    (or one persistent launch), against the same members stepped one after another."""
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+    sizes, widths = [20, 50, 100, 200, 400], [256, 128, 64, 32, 16]
+    C, W, K = args.batch_chunk, 2, args.batch_steps
+    need = 2 * C * (W + K) + 1
+    cases = [synth.make_case(f"tube_{n}k", S=S, n_steps=need, seed=k + 100 * local)
+             for k, (n, S) in enumerate(zip(sizes, widths))]
+    form = "kahan32"
+    members = [pkg.Ensemble.from_case(c, precision=form, stream=stream, device=local) for c in cases]
+    batch = pkg.Batch(members)
+    info = batch.info()
+    ss = sum(c["S"] for c in cases)
+    nss = sum(c["S"] * c["mesh"].n_nodes for c in cases)
+    for _ in range(W):
+        batch.step(C)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(K):
+            batch.step(C)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+    batch.close()
+    # the same members stepped one after another on the same stream
+    for _ in range(W):
+        for m in members:
+            m.step(C)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(K):
+        for m in members:
+            m.step(C)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_solo = ev0.elapsed_time(ev1) / 1e3
+    for m in members:
+        m.close()
+    t_batch = max_over_ranks(t_batch, world)
+    steps = C * K
+    hbm_peak, _ = peaks()
+    gbs = info["bytes_per_step"] * steps / t_batch / 1e9
+    return {
+        "workload": "5 clamped tubes, 20k/50k/100k/200k/400k nodes, S=256/128/64/32/16, own CFL dt, "
+                    "10 kPa step load, compensated FP32",
+        "value": sum_over_ranks(ss * steps / t_batch, world), "unit": "sample-steps/s",
+        "node_sample_steps_per_s": sum_over_ranks(nss * steps / t_batch, world),
+        "ms_per_step": 1e3 * t_batch / K, "time_steps_per_step": C,
+        "achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+        "mode": {1: "graph", 2: "persistent", 3: "sequence"}.get(info["mode"], info["mode"]),
+        "block": info["block"],
+        "autotune_us_per_step": {"graph256": info["mode_us"][0], "graph128": info["mode_us"][1],
+                                 "persistent256": info["mode_us"][2], "persistent128": info["mode_us"][3],
+                                 "sequence": info["mode_us"][4]},
+        "one_after_another_value": ss * steps / t_solo,
+        "speedup_vs_one_after_another": t_solo / t_batch,
+        "clocks": clk.summary(),
+    }
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -334,6 +403,8 @@ def main():
                "h2d_bytes_per_step": int(C * case["amp"].shape[1] * 8),
                "d2h_bytes_per_step": int(2 * N * 3 * 8 + 4)}
 
+    batched = None if args.no_batched else bench_batched(args, local, stream, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case, S)
@@ -370,6 +441,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "forms": results,
+        "batched_uneven": batched,
         "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
     }
     if rank == 0:

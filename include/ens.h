@@ -230,24 +230,27 @@ int ens_set_state(ens_ctx *ctx, const void *buf, size_t bytes);
  * Modes: ENS_BATCH_GRAPH runs one kernel per step covering every member, with the time
  * loop captured in a CUDA graph of 20-step chunks; ENS_BATCH_PERSISTENT runs all steps
  * of a call in one cooperative kernel with a grid barrier between steps (bounded wait:
- * ENS_ERR_TIMEOUT if it gives up); ENS_BATCH_AUTO times both modes at two block shapes
- * on the members' own data during ens_batch_create (states are restored) and keeps the
- * fastest.                                                                            */
+ * ENS_ERR_TIMEOUT if it gives up); ENS_BATCH_SEQUENCE runs every member's own tuned
+ * step kernel back to back per step, the loop captured in a graph; ENS_BATCH_AUTO times
+ * every mode and block shape on the members' own data during ens_batch_create (states
+ * are restored) and keeps the fastest.                                                */
 #define ENS_BATCH_AUTO 0
 #define ENS_BATCH_GRAPH 1
 #define ENS_BATCH_PERSISTENT 2
+#define ENS_BATCH_SEQUENCE 3
 
 typedef struct ens_batch ens_batch;
 
 typedef struct {
     int32_t n_members;
-    int32_t mode;            /* ENS_BATCH_GRAPH or ENS_BATCH_PERSISTENT in use      */
-    int32_t block;           /* threads per block (256 or 128)                      */
+    int32_t mode;            /* ENS_BATCH_GRAPH, _PERSISTENT or _SEQUENCE in use    */
+    int32_t block;           /* threads per block (256 or 128; 0: members' own)     */
     int32_t graph_steps;     /* steps per captured graph                            */
     int32_t n_tiles;         /* work tiles per step (about 1024 node-samples each)  */
     int32_t persistent_grid; /* co-resident blocks of the persistent kernel         */
-    float mode_us[4];        /* autotuner time per step: graph 256, graph 128,
-                                persistent 256, persistent 128 (-1: not possible)   */
+    float mode_us[5];        /* autotuner time per step: graph 256, graph 128,
+                                persistent 256, persistent 128, sequence
+                                (-1: not possible, 0: not timed)                    */
     double bytes_per_step;   /* algorithmic HBM bytes of one batched step           */
 } ens_batch_info_t;
 

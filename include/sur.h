@@ -1,0 +1,87 @@
+/*
+ * sur.h — C ABI of the surrogate network trained on the ensemble solver's output.
+ *
+ * Not part of the paper: its uncertainty propagation runs the ensemble solver directly
+ * (Section 1, Section 3). This library adds a learned shortcut for repeated statistics:
+ * a multilayer perceptron n_in -> H -> H -> n_out with GELU activations maps the
+ * truncated Karhunen-Loeve coefficients of the realisation's E and h fields to POD
+ * coefficients of a displacement field the solver produced. Training minimises the mean
+ * squared error with Adam (beta1 = 0.9, beta2 = 0.999, eps = 1e-8). Matrix products run
+ * on the tensor cores in BF16 with FP32 accumulation; parameters, activations, gradients
+ * and optimiser state are FP32.
+ *
+ * Conventions: every call returns SUR_OK (0) or a negative SUR_ERR_* code and
+ * sur_last_error gives the message. Arrays with the suffix _dev are device pointers
+ * (row-major, FP32, caller-owned); host arrays are caller-owned. Work runs on the stream
+ * given to sur_create and calls that return host data synchronise it.
+ * Parameter vector layout (sur_get_params, sur_set_params, gradients): W1 [H][n_in], b1 [H],
+ * W2 [H][H], b2 [H], W3 [n_out][H], b3 [n_out] at the offsets sur_param_offsets reports
+ * (each tensor starts on a 16-byte boundary; y = x W^T + b).
+ */
+#ifndef SUR_H
+#define SUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SUR_OK 0
+#define SUR_ERR_INVALID_ARG (-1)
+#define SUR_ERR_ALLOC (-2)
+#define SUR_ERR_CUDA (-3)
+
+typedef struct sur_ctx sur_ctx;
+
+/* Network n_in -> n_hidden -> n_hidden -> n_out with weights drawn uniformly in
+ * +-1/sqrt(fan_in) from `seed`; max_batch = most rows one forward or training step handles. */
+int sur_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, uint64_t seed,
+               void *stream, sur_ctx **out);
+
+int64_t sur_param_count(const sur_ctx *c);
+int sur_param_offsets(const sur_ctx *c, int64_t *offsets6);
+/* Replace the parameters (host FP32, sur_param_count values); resets the Adam state.    */
+int sur_set_params(sur_ctx *c, const float *host);
+int sur_get_params(sur_ctx *c, float *host);
+
+/* y_dev [B][n_out] = network(x_dev [B][n_in]), any B >= 0 (processed in max_batch rows). */
+int sur_forward(sur_ctx *c, const float *x_dev, int64_t B, float *y_dev);
+
+/* Mean squared error of one batch (1 <= B <= max_batch) and its gradient with respect to
+ * every parameter (host, sur_param_count values; either output may be NULL).             */
+int sur_loss_grad(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, float *loss_host,
+                  float *grad_host);
+
+/* Mean squared error over B >= 1 rows (host result).                                     */
+int sur_loss(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, float *loss_host);
+
+/* One Adam step on one batch (1 <= B <= max_batch) with learning rate lr.               */
+int sur_adam_step(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, float lr);
+
+/* `epochs` passes over n rows (X_dev [n][n_in], T_dev [n][n_out]) in shuffled mini-batches
+ * of `batch` rows (a seeded permutation per epoch; the last n % batch rows of each
+ * permutation are skipped). loss_host (may be NULL): mean mini-batch loss per epoch.
+ * One epoch is captured in a CUDA graph on first use and replayed.                       */
+int sur_train(sur_ctx *c, const float *X_dev, const float *T_dev, int64_t n, int32_t batch,
+              int32_t epochs, float lr, uint64_t seed, float *loss_host);
+
+/* POD reconstruction u_dev [B][D] = mean_dev [D] + coef_dev [B][r] phi_dev [D][r]^T.     */
+int sur_reconstruct(const float *coef_dev, const float *mean_dev, const float *phi_dev, int32_t B,
+                    int64_t D, int32_t r, float *u_dev, void *stream);
+
+/* General product on the tensor cores (BF16 inputs, FP32 accumulation):
+ * C[m][n] (row stride ldc) = sum_k A[m sam + k sak] B[k sbk + n sbn]; used for POD
+ * projections, coefficients = (u - mean) phi.                                            */
+int sur_matmul(const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn,
+               float *C, int32_t M, int32_t N, int32_t K, int32_t ldc, void *stream);
+
+const char *sur_last_error(const sur_ctx *c);
+void sur_destroy(sur_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUR_H */

@@ -3,8 +3,8 @@
 and a thin Python binding."""
 from ._lib import build, load, declared_functions
 from .ensemble import (Ensemble, Batch, EnsError, FP64, FP32_FORCE, KAHAN32, PRECISIONS, BATCH_AUTO,
-                       BATCH_GRAPH, BATCH_PERSISTENT)
+                       BATCH_GRAPH, BATCH_PERSISTENT, BATCH_SEQUENCE)
 
 __all__ = ["build", "load", "declared_functions", "Ensemble", "Batch", "EnsError", "BATCH_AUTO",
-           "BATCH_GRAPH", "BATCH_PERSISTENT", "FP64", "FP32_FORCE",
+           "BATCH_GRAPH", "BATCH_PERSISTENT", "BATCH_SEQUENCE", "FP64", "FP32_FORCE",
            "KAHAN32", "PRECISIONS"]

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libens.so")
-HEADERS = [os.path.join(ROOT, "include", "ens.h")]
+HEADERS = [os.path.join(ROOT, "include", "ens.h"), os.path.join(ROOT, "include", "sur.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
@@ -112,7 +112,7 @@ class ens_info_t(ctypes.Structure):
 class ens_batch_info_t(ctypes.Structure):
     _fields_ = [("n_members", ctypes.c_int32), ("mode", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("graph_steps", ctypes.c_int32), ("n_tiles", ctypes.c_int32),
-                ("persistent_grid", ctypes.c_int32), ("mode_us", ctypes.c_float * 4),
+                ("persistent_grid", ctypes.c_int32), ("mode_us", ctypes.c_float * 5),
                 ("bytes_per_step", ctypes.c_double)]
 
 
@@ -157,6 +157,20 @@ def load(build_if_missing: bool = True):
         "ens_batch_info": ([vp, ctypes.POINTER(ens_batch_info_t)], ctypes.c_int),
         "ens_batch_last_error": ([vp], ctypes.c_char_p),
         "ens_batch_destroy": ([vp], None),
+        "sur_create": ([i32, i32, i32, i32, ctypes.c_uint64, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "sur_param_count": ([vp], ctypes.c_int64),
+        "sur_param_offsets": ([vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sur_set_params": ([vp, dp], ctypes.c_int),
+        "sur_get_params": ([vp, dp], ctypes.c_int),
+        "sur_forward": ([vp, dp, i64, dp], ctypes.c_int),
+        "sur_loss_grad": ([vp, dp, dp, i64, dp, dp], ctypes.c_int),
+        "sur_loss": ([vp, dp, dp, i64, dp], ctypes.c_int),
+        "sur_adam_step": ([vp, dp, dp, i64, ctypes.c_float], ctypes.c_int),
+        "sur_train": ([vp, dp, dp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, dp], ctypes.c_int),
+        "sur_reconstruct": ([dp, dp, dp, i32, i64, i32, dp, vp], ctypes.c_int),
+        "sur_matmul": ([dp, i64, i64, dp, i64, i64, dp, i32, i32, i32, i32, vp], ctypes.c_int),
+        "sur_last_error": ([vp], ctypes.c_char_p),
+        "sur_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

@@ -116,44 +116,52 @@ double bytes_per_step(const ens_ctx *c) {
 }
 
 
-int run_steps(ens_ctx *c, int64_t n) {
+// Launch step k of a chunk whose first step reads buffer c->cur (the context is not
+// changed): reads ug[cur ^ (k & 1)], writes the other buffer; start = Taylor start step.
+cudaError_t launch_chunk_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s) {
     const double beta = 0.5 * c->alpha * c->dt;
+    double c1, c2;
+    if (start) {  // Taylor start: v_{1/2} = (1 - beta) v_0 + dt/2 a_0
+        c1 = 1.0 - beta;
+        c2 = 0.5 * c->dt;
+    } else {
+        c1 = (1.0 - beta) / (1.0 + beta);
+        c2 = c->dt / (1.0 + beta);
+    }
+    const int par = c->cur ^ (k & 1);
+    if (c->form == kFP64) {
+        StepArgs<double> a = make_args<double>(c);
+        a.ug_cur = (const double *)c->ug[par];
+        a.ug_next = (double *)c->ug[par ^ 1];
+        a.k_off = k;
+        a.c1 = c1;
+        a.c2 = c2;
+        return launch_step<double>(c->form, a, false, s, &c->plan);
+    }
+    StepArgs<float> a = make_args<float>(c);
+    a.ug_cur = (const float *)c->ug[par];
+    a.ug_next = (float *)c->ug[par ^ 1];
+    a.k_off = k;
+    a.c1 = c1;
+    a.c2 = c2;
+    return launch_step<float>(c->form, a, false, s, &c->plan);
+}
+
+int run_steps(ens_ctx *c, int64_t n) {
     const cudaError_t stale = cudaGetLastError();
     if (stale != cudaSuccess)
         return fail(c, ENS_ERR_CUDA, "error pending before the step launches: %s",
                     cudaGetErrorString(stale));
+    const int cur0 = c->cur;
     for (int64_t k = 0; k < n; k++) {
-        double c1, c2;
-        if (!c->started && k == 0) {  // Taylor start: v_{1/2} = (1 - beta) v_0 + dt/2 a_0
-            c1 = 1.0 - beta;
-            c2 = 0.5 * c->dt;
-        } else {
-            c1 = (1.0 - beta) / (1.0 + beta);
-            c2 = c->dt / (1.0 + beta);
-        }
-        cudaError_t e;
-        if (c->form == kFP64) {
-            StepArgs<double> a = make_args<double>(c);
-            a.ug_cur = (const double *)c->ug[c->cur];
-            a.ug_next = (double *)c->ug[c->cur ^ 1];
-            a.k_off = (int32_t)k;
-            a.c1 = c1;
-            a.c2 = c2;
-            e = launch_step<double>(c->form, a, false, c->stream, &c->plan);
-        } else {
-            StepArgs<float> a = make_args<float>(c);
-            a.ug_cur = (const float *)c->ug[c->cur];
-            a.ug_next = (float *)c->ug[c->cur ^ 1];
-            a.k_off = (int32_t)k;
-            a.c1 = c1;
-            a.c2 = c2;
-            e = launch_step<float>(c->form, a, false, c->stream, &c->plan);
-        }
-        if (e != cudaSuccess)
+        const cudaError_t e = launch_chunk_step(c, (int32_t)k, !c->started && k == 0, c->stream);
+        if (e != cudaSuccess) {
+            c->cur = cur0 ^ (int)(k & 1);
             return fail(c, ENS_ERR_CUDA, "step launch (variant staged=%d block=%d): %s [%s]",
                         c->plan.staged, c->plan.block, cudaGetErrorString(e), last_launch_note());
-        c->cur ^= 1;
+        }
     }
+    c->cur = cur0 ^ (int)(n & 1);
     return ENS_OK;
 }
 
@@ -258,6 +266,9 @@ int ctx_fail(ens_ctx *c, int code, const char *fmt, ...) {
     return code;
 }
 void *ctx_alloc(ens_ctx *c, size_t bytes) { return dev_alloc(c, bytes); }
+cudaError_t ctx_launch_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s) {
+    return launch_chunk_step(c, k, start, s);
+}
 void ctx_free(ens_ctx *c, void *p) { dev_free(c, p); }
 }  // namespace ens
 

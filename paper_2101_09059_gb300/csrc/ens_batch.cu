@@ -20,7 +20,7 @@ struct ens_batch {
     int block = 256;
     int graph_steps = 20;
     int coop_grid[2] = {0, 0};  // co-resident blocks of the persistent kernel (256, 128)
-    float mode_us[4] = {0, 0, 0, 0};
+    float mode_us[5] = {0, 0, 0, 0, 0};
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     std::string err;
@@ -33,6 +33,8 @@ struct ens_batch {
     unsigned *bar = nullptr;
     int *h_flags = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per block shape
+    cudaGraphExec_t seq_graph = nullptr;             // sequence mode
+    std::vector<uintptr_t> seq_key;
 };
 
 namespace {
@@ -131,8 +133,77 @@ void advance_members(ens_batch *b, int64_t n) {
 
 // Run n steps in the given mode and shape; on return the host bookkeeping is updated and
 // the step counters advanced (asynchronously).
+// Sequence mode: every member's own (autotuned, staged) step kernel, back to back per
+// step, with the time loop captured in a graph. The graph bakes each member's buffer
+// parity, so it is rebuilt when a member's parity changed since the capture.
+int run_sequence(ens_batch *b, int64_t n, bool tuning) {
+    const int32_t nm = (int32_t)b->m.size();
+    int64_t left = n;
+    bool any_first = false;
+    for (ens_ctx *c : b->m) any_first |= (!tuning && !c->started);
+    if (any_first) {
+        for (ens_ctx *c : b->m) BCK(ctx_launch_step(c, 0, !c->started, b->stream));
+        BCK(launch_advance_many(b->ctrs_d, nm, 1, b->stream));
+        advance_members(b, 1);
+        left -= 1;
+    }
+    const int K = b->graph_steps;
+    // everything the graph bakes into kernel parameters: parities and traction buffers
+    std::vector<uintptr_t> key;
+    for (ens_ctx *c : b->m) {
+        key.push_back((uintptr_t)(c->cur & 1));
+        key.push_back((uintptr_t)c->amp);
+        key.push_back((uintptr_t)c->modes);
+        key.push_back((uintptr_t)(tuning ? 0 : c->J));
+    }
+    if (left >= K && (!b->seq_graph || b->seq_key != key)) {
+        if (b->seq_graph) cudaGraphExecDestroy(b->seq_graph);
+        b->seq_graph = nullptr;
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        std::vector<int> saved_J(nm);
+        for (int32_t m = 0; m < nm; m++) {
+            saved_J[m] = b->m[m]->J;
+            if (tuning) b->m[m]->J = 0;  // timing runs apply no load
+        }
+        for (int k = 0; k < K && e == cudaSuccess; k++)
+            for (int32_t m = 0; m < nm && e == cudaSuccess; m++) e = ctx_launch_step(b->m[m], k, false, b->stream);
+        for (int32_t m = 0; m < nm; m++) b->m[m]->J = saved_J[m];
+        if (e == cudaSuccess) e = launch_advance_many(b->ctrs_d, nm, K, b->stream);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return bfail(b, ENS_ERR_CUDA, "sequence graph capture", e != cudaSuccess ? e : e2);
+        e = cudaGraphInstantiate(&b->seq_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, ENS_ERR_CUDA, "sequence graph instantiate", e);
+        b->seq_key = key;
+    }
+    while (left >= K) {
+        BCK(cudaGraphLaunch(b->seq_graph, b->stream));
+        advance_members(b, K);
+        left -= K;
+    }
+    if (left > 0) {
+        std::vector<int> saved_J(nm);
+        for (int32_t m = 0; m < nm; m++) {
+            saved_J[m] = b->m[m]->J;
+            if (tuning) b->m[m]->J = 0;
+        }
+        cudaError_t e = cudaSuccess;
+        for (int32_t k = 0; k < (int32_t)left && e == cudaSuccess; k++)
+            for (int32_t m = 0; m < nm && e == cudaSuccess; m++) e = ctx_launch_step(b->m[m], k, false, b->stream);
+        for (int32_t m = 0; m < nm; m++) b->m[m]->J = saved_J[m];
+        BCK(e);
+        BCK(launch_advance_many(b->ctrs_d, nm, left, b->stream));
+        advance_members(b, left);
+    }
+    return ENS_OK;
+}
+
 int run(ens_batch *b, int mode, int block, int64_t n, bool tuning) {
     if (n <= 0) return ENS_OK;
+    if (mode == ENS_BATCH_SEQUENCE) return run_sequence(b, n, tuning);
     int rc = upload(b, tuning);
     if (rc != ENS_OK) return rc;
     const int32_t nm = (int32_t)b->m.size();
@@ -242,11 +313,12 @@ int autotune(ens_batch *b) {
     if (rc == ENS_OK) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        const int modes[4] = {ENS_BATCH_GRAPH, ENS_BATCH_GRAPH, ENS_BATCH_PERSISTENT, ENS_BATCH_PERSISTENT};
-        const int blocks[4] = {256, 128, 256, 128};
+        const int modes[5] = {ENS_BATCH_GRAPH, ENS_BATCH_GRAPH, ENS_BATCH_PERSISTENT,
+                              ENS_BATCH_PERSISTENT, ENS_BATCH_SEQUENCE};
+        const int blocks[5] = {256, 128, 256, 128, 0};
         float best = -1.0f;
         const int steps = 2 * b->graph_steps;
-        for (int v = 0; v < 4 && rc == ENS_OK; v++) {
+        for (int v = 0; v < 5 && rc == ENS_OK; v++) {
             if (modes[v] == ENS_BATCH_PERSISTENT && b->coop_grid[idx_of(blocks[v])] <= 0) {
                 b->mode_us[v] = -1.0f;
                 continue;
@@ -307,6 +379,7 @@ void ens_batch_destroy(ens_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (auto &g : b->graph)
         if (g) cudaGraphExecDestroy(g);
+    if (b->seq_graph) cudaGraphExecDestroy(b->seq_graph);
     if (!b->m.empty()) {
         ens_ctx *c0 = b->m[0];
         ctx_free(c0, b->mem_d);
@@ -327,7 +400,7 @@ const char *ens_batch_last_error(const ens_batch *b) { return b ? b->err.c_str()
 int ens_batch_create(ens_ctx *const *members, int32_t n, int32_t mode, ens_batch **out) {
     if (!out) return ENS_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!members || n < 1 || mode < ENS_BATCH_AUTO || mode > ENS_BATCH_PERSISTENT)
+    if (!members || n < 1 || mode < ENS_BATCH_AUTO || mode > ENS_BATCH_SEQUENCE)
         return ENS_ERR_INVALID_ARG;
     for (int32_t k = 0; k < n; k++) {
         if (!members[k]) return ENS_ERR_INVALID_ARG;
@@ -427,7 +500,7 @@ int ens_batch_info(const ens_batch *b, ens_batch_info_t *info) {
     r.graph_steps = b->graph_steps;
     r.n_tiles = b->n_items[idx_of(b->block)];
     r.persistent_grid = b->coop_grid[idx_of(b->block)];
-    for (int k = 0; k < 4; k++) r.mode_us[k] = b->mode_us[k];
+    for (int k = 0; k < 5; k++) r.mode_us[k] = b->mode_us[k];
     double bytes = 0.0;
     for (ens_ctx *c : b->m) {
         ens_info_t i{};

@@ -56,6 +56,8 @@ namespace ens {
 int ctx_fail(ens_ctx *c, int code, const char *fmt, ...);
 void *ctx_alloc(ens_ctx *c, size_t bytes);
 void ctx_free(ens_ctx *c, void *p);
+// Launch step k of a chunk starting at the context's current buffer (context unchanged).
+cudaError_t ctx_launch_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s);
 inline size_t elem_size(int form) { return form == kFP64 ? 8 : 4; }
 
 template <typename R>

@@ -1,0 +1,557 @@
+// Surrogate network on the GPU: a GELU multilayer perceptron (n_in -> H -> H -> n_out)
+// trained with mean-squared error and Adam, every step in this file's kernels.
+//
+// Matrix products run on the tensor cores in BF16 with FP32 accumulation (warp-level
+// mma m16n8k16); master weights, activations, gradients and optimiser state stay FP32.
+// One training epoch (gather of each shuffled mini-batch, forward, loss, backward, Adam)
+// is captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/sur.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32;  // block tile
+constexpr int LDS = BK + 8;                // padded smem row (bf16 elements)
+constexpr int kThreads = 128;              // 4 warps, 2 x 2, each 32 x 32
+
+enum Epi : int {
+    kStore = 0,      // C = acc
+    kBiasStore = 1,  // C = acc + bias[n]
+    kBiasGelu = 2,   // Z = acc + bias[n]; C = gelu(Z) (Z kept for the backward pass)
+    kGeluGrad = 3,   // C = acc * gelu'(Z[m][n])
+};
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+           z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[M][N] (row stride ldc) = epilogue( sum_k A(m, k) B(k, n) ), FP32 sources staged to BF16.
+// A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn]. Out-of-range elements
+// are read as zero and not written.
+template <int EPI>
+__global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, const float *__restrict__ A,
+                                                        long long sam, long long sak,
+                                                        const float *__restrict__ B, long long sbk,
+                                                        long long sbn, float *__restrict__ C, int ldc,
+                                                        const float *__restrict__ bias,
+                                                        float *__restrict__ Z) {
+    __shared__ __align__(16) __nv_bfloat16 As[BM][LDS];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][LDS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[i][j][r] = 0.0f;
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        // stage A tile (BM x BK) and B tile (BN x BK), walking the contiguous index fastest
+        for (int e = tid; e < BM * BK; e += kThreads) {
+            int mm, kk;
+            if (sak == 1) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+            const int m = m0 + mm, k = k0 + kk;
+            const float v = (m < M && k < K) ? A[(long long)m * sam + (long long)k * sak] : 0.0f;
+            As[mm][kk] = __float2bfloat16_rn(v);
+        }
+        for (int e = tid; e < BN * BK; e += kThreads) {
+            int nn, kk;
+            if (sbk == 1) { nn = e / BK; kk = e % BK; } else { nn = e % BN; kk = e / BN; }
+            const int n = n0 + nn, k = k0 + kk;
+            const float v = (n < N && k < K) ? B[(long long)k * sbk + (long long)n * sbn] : 0.0f;
+            Bs[nn][kk] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int r = wm + 16 * i;
+                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r + g][ks + 2 * t]);
+                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + g + 8][ks + 2 * t]);
+                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r + g][ks + 2 * t + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + g + 8][ks + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int c = wn + 8 * j;
+                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c + g][ks + 2 * t]);
+                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c + g][ks + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue: acc[i][j] = {C[g][2t], C[g][2t+1], C[g+8][2t], C[g+8][2t+1]} of its 16 x 8 tile
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int m = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * t + (r & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][r];
+                const long long o = (long long)m * ldc + n;
+                if constexpr (EPI == kBiasStore) v += bias[n];
+                if constexpr (EPI == kBiasGelu) {
+                    v += bias[n];
+                    Z[o] = v;
+                    v = gelu(v);
+                }
+                if constexpr (EPI == kGeluGrad) v *= gelu_grad(Z[o]);
+                C[o] = v;
+            }
+}
+
+// loss = sum (y - t)^2 / count (one block, fixed order); dy = 2 (y - t) / count.
+__global__ void mse_kernel(const float *__restrict__ y, const float *__restrict__ tgt, long long count,
+                           float *__restrict__ dy, float *__restrict__ loss_out) {
+    __shared__ double part[256];
+    double s = 0.0;
+    const float scale = 2.0f / (float)count;
+    for (long long i = threadIdx.x; i < count; i += blockDim.x) {
+        const float d = y[i] - tgt[i];
+        if (dy) dy[i] = scale * d;
+        s += (double)d * (double)d;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss_out) *loss_out = (float)(part[0] / (double)count);
+}
+
+// db[n] = sum_m dz[m][n] (one thread per column, fixed order).
+__global__ void colsum_kernel(const float *__restrict__ dz, int M, int N, float *__restrict__ db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int m = 0; m < M; m++) s += dz[(long long)m * N + n];
+    db[n] = s;
+}
+
+// rows of a mini-batch: dst[i][:] = src[perm[off + i]][:]
+__global__ void gather_rows_kernel(const float *__restrict__ src, const int *__restrict__ perm, int off,
+                                   int rows, int cols, float *__restrict__ dst) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * cols) return;
+    const int i = (int)(e / cols), c = (int)(e % cols);
+    dst[e] = src[(long long)perm[off + i] * cols + c];
+}
+
+__global__ void tick_kernel(int *t) { *t += 1; }
+
+// Adam (bias-corrected): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, long long n, const int *__restrict__ tstep, float lr,
+                            float b1, float b2, float eps) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float t = (float)*tstep;
+    const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// u[b][d] = mean[d] + sum_r c[b][r] phi[d][r]  (POD reconstruction, FP32)
+__global__ void reconstruct_kernel(const float *__restrict__ c, const float *__restrict__ mean,
+                                   const float *__restrict__ phi, int B, long long D, int r,
+                                   float *__restrict__ u) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)B * D) return;
+    const int b = (int)(e / D);
+    const long long d = e % D;
+    float s = mean[d];
+    for (int k = 0; k < r; k++) s = fmaf(c[(long long)b * r + k], phi[d * r + k], s);
+    u[e] = s;
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+long long float_bits(float f) {
+    int32_t i;
+    memcpy(&i, &f, sizeof(i));
+    return i;
+}
+
+template <int EPI>
+cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float *A, long long sam, long long sak,
+                 const float *B, long long sbk, long long sbn, float *C, int ldc,
+                 const float *bias = nullptr, float *Z = nullptr) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid(cdiv(N, BN), cdiv(M, BM));
+    gemm_kernel<EPI><<<grid, kThreads, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, Z);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+struct sur_ctx {
+    int nin = 0, H = 0, nout = 0, max_batch = 0;
+    long long np = 0;  // parameter count
+    long long off[6] = {0, 0, 0, 0, 0, 0};  // W1 b1 W2 b2 W3 b3 in the flat vectors
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream for graph capture
+    std::string err;
+    float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    // device buffers
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    float *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *y = nullptr;
+    float *dy = nullptr, *d2 = nullptr, *d1 = nullptr;
+    float *xb = nullptr, *tb = nullptr, *loss = nullptr;
+    int *tstep = nullptr, *perm = nullptr;
+    long long perm_n = 0;
+    float *loss_hist = nullptr;
+    long long loss_hist_n = 0;
+    cudaGraphExec_t epoch_graph = nullptr;
+    long long graph_key[5] = {0, 0, 0, 0, 0};
+    std::vector<void *> bufs;
+};
+
+namespace {
+
+int sfail(sur_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[400];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define SCK(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return sfail(c, SUR_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+int salloc(sur_ctx *c, T **p, long long n) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(c, SUR_ERR_ALLOC, "cudaMalloc of %lld elements", n);
+    }
+    c->bufs.push_back(q);
+    *p = (T *)q;
+    return SUR_OK;
+}
+
+// Forward pass of B rows already in x (device): z1, a1, z2, a2, y.
+int forward(sur_ctx *c, cudaStream_t s, const float *x, int B) {
+    const float *W1 = c->p + c->off[0], *b1 = c->p + c->off[1], *W2 = c->p + c->off[2];
+    const float *b2 = c->p + c->off[3], *W3 = c->p + c->off[4], *b3 = c->p + c->off[5];
+    const int H = c->H;
+    SCK((gemm<kBiasGelu>(s, B, H, c->nin, x, c->nin, 1, W1, 1, c->nin, c->a1, H, b1, c->z1)));
+    SCK((gemm<kBiasGelu>(s, B, H, H, c->a1, H, 1, W2, 1, H, c->a2, H, b2, c->z2)));
+    SCK((gemm<kBiasStore>(s, B, c->nout, H, c->a2, H, 1, W3, 1, H, c->y, c->nout, b3)));
+    return SUR_OK;
+}
+
+// Loss and gradients of B rows (x, t on device) into c->g; loss to *loss_dev.
+int backward(sur_ctx *c, cudaStream_t s, const float *x, const float *t, int B, float *loss_dev) {
+    const int H = c->H, no = c->nout, ni = c->nin;
+    const float *W2 = c->p + c->off[2], *W3 = c->p + c->off[4];
+    float *gW1 = c->g + c->off[0], *gb1 = c->g + c->off[1], *gW2 = c->g + c->off[2];
+    float *gb2 = c->g + c->off[3], *gW3 = c->g + c->off[4], *gb3 = c->g + c->off[5];
+    int rc = forward(c, s, x, B);
+    if (rc != SUR_OK) return rc;
+    mse_kernel<<<1, 256, 0, s>>>(c->y, t, (long long)B * no, c->dy, loss_dev);
+    SCK(cudaGetLastError());
+    // layer 3: dW3 = dy^T a2, db3 = colsum dy, d2 = (dy W3) * gelu'(z2)
+    SCK((gemm<kStore>(s, no, H, B, c->dy, 1, no, c->a2, H, 1, gW3, H)));
+    colsum_kernel<<<cdiv(no, 128), 128, 0, s>>>(c->dy, B, no, gb3);
+    SCK((gemm<kGeluGrad>(s, B, H, no, c->dy, no, 1, W3, H, 1, c->d2, H, nullptr, c->z2)));
+    // layer 2
+    SCK((gemm<kStore>(s, H, H, B, c->d2, 1, H, c->a1, H, 1, gW2, H)));
+    colsum_kernel<<<cdiv(H, 128), 128, 0, s>>>(c->d2, B, H, gb2);
+    SCK((gemm<kGeluGrad>(s, B, H, H, c->d2, H, 1, W2, H, 1, c->d1, H, nullptr, c->z1)));
+    // layer 1
+    SCK((gemm<kStore>(s, H, ni, B, c->d1, 1, H, x, ni, 1, gW1, ni)));
+    colsum_kernel<<<cdiv(H, 128), 128, 0, s>>>(c->d1, B, H, gb1);
+    SCK(cudaGetLastError());
+    return SUR_OK;
+}
+
+int adam(sur_ctx *c, cudaStream_t s, float lr) {
+    tick_kernel<<<1, 1, 0, s>>>(c->tstep);
+    adam_kernel<<<cdiv(c->np, 256), 256, 0, s>>>(c->p, c->g, c->m, c->v, c->np, c->tstep, lr, c->b1,
+                                                c->b2, c->eps);
+    SCK(cudaGetLastError());
+    return SUR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sur_last_error(const sur_ctx *c) { return c ? c->err.c_str() : ""; }
+
+void sur_destroy(sur_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->epoch_graph) cudaGraphExecDestroy(c->epoch_graph);
+    for (void *p : c->bufs) cudaFree(p);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+int sur_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch, uint64_t seed,
+               void *stream, sur_ctx **out) {
+    if (!out) return SUR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_in < 1 || n_hidden < 1 || n_out < 1 || max_batch < 1 || n_in > 65536 || n_hidden > 65536 ||
+        n_out > 65536)
+        return SUR_ERR_INVALID_ARG;
+    sur_ctx *c = new (std::nothrow) sur_ctx();
+    if (!c) return SUR_ERR_ALLOC;
+    c->nin = n_in;
+    c->H = n_hidden;
+    c->nout = n_out;
+    c->max_batch = max_batch;
+    c->stream = (cudaStream_t)stream;
+    const long long sizes[6] = {(long long)n_hidden * n_in, n_hidden, (long long)n_hidden * n_hidden,
+                                n_hidden, (long long)n_out * n_hidden, n_out};
+    long long o = 0;
+    for (int k = 0; k < 6; k++) {
+        c->off[k] = o;
+        o += (sizes[k] + 3) / 4 * 4;  // 16-byte aligned tensors
+    }
+    c->np = o;
+    int rc = [&]() -> int {
+        int r;
+        const long long B = max_batch, H = n_hidden;
+        if ((r = salloc(c, &c->p, c->np)) || (r = salloc(c, &c->g, c->np)) || (r = salloc(c, &c->m, c->np)) ||
+            (r = salloc(c, &c->v, c->np)) || (r = salloc(c, &c->z1, B * H)) || (r = salloc(c, &c->a1, B * H)) ||
+            (r = salloc(c, &c->z2, B * H)) || (r = salloc(c, &c->a2, B * H)) ||
+            (r = salloc(c, &c->y, B * n_out)) || (r = salloc(c, &c->dy, B * n_out)) ||
+            (r = salloc(c, &c->d2, B * H)) || (r = salloc(c, &c->d1, B * H)) ||
+            (r = salloc(c, &c->xb, B * n_in)) || (r = salloc(c, &c->tb, B * n_out)) ||
+            (r = salloc(c, &c->loss, 1)) || (r = salloc(c, &c->tstep, 1)))
+            return r;
+        // Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation from a seeded generator.
+        std::vector<float> h(c->np, 0.0f);
+        std::mt19937_64 gen(seed);
+        const int fan[6] = {n_in, n_in, n_hidden, n_hidden, n_hidden, n_hidden};
+        for (int k = 0; k < 6; k++) {
+            std::uniform_real_distribution<float> U(-1.0f / std::sqrt((float)fan[k]), 1.0f / std::sqrt((float)fan[k]));
+            for (long long i = 0; i < sizes[k]; i++) h[c->off[k] + i] = U(gen);
+        }
+        SCK(cudaMemcpy(c->p, h.data(), sizeof(float) * c->np, cudaMemcpyHostToDevice));
+        SCK(cudaMemset(c->m, 0, sizeof(float) * c->np));
+        SCK(cudaMemset(c->v, 0, sizeof(float) * c->np));
+        SCK(cudaMemset(c->g, 0, sizeof(float) * c->np));
+        SCK(cudaMemset(c->tstep, 0, sizeof(int)));
+        SCK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        return SUR_OK;
+    }();
+    if (rc != SUR_OK) {
+        sur_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return SUR_OK;
+}
+
+int64_t sur_param_count(const sur_ctx *c) { return c ? (int64_t)c->np : -1; }
+
+int sur_param_offsets(const sur_ctx *c, int64_t *offsets6) {
+    if (!c || !offsets6) return SUR_ERR_INVALID_ARG;
+    for (int k = 0; k < 6; k++) offsets6[k] = c->off[k];
+    return SUR_OK;
+}
+
+int sur_set_params(sur_ctx *c, const float *host) {
+    if (!c || !host) return SUR_ERR_INVALID_ARG;
+    SCK(cudaMemcpyAsync(c->p, host, sizeof(float) * c->np, cudaMemcpyHostToDevice, c->stream));
+    SCK(cudaMemsetAsync(c->m, 0, sizeof(float) * c->np, c->stream));
+    SCK(cudaMemsetAsync(c->v, 0, sizeof(float) * c->np, c->stream));
+    SCK(cudaMemsetAsync(c->tstep, 0, sizeof(int), c->stream));
+    SCK(cudaStreamSynchronize(c->stream));
+    return SUR_OK;
+}
+
+int sur_get_params(sur_ctx *c, float *host) {
+    if (!c || !host) return SUR_ERR_INVALID_ARG;
+    SCK(cudaMemcpyAsync(host, c->p, sizeof(float) * c->np, cudaMemcpyDeviceToHost, c->stream));
+    SCK(cudaStreamSynchronize(c->stream));
+    return SUR_OK;
+}
+
+int sur_forward(sur_ctx *c, const float *x_dev, int64_t B, float *y_dev) {
+    if (!c || !x_dev || !y_dev || B < 0) return SUR_ERR_INVALID_ARG;
+    for (int64_t b0 = 0; b0 < B; b0 += c->max_batch) {
+        const int nb = (int)std::min<int64_t>(c->max_batch, B - b0);
+        int rc = forward(c, c->stream, x_dev + b0 * c->nin, nb);
+        if (rc != SUR_OK) return rc;
+        SCK(cudaMemcpyAsync(y_dev + b0 * c->nout, c->y, sizeof(float) * nb * c->nout,
+                            cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return SUR_OK;
+}
+
+int sur_loss_grad(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, float *loss_host,
+                  float *grad_host) {
+    if (!c || !x_dev || !t_dev || B < 1 || B > c->max_batch) return SUR_ERR_INVALID_ARG;
+    int rc = backward(c, c->stream, x_dev, t_dev, (int)B, c->loss);
+    if (rc != SUR_OK) return rc;
+    if (loss_host) SCK(cudaMemcpyAsync(loss_host, c->loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (grad_host)
+        SCK(cudaMemcpyAsync(grad_host, c->g, sizeof(float) * c->np, cudaMemcpyDeviceToHost, c->stream));
+    SCK(cudaStreamSynchronize(c->stream));
+    return SUR_OK;
+}
+
+int sur_adam_step(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, float lr) {
+    if (!c || !x_dev || !t_dev || B < 1 || B > c->max_batch) return SUR_ERR_INVALID_ARG;
+    int rc = backward(c, c->stream, x_dev, t_dev, (int)B, c->loss);
+    if (rc != SUR_OK) return rc;
+    return adam(c, c->stream, lr);
+}
+
+int sur_train(sur_ctx *c, const float *X_dev, const float *T_dev, int64_t n, int32_t batch,
+              int32_t epochs, float lr, uint64_t seed, float *loss_host) {
+    if (!c || !X_dev || !T_dev || n < 1 || batch < 1 || batch > c->max_batch || epochs < 0)
+        return SUR_ERR_INVALID_ARG;
+    const long long steps = n / batch;  // full mini-batches per epoch (the remainder is dropped)
+    if (steps < 1) return sfail(c, SUR_ERR_INVALID_ARG, "fewer rows (%lld) than one mini-batch", (long long)n);
+    if (c->perm_n < n) {
+        int r = salloc(c, &c->perm, n);
+        if (r) return r;
+        c->perm_n = n;
+    }
+    if (c->loss_hist_n < steps) {
+        int r = salloc(c, &c->loss_hist, steps);
+        if (r) return r;
+        c->loss_hist_n = steps;
+    }
+    const long long key[5] = {(long long)(size_t)X_dev, (long long)(size_t)T_dev, n, batch,
+                              float_bits(lr)};
+    bool same = c->epoch_graph != nullptr;
+    for (int k = 0; k < 5; k++) same = same && key[k] == c->graph_key[k];
+    if (!same) {
+        if (c->epoch_graph) cudaGraphExecDestroy(c->epoch_graph);
+        c->epoch_graph = nullptr;
+        cudaGraph_t g = nullptr;
+        SCK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = SUR_OK;
+        for (long long st = 0; st < steps && rc == SUR_OK; st++) {
+            gather_rows_kernel<<<cdiv((long long)batch * c->nin, 256), 256, 0, c->cap>>>(
+                X_dev, c->perm, (int)(st * batch), batch, c->nin, c->xb);
+            gather_rows_kernel<<<cdiv((long long)batch * c->nout, 256), 256, 0, c->cap>>>(
+                T_dev, c->perm, (int)(st * batch), batch, c->nout, c->tb);
+            rc = backward(c, c->cap, c->xb, c->tb, batch, c->loss_hist + st);
+            if (rc == SUR_OK) rc = adam(c, c->cap, lr);
+        }
+        cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        if (rc != SUR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return sfail(c, SUR_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->epoch_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return sfail(c, SUR_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+        for (int k = 0; k < 5; k++) c->graph_key[k] = key[k];
+    }
+    std::mt19937_64 gen(seed);
+    std::vector<int> perm(n);
+    std::vector<float> hist(steps);
+    for (int ep = 0; ep < epochs; ep++) {
+        for (long long i = 0; i < n; i++) perm[i] = (int)i;
+        for (long long i = n - 1; i > 0; i--) {  // Fisher-Yates with the seeded generator
+            std::uniform_int_distribution<long long> U(0, i);
+            std::swap(perm[i], perm[U(gen)]);
+        }
+        SCK(cudaMemcpyAsync(c->perm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+        SCK(cudaGraphLaunch(c->epoch_graph, c->stream));
+        if (loss_host) {
+            SCK(cudaMemcpyAsync(hist.data(), c->loss_hist, sizeof(float) * steps, cudaMemcpyDeviceToHost,
+                                c->stream));
+            SCK(cudaStreamSynchronize(c->stream));
+            double s = 0.0;
+            for (float x : hist) s += x;
+            loss_host[ep] = (float)(s / steps);
+        }
+    }
+    SCK(cudaStreamSynchronize(c->stream));
+    return SUR_OK;
+}
+
+int sur_loss(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, float *loss_host) {
+    if (!c || !x_dev || !t_dev || B < 1 || !loss_host) return SUR_ERR_INVALID_ARG;
+    double acc = 0.0;
+    for (int64_t b0 = 0; b0 < B; b0 += c->max_batch) {
+        const int nb = (int)std::min<int64_t>(c->max_batch, B - b0);
+        int rc = forward(c, c->stream, x_dev + b0 * c->nin, nb);
+        if (rc != SUR_OK) return rc;
+        mse_kernel<<<1, 256, 0, c->stream>>>(c->y, t_dev + b0 * c->nout, (long long)nb * c->nout, nullptr,
+                                             c->loss);
+        float l = 0.0f;
+        SCK(cudaMemcpyAsync(&l, c->loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        SCK(cudaStreamSynchronize(c->stream));
+        acc += (double)l * nb;
+    }
+    *loss_host = (float)(acc / B);
+    return SUR_OK;
+}
+
+int sur_reconstruct(const float *coef_dev, const float *mean_dev, const float *phi_dev, int32_t B,
+                    int64_t D, int32_t r, float *u_dev, void *stream) {
+    if (!coef_dev || !mean_dev || !phi_dev || !u_dev || B < 0 || D < 0 || r < 1) return SUR_ERR_INVALID_ARG;
+    reconstruct_kernel<<<cdiv((long long)B * D, 256), 256, 0, (cudaStream_t)stream>>>(coef_dev, mean_dev, phi_dev,
+                                                                                      B, D, r, u_dev);
+    return cudaGetLastError() == cudaSuccess ? SUR_OK : SUR_ERR_CUDA;
+}
+
+int sur_matmul(const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn,
+               float *C, int32_t M, int32_t N, int32_t K, int32_t ldc, void *stream) {
+    if (!A || !B || !C || M < 0 || N < 0 || K < 0 || ldc < N) return SUR_ERR_INVALID_ARG;
+    return gemm<kStore>((cudaStream_t)stream, M, N, K, A, sam, sak, B, sbk, sbn, C, ldc) == cudaSuccess
+               ? SUR_OK
+               : SUR_ERR_CUDA;
+}
+
+}  // extern "C"

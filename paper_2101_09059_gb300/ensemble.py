@@ -218,7 +218,7 @@ class Ensemble:
         return out
 
 
-BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
+BATCH_AUTO, BATCH_GRAPH, BATCH_PERSISTENT, BATCH_SEQUENCE = 0, 1, 2, 3
 
 
 class Batch:

@@ -301,7 +301,8 @@ def _batch_cases(sizes, widths):
 
 
 @pytest.mark.parametrize("precision", ["kahan32", "fp32_force", "fp64"])
-@pytest.mark.parametrize("mode", [ens.BATCH_GRAPH, ens.BATCH_PERSISTENT, ens.BATCH_AUTO])
+@pytest.mark.parametrize("mode", [ens.BATCH_GRAPH, ens.BATCH_PERSISTENT, ens.BATCH_SEQUENCE,
+                                  ens.BATCH_AUTO])
 def test_batched_members_equal_individual_runs(precision, mode):
     """Uneven members (different meshes, widths and time steps) advanced by one batched
     launch per step or by one persistent launch give bit for bit the trajectories of
@@ -320,7 +321,7 @@ def test_batched_members_equal_individual_runs(precision, mode):
     members = [ens.Ensemble.from_case(c, precision=precision) for c in cases]
     with ens.Batch(members, mode=mode) as b:
         info = b.info()
-        assert info["n_members"] == 4 and info["mode"] in (1, 2)
+        assert info["n_members"] == 4 and info["mode"] in (1, 2, 3)
         b.step(53)     # start step + two graph replays + a remainder of 12
         b.step(20)
     for m, ref in zip(members, solo):

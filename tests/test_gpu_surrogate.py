@@ -1,0 +1,113 @@
+"""GPU surrogate network (BF16 tensor-core products, FP32 state) against the FP64
+oracle network (oracle/mlp.py).
+
+Tolerances: the products round their inputs to BF16 (8 significant bits, relative
+error 2^-9 per input), so outputs and gradients agree with the FP64 oracle to about
+1e-2 relative; tests use 3e-2 (relative L2 per tensor)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2101_09059_gb300 as ens  # noqa: E402
+from paper_2101_09059_gb300 import surrogate as sur  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ens.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - np.asarray(b, float)) / np.linalg.norm(np.asarray(b, float)))
+
+
+def _data(B, n_in=64, n_out=32, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((B, n_in))
+    t = np.tanh(x[:, :n_out] * 0.7) + 0.1 * x[:, n_out:2 * n_out] ** 2 if n_in >= 2 * n_out else rng.standard_normal((B, n_out))
+    return x, t
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("B", [1, 37, 256, 1000])
+def test_forward_matches_oracle(B):
+    net = sur.Surrogate(64, 256, 32, max_batch=1024, seed=3)
+    P = net.params()
+    x, _ = _data(B)
+    y = net.forward(_dev(x)).cpu().numpy()
+    y_ref, _ = mlp.forward(P, x.astype(np.float32).astype(np.float64))
+    assert rel(y, y_ref) < 3e-2
+    net.close()
+
+
+def test_gradients_match_oracle():
+    net = sur.Surrogate(64, 256, 32, max_batch=512, seed=5)
+    P = net.params()
+    x, t = _data(300, seed=2)
+    loss, g = net.loss_grad(_dev(x), _dev(t))
+    L_ref, g_ref = mlp.gradients(P, x.astype(np.float32).astype(np.float64), t.astype(np.float32).astype(np.float64))
+    assert loss == pytest.approx(L_ref, rel=3e-2)
+    for k, (a, b) in enumerate(zip(g, g_ref)):
+        assert rel(a, b) < 3e-2, k
+    net.close()
+
+
+def test_adam_first_step():
+    net = sur.Surrogate(64, 256, 32, max_batch=512, seed=7)
+    P0 = net.params()
+    x, t = _data(256, seed=4)
+    _, g = net.loss_grad(_dev(x), _dev(t))
+    net.adam_step(_dev(x), _dev(t), 1e-3)
+    P1 = net.params()
+    for a, b, gg in zip(P1, P0, g):
+        d = a - b
+        # the first bias-corrected Adam step is exactly -lr * g / (|g| + eps)
+        expect = -1e-3 * gg / (np.abs(gg) + 1e-8)
+        assert np.allclose(d, expect, rtol=2e-3, atol=2e-9)
+    net.close()
+
+
+def test_training_reduces_loss_like_the_oracle():
+    x, t = _data(2048, seed=9)
+    net = sur.Surrogate(64, 256, 32, max_batch=2048, seed=11)
+    P = net.params()
+    X, T = _dev(x), _dev(t)
+    l0 = net.loss(X, T)
+    hist = net.train(X, T, epochs=30, batch=256, lr=1e-3, seed=1)
+    l1 = net.loss(X, T)
+    assert hist.shape == (30,) and np.all(np.isfinite(hist))
+    assert l1 < 0.2 * l0
+    # the FP64 oracle, same initial weights and data, full-batch Adam for a few steps,
+    # ends at a loss of the same order
+    opt = mlp.Adam(P, lr=1e-3)
+    xr, tr = x.astype(np.float32).astype(np.float64), t.astype(np.float32).astype(np.float64)
+    for _ in range(240):
+        _, gr = mlp.gradients(P, xr, tr)
+        opt.step(P, gr)
+    l_ref = mlp.loss(P, xr, tr)
+    assert l1 < 5 * l_ref + 1e-3
+    net.close()
+
+
+def test_matmul_and_reconstruct():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((300, 1111))
+    B = rng.standard_normal((1111, 40))
+    C = sur.matmul(_dev(A), _dev(B)).cpu().numpy()
+    assert rel(C, A @ B) < 1e-2
+    Ct = sur.matmul(_dev(A.T.copy()), _dev(B.T.copy()), transpose_a=True, transpose_b=True).cpu().numpy()
+    assert rel(Ct, A @ B) < 1e-2
+    coef = rng.standard_normal((7, 5))
+    mean = rng.standard_normal(1234)
+    phi = rng.standard_normal((1234, 5))
+    u = sur.reconstruct(_dev(coef), _dev(mean), _dev(phi)).cpu().numpy()
+    assert rel(u, mean[None, :] + coef @ phi.T) < 1e-6
