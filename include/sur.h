@@ -71,6 +71,14 @@ int sur_train(sur_ctx *c, const float *X_dev, const float *T_dev, int64_t n, int
 int sur_reconstruct(const float *coef_dev, const float *mean_dev, const float *phi_dev, int32_t B,
                     int64_t D, int32_t r, float *u_dev, void *stream);
 
+/* Statistics of the fields u = mean + phi c implied by M predicted coefficient rows
+ * coef_dev [M][r] (1 <= r <= 64): out_mean [D] = mean + phi mu_c and out_std [D] =
+ * sqrt(diag(phi C_c phi^T)) with mu_c, C_c the coefficients' sample mean and covariance
+ * (divisor M - 1). work_dev: device scratch of r + r * r floats.                        */
+int sur_field_stats(const float *coef_dev, int32_t M, int32_t r, const float *mean_dev,
+                    const float *phi_dev, int64_t D, float *work_dev, float *out_mean_dev,
+                    float *out_std_dev, void *stream);
+
 /* General product on the tensor cores (BF16 inputs, FP32 accumulation):
  * C[m][n] (row stride ldc) = sum_k A[m sam + k sak] B[k sbk + n sbn]; used for POD
  * projections, coefficients = (u - mean) phi.                                            */

@@ -205,6 +205,50 @@ __global__ void reconstruct_kernel(const float *__restrict__ c, const float *__r
     u[e] = s;
 }
 
+// Mean of each coefficient column: mu[i] = sum_m c[m][i] / M (one thread per column).
+__global__ void coef_mean_kernel(const float *__restrict__ c, int M, int r, float *__restrict__ mu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    double s = 0.0;
+    for (int m = 0; m < M; m++) s += c[(long long)m * r + i];
+    mu[i] = (float)(s / M);
+}
+
+// Sample covariance of the coefficients, C[i][j] = sum_m (c_i - mu_i)(c_j - mu_j) / (M - 1).
+__global__ void coef_cov_kernel(const float *__restrict__ c, int M, int r, const float *__restrict__ mu,
+                                float *__restrict__ C) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r * r) return;
+    const int i = e / r, j = e % r;
+    double s = 0.0;
+    for (int m = 0; m < M; m++)
+        s += ((double)c[(long long)m * r + i] - mu[i]) * ((double)c[(long long)m * r + j] - mu[j]);
+    C[e] = M > 1 ? (float)(s / (M - 1)) : 0.0f;
+}
+
+// Field statistics implied by the coefficient statistics: mean[d] = u0[d] + phi[d] . mu,
+// std[d] = sqrt(phi[d]^T C phi[d]).
+__global__ void field_stats_kernel(const float *__restrict__ u0, const float *__restrict__ phi, long long D,
+                                   int r, const float *__restrict__ mu, const float *__restrict__ C,
+                                   float *__restrict__ mean, float *__restrict__ stdv) {
+    extern __shared__ float sh[];  // mu [r], C [r][r]
+    for (int e = threadIdx.x; e < r + r * r; e += blockDim.x) sh[e] = e < r ? mu[e] : C[e - r];
+    __syncthreads();
+    const long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= D) return;
+    const float *p = phi + d * r;
+    float m = u0[d], v = 0.0f;
+    for (int i = 0; i < r; i++) {
+        const float pi = p[i];
+        m = fmaf(pi, sh[i], m);
+        float t = 0.0f;
+        for (int j = 0; j < r; j++) t = fmaf(sh[r + i * r + j], p[j], t);
+        v = fmaf(pi, t, v);
+    }
+    mean[d] = m;
+    stdv[d] = sqrtf(fmaxf(v, 0.0f));
+}
+
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 long long float_bits(float f) {
@@ -543,6 +587,20 @@ int sur_reconstruct(const float *coef_dev, const float *mean_dev, const float *p
     if (!coef_dev || !mean_dev || !phi_dev || !u_dev || B < 0 || D < 0 || r < 1) return SUR_ERR_INVALID_ARG;
     reconstruct_kernel<<<cdiv((long long)B * D, 256), 256, 0, (cudaStream_t)stream>>>(coef_dev, mean_dev, phi_dev,
                                                                                       B, D, r, u_dev);
+    return cudaGetLastError() == cudaSuccess ? SUR_OK : SUR_ERR_CUDA;
+}
+
+int sur_field_stats(const float *coef_dev, int32_t M, int32_t r, const float *mean_dev, const float *phi_dev,
+                    int64_t D, float *work_dev, float *out_mean_dev, float *out_std_dev, void *stream) {
+    if (!coef_dev || !mean_dev || !phi_dev || !work_dev || !out_mean_dev || !out_std_dev || M < 1 || r < 1 ||
+        r > 64 || D < 0)
+        return SUR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *mu = work_dev, *C = work_dev + r;
+    coef_mean_kernel<<<1, 64, 0, s>>>(coef_dev, M, r, mu);
+    coef_cov_kernel<<<cdiv((long long)r * r, 256), 256, 0, s>>>(coef_dev, M, r, mu, C);
+    field_stats_kernel<<<cdiv(D, 256), 256, sizeof(float) * (r + r * r), s>>>(mean_dev, phi_dev, D, r, mu, C,
+                                                                              out_mean_dev, out_std_dev);
     return cudaGetLastError() == cudaSuccess ? SUR_OK : SUR_ERR_CUDA;
 }
 

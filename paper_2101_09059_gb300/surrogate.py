@@ -97,6 +97,15 @@ class Surrogate:
     def adam_step(self, x, t, lr):
         self._chk(self._L.sur_adam_step(self._c, _dp(x), _dp(t), x.shape[0], ctypes.c_float(lr)))
 
+    def scale_outputs(self, scale):
+        """Multiply the network's outputs by `scale` [n_out] by rescaling the last layer
+        (exact): used to undo the target standardisation after training."""
+        P = self.params()
+        sc = np.asarray(scale, dtype=np.float64)
+        P[4] = P[4] * sc[:, None]
+        P[5] = P[5] * sc
+        self.set_params(P)
+
     def train(self, X, T, epochs, batch=256, lr=1e-3, seed=0):
         _check_f32(X)
         _check_f32(T)
@@ -150,3 +159,58 @@ def reconstruct(coef, mean, phi, out=None, stream=None):
     if rc != 0:
         raise EnsError(rc, "sur_reconstruct failed")
     return out
+
+
+def field_stats(coef, mean, phi, stream=None):
+    """(mean [D], std [D]) of u = mean + phi c over the coefficient rows coef [M][r]."""
+    import torch
+    L = _lib.load()
+    M, r = coef.shape
+    D = mean.shape[0]
+    work = torch.empty(r + r * r, dtype=torch.float32, device=coef.device)
+    m_out = torch.empty(D, dtype=torch.float32, device=coef.device)
+    s_out = torch.empty(D, dtype=torch.float32, device=coef.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.sur_field_stats(_dp(coef), M, r, _dp(mean), _dp(phi), D, _dp(work), _dp(m_out), _dp(s_out),
+                           ctypes.c_void_p(s.cuda_stream))
+    if rc != 0:
+        raise EnsError(rc, "sur_field_stats failed")
+    return m_out, s_out
+
+
+# ---- pipeline: solver data -> POD -> training -> prediction ---------------------------
+
+def solver_fields(mesh, fields_for, n_runs, S, params, modes, amp, n_steps, precision="kahan32",
+                  stream=None, device=0):
+    """Final displacements [n_runs][3N] (float32) of n_runs realisations, S per launch;
+    fields_for(rows) returns the nodal (E, h) [N][len(rows)] of those realisations."""
+    from .ensemble import Ensemble
+    N = mesh.n_nodes
+    out = np.empty((n_runs, 3 * N), dtype=np.float32)
+    for r0 in range(0, n_runs, S):
+        rows = list(range(r0, min(n_runs, r0 + S)))
+        E, h = fields_for(rows)
+        with Ensemble(mesh.xyz, mesh.tri, mesh.fixed, E, h, precision=precision, stream=stream,
+                      device=device, **params) as e:
+            e.set_traction(modes, amp)
+            e.step(n_steps)
+            out[r0:r0 + len(rows)] = e.displacement("snc").reshape(len(rows), -1)
+    return out
+
+
+def pod(snapshots, r):
+    """POD of snapshot rows: (mean [D], modes phi [D][r] orthonormal, coefficients [n][r],
+    captured fraction of the fluctuation energy). Host linear algebra (set-up, not the
+    time loop): eigenpairs of the snapshot Gram matrix."""
+    X = np.asarray(snapshots, dtype=np.float32)
+    mean = X.mean(axis=0, dtype=np.float64)
+    Xc = X - mean.astype(np.float32)[None, :]
+    G = (Xc @ Xc.T).astype(np.float64)
+    w, V = np.linalg.eigh(G)
+    order = np.argsort(-w)
+    w, V = w[order], V[:, order]
+    sig = np.sqrt(np.maximum(w[:r], 1e-300))
+    phi = (Xc.T.astype(np.float64) @ V[:, :r]) / sig[None, :]
+    coef = V[:, :r] * sig[None, :]
+    frac = float(w[:r].sum() / max(w.sum(), 1e-300))
+    return mean, np.ascontiguousarray(phi), np.ascontiguousarray(coef), frac

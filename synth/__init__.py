@@ -11,12 +11,14 @@ All units are SI (m, Pa, kg/m^3, s).
 """
 from .mesh import Mesh, tube_mesh, aneurysm_mesh, tube_for_nodes, plate_mesh, single_triangle, arch_mesh
 from .fields import gmrf_fields, lognormal_fields, matern_correlation
-from .loads import pressure_shear_modes, step_amplitudes, pulsatile_amplitudes, waveform
+from .loads import pressure_shear_modes, step_amplitudes, pulsatile_amplitudes, waveform, peak_amplitudes
+from .kl import kl_basis, kl_coefficients, kl_fields
 from .configs import cfl_dt, make_case
 
 __all__ = [
     "Mesh", "tube_mesh", "aneurysm_mesh", "tube_for_nodes", "plate_mesh", "single_triangle", "arch_mesh",
     "gmrf_fields", "lognormal_fields", "matern_correlation",
-    "pressure_shear_modes", "step_amplitudes", "pulsatile_amplitudes", "waveform",
+    "pressure_shear_modes", "step_amplitudes", "pulsatile_amplitudes", "waveform", "peak_amplitudes",
+    "kl_basis", "kl_coefficients", "kl_fields",
     "cfl_dt", "make_case",
 ]

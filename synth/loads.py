@@ -129,3 +129,12 @@ def delayed_pressure(mesh, s_node, n_steps: int, dt: float, speed: float = 5.0,
         cols.append(r * ak * np.cos(kk * w * t))
         cols.append(r * ak * np.sin(kk * w * t))
     return modes, np.ascontiguousarray(np.stack(cols, axis=1))
+
+
+def peak_amplitudes(n_steps: int, dt: float, pressure: float = 13.4e3, shear: float = 1.0,
+                    ramp_duration: float = 5.0e-3) -> np.ndarray:
+    """Amplitude table [n_steps][2] holding the peak-systole pressure (10.7 + 2.7 kPa) and
+    the axial shear after a quarter-sine ramp of `ramp_duration`."""
+    t = dt * np.arange(n_steps)
+    r = ramp(t, ramp_duration)
+    return np.ascontiguousarray(np.stack([r * pressure, r * shear], axis=1))
