@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-chunk", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-train", type=int, default=4096)
+    ap.add_argument("--sur-val", type=int, default=512)
+    ap.add_argument("--sur-epochs", type=int, default=400)
+    ap.add_argument("--sur-settle", type=float, default=0.03, help="simulated seconds per run")
     return ap.parse_args()
 
 
@@ -303,6 +308,102 @@ def bench_batched(args, local, stream, world):
     }
 
 
+def bench_surrogate(args, local, stream):
+    """Surrogate on the 50k-node aneurysm: 32 + 32 KL coefficients -> 32 POD coefficients of
+    the settled peak-systole displacement, trained on solver runs (S = 256 per launch)."""
+    import torch
+    import synth
+    from paper_2101_09059_gb300 import surrogate as sur
+    dev = torch.device("cuda", local)
+    n_train, n_val, S, nm, r = args.sur_train, args.sur_val, 256, 32, 32
+    mesh = synth.aneurysm_mesh(200, 250)
+    t0 = time.perf_counter()
+    basis = synth.kl_basis(mesh, nm)
+    xi = synth.kl_coefficients(n_train + n_val, nm, seed=11)
+    E_all, h_all = synth.kl_fields(basis, xi)
+    dt = synth.cfl_dt(mesh, E_all)
+    n_steps = int(round(args.sur_settle / dt))
+    params = dict(rho=synth.configs.RHO, nu=synth.configs.NU, kshear=synth.configs.KSHEAR,
+                  alpha=synth.configs.ALPHA, dt=dt)
+    modes = synth.pressure_shear_modes(mesh, with_shear=True)
+    amp = synth.peak_amplitudes(n_steps, dt)
+    t_inputs = time.perf_counter() - t0
+
+    def fields_for(rows):
+        return np.ascontiguousarray(E_all[:, rows]), np.ascontiguousarray(h_all[:, rows])
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    U = sur.solver_fields(mesh, fields_for, n_train, S, params, modes, amp, n_steps, stream=stream,
+                          device=local)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mean, phi, coef, frac = sur.pod(U, r)
+    t_pod = time.perf_counter() - t0
+    cs = coef.std(axis=0)
+    net = sur.Surrogate(2 * nm, 256, r, max_batch=4096, seed=1, stream=stream)
+    X = torch.from_numpy(xi[:n_train].astype(np.float32)).to(dev)
+    T = torch.from_numpy((coef / cs).astype(np.float32)).to(dev)
+    epochs = [(1e-3, args.sur_epochs // 2), (3e-4, args.sur_epochs // 4), (1e-4, args.sur_epochs // 4)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = []
+    for k, (lr, ep) in enumerate(epochs):
+        hist += list(net.train(X, T, epochs=ep, batch=256, lr=lr, seed=k))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    steps = (n_train // 256) * sum(ep for _, ep in epochs)
+    H = 256
+    flops_step = 6.0 * 256 * (2 * nm * H + H * H + H * r)   # forward 2x, backward 4x per MAC
+    net.scale_outputs(cs)
+    Xv = torch.from_numpy(xi[n_train:].astype(np.float32)).to(dev)
+    mean_d = torch.from_numpy(mean.astype(np.float32)).to(dev)
+    phi_d = torch.from_numpy(phi.astype(np.float32)).to(dev)
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cpred = net.forward(Xv)
+        mu_s, sd_s = sur.field_stats(cpred, mean_d, phi_d)
+        torch.cuda.synchronize()
+        t_pred = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Uv = sur.solver_fields(mesh, lambda rows: fields_for([n_train + q for q in rows]), n_val, S, params,
+                           modes, amp, n_steps, stream=stream, device=local)
+    torch.cuda.synchronize()
+    t_solver = time.perf_counter() - t0
+    mu_ref, sd_ref = Uv.mean(axis=0), Uv.std(axis=0, ddof=1)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    upred = sur.reconstruct(cpred, mean_d, phi_d).cpu().numpy()
+    proj = mean[None, :] + ((Uv - mean[None, :]) @ phi) @ phi.T
+    out = {
+        "workload": f"aneurysm tube {mesh.n_nodes} nodes, {nm}+{nm} KL coefficients -> {r} POD coefficients, "
+                    f"MLP {2 * nm}-256-256-{r} GELU, {n_train} train / {n_val} held-out solver runs",
+        "target": f"settled peak-systole displacement ({args.sur_settle * 1e3:.0f} ms, {n_steps} steps, "
+                  "13.4 kPa + 1 Pa shear after a 5 ms ramp)",
+        "kl_variance_fraction": float(basis[0].sum() / (mesh.n_nodes * 0.01)),
+        "pod_energy_fraction": frac,
+        "data_generation_s": t_data, "solver_sample_steps_per_s": n_train * n_steps / t_data,
+        "pod_s": t_pod, "inputs_s": t_inputs,
+        "train_s": t_train, "train_steps": steps, "final_train_loss": float(hist[-1]),
+        "train_tflops": flops_step * steps / t_train / 1e12,
+        "held_out_rel_l2_field": rel(upred, Uv),
+        "held_out_rel_l2_fluctuation": rel(upred - mu_ref[None, :], Uv - mu_ref[None, :]),
+        "pod_projection_floor_fluctuation": rel(proj - mu_ref[None, :], Uv - mu_ref[None, :]),
+        "stats_rel_err_mean": rel(mu_s.cpu().numpy(), mu_ref),
+        "stats_rel_err_std": rel(sd_s.cpu().numpy(), sd_ref),
+        "time_to_statistics_surrogate_ms": 1e3 * t_pred,
+        "time_to_statistics_solver_ms": 1e3 * t_solver,
+        "time_to_statistics_speedup": t_solver / t_pred,
+    }
+    net.close()
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -404,6 +505,7 @@ def main():
                "d2h_bytes_per_step": int(2 * N * 3 * 8 + 4)}
 
     batched = None if args.no_batched else bench_batched(args, local, stream, world)
+    surrogate = None if (args.no_surrogate or rank != 0) else bench_surrogate(args, local, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -442,6 +544,7 @@ def main():
         "cpu_baseline": cpu,
         "forms": results,
         "batched_uneven": batched,
+        "surrogate": surrogate,
         "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
     }
     if rank == 0:
