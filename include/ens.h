@@ -62,6 +62,9 @@ typedef enum { ENS_FP64 = 0, ENS_FP32_FORCE = 1, ENS_KAHAN32 = 2 } ens_precision
  * ENS_FLAG_UNSTAGED    : use the kernel without shared-memory staging.              */
 #define ENS_FLAG_NO_AUTOTUNE 1
 #define ENS_FLAG_UNSTAGED 2
+/* Use launch shape k of ens_info_t.kernel_variant (when it applies to the context's
+ * sizes; otherwise the unstaged kernel) instead of timing candidates.                 */
+#define ENS_FLAG_FORCE_VARIANT(k) (((k) + 1) << 8)
 
 /* ---- displacement layouts for the getters ---------------------------------------- */
 #define ENS_LAYOUT_SNC 0 /* out[s][node][dof]  */
@@ -127,8 +130,10 @@ typedef struct {
     double device_bytes;    /* device memory held by the context                */
     int32_t kernel_variant; /* launch shape in use: 0 unstaged, 1 staged 256x4,
                                2 staged 256x3, 3 staged 128x6, 4 staged 64x12
-                               (threads per block x blocks per SM)                */
-    float variant_us[6];    /* autotuner's time per step of each shape (-1: n/a,
+                               (threads per block x blocks per SM), 5 staged 256x5
+                               and 6 staged 128x10 with two samples per thread
+                               (binary32 forms)                                   */
+    float variant_us[8];    /* autotuner's time per step of each shape (-1: n/a,
                                0: not timed)                                      */
 } ens_info_t;
 

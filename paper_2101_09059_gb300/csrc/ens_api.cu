@@ -169,12 +169,14 @@ int run_steps(ens_ctx *c, int64_t n) {
 // any block, shared-memory size). Returns an unstaged plan when the shape does not apply
 // (threads per node do not divide the block, or the staging does not fit).
 int make_stage_plan(ens_ctx *c, const std::vector<int32_t> &rowptr, int32_t block,
-                    int32_t minb, StagePlan *out) {
+                    int32_t minb, StagePlan *out, int32_t vw = 0) {
     StagePlan p{};
     p.block = block;
     p.minb = minb;
+    p.vw = vw > 0 ? vw : (c->form == kFP64 ? Vw<double>::V : Vw<float>::V);
     *out = p;
-    const int32_t Q = c->Q, N = c->N, Sp = c->Sp;
+    const int32_t N = c->N, Sp = c->Sp;
+    const int32_t Q = Sp / p.vw;
     if (Q <= 0 || Q > block || (block % Q) != 0) return ENS_OK;
     const int32_t nb = block / Q;
     const size_t es = elem_size(c->form);
@@ -198,6 +200,15 @@ int make_stage_plan(ens_ctx *c, const std::vector<int32_t> &rowptr, int32_t bloc
 // own data (state at rest, no traction, so every value stays exactly zero) and keep the
 // fastest. Candidate 0 is the unstaged kernel.
 int autotune(ens_ctx *c, const StagePlan *cand, int n) {
+    // time on non-zero data (zeros take shortcuts in some arithmetic); reset afterwards
+    const int64_t ns = (int64_t)c->N * 3 * c->Sp;
+    const int dbl = c->form == kFP64;
+    CK(launch_fill(c->ug[0], ns, dbl, 1e-4f, 1u, c->stream));
+    CK(launch_fill(c->ug[1], ns, dbl, 1e-4f, 2u, c->stream));
+    if (c->u64) CK(launch_fill(c->u64, ns, 1, 1e-4f, 3u, c->stream));
+    if (c->v64) CK(launch_fill(c->v64, ns, 1, 1e-2f, 4u, c->stream));
+    if (c->ulo) CK(launch_fill(c->ulo, ns, 0, 1e-11f, 5u, c->stream));
+    if (c->v32) CK(launch_fill(c->v32, ns, 0, 1e-2f, 6u, c->stream));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -302,7 +313,8 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         !(p->alpha >= 0.0) || !(p->dt > 0.0) || !std::isfinite(p->rho) ||
         !std::isfinite(p->kshear) || !std::isfinite(p->alpha) || !std::isfinite(p->dt) ||
         p->precision < 0 || p->precision > 2 ||
-        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED)) != 0)
+        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | 0xf00)) != 0 ||
+        ((p->flags >> 8) & 0xf) > kVariants)
         return ENS_ERR_INVALID_ARG;
     if (alloc && (!alloc->alloc || !alloc->release)) return ENS_ERR_INVALID_ARG;
     if (!finite_all(mesh->xyz, 3 * (size_t)N)) return ENS_ERR_INVALID_ARG;
@@ -424,18 +436,28 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         const int to_f = c->form != kFP64;
         StagePlan cand[kVariants] = {};  // every slot unstaged until a plan is built
         if (!(c->flags_in & ENS_FLAG_UNSTAGED)) {
+            const int forced = ((c->flags_in >> 8) & 0xf) - 1;  // -1: none
             int rcp = make_stage_plan(c, rowptr, 256, 4, &cand[1]);
-            if (rcp == ENS_OK && !(c->flags_in & ENS_FLAG_NO_AUTOTUNE)) {
+            if (rcp == ENS_OK && (!(c->flags_in & ENS_FLAG_NO_AUTOTUNE) || forced >= 0)) {
                 cand[2] = cand[1];
                 cand[2].minb = 3;
                 rcp = make_stage_plan(c, rowptr, 128, 6, &cand[3]);
                 if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 64, 12, &cand[4]);
+                if (rcp == ENS_OK && c->form != kFP64) {  // two samples per thread: more warps
+                    rcp = make_stage_plan(c, rowptr, 256, 5, &cand[5], 2);
+                    if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 128, 10, &cand[6], 2);
+                }
             }
             if (rcp != ENS_OK) return rcp;
         }
         c->plan = cand[1];
         c->plan_fo = cand[1];
         c->variant = c->plan.staged ? 1 : 0;
+        const int forced_v = ((c->flags_in >> 8) & 0xf) - 1;
+        if (forced_v >= 0) {
+            c->plan = cand[forced_v];
+            c->variant = c->plan.staged ? forced_v : 0;
+        }
         c->kc = dev_alloc(c, es * (size_t)c->nnz * (to_f ? 20 : 18));
         c->minv = dev_alloc(c, es * (size_t)NSp);
         if (!c->kc || !c->minv) return fail(c, ENS_ERR_ALLOC, "coefficient buffers");
@@ -503,7 +525,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         ALLOC(c->stat_var, double, 3 * (int64_t)N);
         int rc0 = ens_reset(c);
         if (rc0 != ENS_OK) return rc0;
-        if (!(c->flags_in & (ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED)) && c->plan.staged) {
+        if (!(c->flags_in & (ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | 0xf00)) && c->plan.staged) {
             rc0 = autotune(c, cand, kVariants);
             if (rc0 != ENS_OK) return rc0;
         }

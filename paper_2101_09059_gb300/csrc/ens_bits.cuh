@@ -4,36 +4,60 @@
 // On GB300 the binary64 pipe issues about 2 operations per SM per clock, and the
 // hardware F2F conversions between binary32 and binary64 run on that same pipe. The
 // FP32-force update converts twice per dof and step, so the conversions below rebuild
-// the IEEE-754 bit patterns with integer operations instead (sign, exponent rebias
-// 127 <-> 1023, mantissa shift by 29 bits), falling back to the hardware conversion only
-// for the rare operands outside the normal range.
+// the IEEE-754 bit patterns with integer operations only (sign, exponent rebias
+// 127 <-> 1023, mantissa shift by 29 bits, and the special classes), never issuing a
+// binary64 instruction.
 #pragma once
 
 #include <cstdint>
 
 namespace ens {
 
-// Exact binary32 -> binary64 for every input (normal values via bit rebuild).
+// Exact binary32 -> binary64 for every input, integer operations only: normal values by
+// rebiasing the exponent (127 -> 1023) and shifting the mantissa 29 bits; subnormals are
+// normalised with a count of leading zeros; zero, Inf and NaN keep their class and sign.
 __device__ __forceinline__ double f32_to_f64(float x) {
     const uint32_t b = __float_as_uint(x);
+    const uint64_t sign = (uint64_t)(b >> 31) << 63;
     const uint32_t e = (b >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)x;  // zero, subnormal, Inf, NaN
-    const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-    const uint32_t lo = b << 29;
-    return __hiloint2double((int)hi, (int)lo);
+    const uint32_t m = b & 0x7fffffu;
+    uint64_t bits;
+    if (e == 0u) {
+        if (m == 0u) {
+            bits = sign;
+        } else {  // subnormal: value m * 2^-149, leading one at bit p
+            const int p = 31 - __clz(m);
+            const uint64_t mm = ((uint64_t)m << (52 - p)) & 0xfffffffffffffull;
+            bits = sign | ((uint64_t)(p - 149 + 1023) << 52) | mm;
+        }
+    } else if (e == 0xffu) {
+        bits = sign | (0x7ffull << 52) | ((uint64_t)m << 29);
+    } else {
+        bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+    }
+    return __longlong_as_double((long long)bits);
 }
 
-// binary64 -> binary32 rounding toward zero. Magnitudes below the smallest normal
-// binary32 (2^-126) become signed zero; Inf, NaN and overflow use the hardware path.
+// binary64 -> binary32 rounding toward zero, integer operations only. Magnitudes below
+// the smallest normal binary32 (2^-126) become signed zero; finite values beyond the
+// largest binary32 become the largest finite value (toward zero); Inf stays Inf and NaN
+// stays NaN.
 __device__ __forceinline__ float f64_to_f32_rz(double d) {
-    const uint32_t hi = (uint32_t)__double2hiint(d);
-    const uint32_t lo = (uint32_t)__double2loint(d);
-    const uint32_t e = (hi >> 20) & 0x7ffu;
-    const uint32_t s = hi & 0x80000000u;
-    if (e < 897u) return __uint_as_float(s);
-    if (e > 1150u) return __double2float_rz(d);
-    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    return __uint_as_float(s | ((e - 896u) << 23) | m);
+    const uint64_t bits = (uint64_t)__double_as_longlong(d);
+    const uint32_t sign = (uint32_t)(bits >> 32) & 0x80000000u;
+    const uint32_t e = (uint32_t)(bits >> 52) & 0x7ffu;
+    const uint64_t m = bits & 0xfffffffffffffull;
+    uint32_t out;
+    if (e < 897u) {
+        out = sign;
+    } else if (e == 0x7ffu) {
+        out = sign | 0x7f800000u | (m ? 0x400000u : 0u);
+    } else if (e > 1150u) {
+        out = sign | 0x7f7fffffu;
+    } else {
+        out = sign | ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    }
+    return __uint_as_float(out);
 }
 
 // ---- mbarrier and bulk copies (PTX ISA: mbarrier, cp.async.bulk) --------------------

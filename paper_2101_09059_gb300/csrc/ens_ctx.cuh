@@ -9,7 +9,7 @@
 #include "ens_internal.cuh"
 
 namespace ens {
-constexpr int kVariants = 6;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kVariants = 8;  // launch shapes the autotuner can time (see ens_info_t)
 }
 
 struct ens_ctx {
@@ -45,7 +45,7 @@ struct ens_ctx {
     ens::StagePlan plan{};     // launch shape of the step kernel
     ens::StagePlan plan_fo{};  // launch shape of force-only evaluations
     int32_t variant = 0;
-    float variant_us[ens::kVariants] = {0, 0, 0, 0, 0, 0};
+    float variant_us[ens::kVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
     int32_t flags_in = 0;
 };
 

@@ -78,6 +78,7 @@ struct StagePlan {
     int32_t cnt_max;  // most incidences of any block
     uint32_t smem;    // dynamic shared memory per block
     int32_t minb;     // resident blocks per SM the register budget targets
+    int32_t vw;       // samples per thread (the binary32 forms also have a 2-sample shape)
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or
@@ -124,6 +125,7 @@ template <typename R>
 int batch_persistent_grid(int form, int block);  // co-resident blocks of the persistent kernel
 cudaError_t launch_advance_many(int64_t *const *ctrs, int32_t n, int64_t by, cudaStream_t s);
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s);
+cudaError_t launch_fill(void *p, int64_t n, int is_double, float scale, uint32_t seed, cudaStream_t s);
 cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s);
 cudaError_t launch_export(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,

@@ -43,6 +43,22 @@ __device__ __forceinline__ void ld_nc(const float *p, float (&x)[4]) {
     x[2] = t.z;
     x[3] = t.w;
 }
+__device__ __forceinline__ void ld_nc(const float *p, float (&x)[2]) {
+    float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+}
+__device__ __forceinline__ void ld_cs(const float *p, float (&x)[2]) {
+    float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+}
+__device__ __forceinline__ void st_cs(float *p, const float (&x)[2]) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(x[0], x[1]));
+}
+__device__ __forceinline__ void st_wb(float *p, const float (&x)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+}
 __device__ __forceinline__ void ld_cs(const double *p, double (&x)[2]) {
     double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
     x[0] = t.x;
@@ -109,19 +125,23 @@ __device__ __forceinline__ void ld_cg(const float *p, float (&x)[4]) {
     x[2] = t.z;
     x[3] = t.w;
 }
-template <bool COH, typename R>
-__device__ __forceinline__ void ld_state(const R *p, R (&x)[Vw<R>::V]) {
+__device__ __forceinline__ void ld_cg(const float *p, float (&x)[2]) {
+    float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+}
+template <bool COH, typename R, int V>
+__device__ __forceinline__ void ld_state(const R *p, R (&x)[V]) {
     if constexpr (COH)
         ld_cg(p, x);
     else
         ld_nc(p, x);
 }
 
-template <typename R, bool COH = false>
+template <typename R, int V, bool COH = false>
 __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__restrict__ ug,
-                                           int32_t i, int32_t s0, const R (&ui)[3][Vw<R>::V],
-                                           R (&f)[3][Vw<R>::V]) {
-    constexpr int V = Vw<R>::V;
+                                           int32_t i, int32_t s0, const R (&ui)[3][V],
+                                           R (&f)[3][V]) {
     const int64_t Sp = w.Sp;
 #pragma unroll
     for (int d = 0; d < 3; d++)
@@ -134,8 +154,8 @@ __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__res
         R ua[3][V], ub[3][V], e[V], k[18];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            ld_state<COH>(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
-            ld_state<COH>(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
+            ld_state<COH, R, V>(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
+            ld_state<COH, R, V>(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
         }
         ld_nc(w.eh + (int64_t)en.x * Sp + s0, e);
         ld_kc(w.kc + (int64_t)p * Kc<R>::stride, k);
@@ -172,10 +192,9 @@ __device__ __forceinline__ void node_traction(const StepArgs<R> &a, int32_t i, i
 
 // The fused update of node i, samples [s0, s0 + V): a = (f_ext - f_int) / m, then the
 // velocity form of Eq. (dynamicsCD) with the fixed-dof mask, stored per form.
-template <int FORM, typename R>
+template <int FORM, typename R, int V>
 __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int32_t s0,
-                                            const R (&ui)[3][Vw<R>::V], const R (&f)[3][Vw<R>::V]) {
-    constexpr int V = Vw<R>::V;
+                                            const R (&ui)[3][V], const R (&f)[3][V]) {
     const int64_t Sp = a.fv.Sp;
     const int64_t n = *a.step_ctr + a.k_off;
     R fe[3];
@@ -202,23 +221,20 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             st_cs(a.v64 + row, vv);
             st_wb(a.ug_next + row, un);
         } else if constexpr (FORM == kFP32Force) {
-            double uu[4], vv[4], h2[2];
-            ld_cs(a.u64 + row, h2);
-            uu[0] = h2[0];
-            uu[1] = h2[1];
-            ld_cs(a.u64 + row + 2, h2);
-            uu[2] = h2[0];
-            uu[3] = h2[1];
-            ld_cs(a.v64 + row, h2);
-            vv[0] = h2[0];
-            vv[1] = h2[1];
-            ld_cs(a.v64 + row + 2, h2);
-            vv[2] = h2[0];
-            vv[3] = h2[1];
-            float ug[4];
+            double uu[V], vv[V], h2[2];
+#pragma unroll
+            for (int q = 0; q < V; q += 2) {
+                ld_cs(a.u64 + row + q, h2);
+                uu[q] = h2[0];
+                uu[q + 1] = h2[1];
+                ld_cs(a.v64 + row + q, h2);
+                vv[q] = h2[0];
+                vv[q + 1] = h2[1];
+            }
+            float ug[V];
             const float c2 = (float)a.c2;
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
+            for (int v = 0; v < V; v++) {
                 const float acc = (fe[d] - f[d][v]) * mi[v];
                 // binary64 state update; the conversions run on the integer pipe
                 const double vn = held ? 0.0 : fma(a.c1, vv[v], f32_to_f64(c2 * acc));
@@ -228,18 +244,19 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
                 ug[v] = f64_to_f32_rz(un);
                 bad |= !isfinite(ug[v]);
             }
-            st_cs(a.u64 + row, {uu[0], uu[1]});
-            st_cs(a.u64 + row + 2, {uu[2], uu[3]});
-            st_cs(a.v64 + row, {vv[0], vv[1]});
-            st_cs(a.v64 + row + 2, {vv[2], vv[3]});
+#pragma unroll
+            for (int q = 0; q < V; q += 2) {
+                st_cs(a.u64 + row + q, {uu[q], uu[q + 1]});
+                st_cs(a.v64 + row + q, {vv[q], vv[q + 1]});
+            }
             st_wb(a.ug_next + row, ug);
         } else {  // kKahan32
-            float lo[4], vv[4], hi[4];
+            float lo[V], vv[V], hi[V];
             ld_cs(a.ulo + row, lo);
             ld_cs(a.v32 + row, vv);
             const float c1 = (float)a.c1, c2 = (float)a.c2, dt = (float)a.dt;
 #pragma unroll
-            for (int v = 0; v < 4; v++) {
+            for (int v = 0; v < V; v++) {
                 const float acc = (fe[d] - f[d][v]) * mi[v];
                 const float vn = held ? 0.0f : fmaf(c1, vv[v], c2 * acc);
                 // (hi, lo) += dt * vn as an error-free sum of hi and the small part.
@@ -260,21 +277,20 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
     if (bad) atomicOr(a.flags, 1);
 }
 
-template <typename R>
+template <typename R, int V>
 __device__ __forceinline__ void store_force(const StepArgs<R> &a, int32_t i, int32_t s0,
-                                            const R (&f)[3][Vw<R>::V]) {
+                                            const R (&f)[3][V]) {
 #pragma unroll
     for (int d = 0; d < 3; d++)
 #pragma unroll
-        for (int v = 0; v < Vw<R>::V; v++)
+        for (int v = 0; v < V; v++)
             a.force_out[((int64_t)i * 3 + d) * a.fv.Sp + s0 + v] = (double)f[d][v];
 }
 
 // Unstaged kernel: everything through the cache hierarchy (used when the staged plan
 // does not apply).
-template <int FORM, typename R, bool FORCE_ONLY>
+template <int FORM, typename R, bool FORCE_ONLY, int V = Vw<R>::V>
 __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
-    constexpr int V = Vw<R>::V;
     const int32_t Q = a.fv.Q;
     const int64_t Sp = a.fv.Sp;
     const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
@@ -285,11 +301,11 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
 #pragma unroll
     for (int d = 0; d < 3; d++) ld_nc(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
     R f[3][V];
-    node_force<R>(a.fv, a.ug_cur, i, s0, ui, f);
+    node_force<R, V>(a.fv, a.ug_cur, i, s0, ui, f);
     if constexpr (FORCE_ONLY)
-        store_force<R>(a, i, s0, f);
+        store_force<R, V>(a, i, s0, f);
     else
-        node_update<FORM, R>(a, i, s0, ui, f);
+        node_update<FORM, R, V>(a, i, s0, ui, f);
 }
 
 // Staged kernel. Block b owns nodes [b nb, b nb + nb). One thread issues bulk copies
@@ -298,12 +314,11 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
 // block's remaining state rows, which are only read after the force loop. Every thread
 // then needs a single global round trip per incidence (the two other corners' rows and
 // (E h)), with its own rows, the entry and the 18 coefficients coming from shared memory.
-template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB>
+template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V>
 __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs<R> a,
                                                                   const StagePlan pl) {
     const int32_t nb_block = pl.nb;
     const int32_t cnt_max = pl.cnt_max;
-    constexpr int V = Vw<R>::V;
     constexpr int KS = Kc<R>::stride;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -405,12 +420,27 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
         }
     }
     if constexpr (FORCE_ONLY)
-        store_force<R>(a, i, s0, f);
+        store_force<R, V>(a, i, s0, f);
     else
-        node_update<FORM, R>(a, i, s0, ui, f);
+        node_update<FORM, R, V>(a, i, s0, ui, f);
 }
 
 __global__ void advance_kernel(int64_t *ctr, int64_t n) { *ctr += n; }
+
+// Deterministic non-zero values of magnitude <= scale (an integer hash of the index).
+__global__ void fill_kernel(void *p, int64_t n, int is_double, float scale, uint32_t seed) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t h = (uint32_t)t * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const float v = scale * ((float)(h >> 8) * (1.0f / 16777216.0f) - 0.5f);
+    if (is_double)
+        ((double *)p)[t] = (double)v;
+    else
+        ((float *)p)[t] = v;
+}
 
 __global__ void advance_many_kernel(int64_t *const *ctrs, int32_t n, int64_t by) {
     const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -456,10 +486,10 @@ __device__ __forceinline__ void batch_tile(const MemberDev<R> *__restrict__ mem,
     const int64_t Sp = m.fv.Sp;
     R ui[3][V];
 #pragma unroll
-    for (int d = 0; d < 3; d++) ld_state<COH>(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
+    for (int d = 0; d < 3; d++) ld_state<COH, R, V>(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
     R f[3][V];
-    node_force<R, COH>(a.fv, a.ug_cur, i, s0, ui, f);
-    node_update<FORM, R>(a, i, s0, ui, f);
+    node_force<R, V, COH>(a.fv, a.ug_cur, i, s0, ui, f);
+    node_update<FORM, R, V>(a, i, s0, ui, f);
 }
 
 // Batched step: one launch advances every member one step (graph-captured in chunks).
@@ -634,9 +664,11 @@ void note_launch(const char *what, int block, int minb, uint32_t smem, cudaError
              block, minb, smem, cudaGetErrorString(e));
 }
 
-template <int FORM, typename R, bool FO, int BLOCK, int MINB>
-cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
-    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB>;
+template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V>
+cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
+    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V>;
+    StepArgs<R> a = a0;
+    a.fv.Q = a.fv.Sp / V;
     if (plan->smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)plan->smem);
@@ -660,6 +692,12 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
             // force-only evaluations have one staged shape; other plans run unstaged
             if (plan->block == 256 && plan->minb == 4) return launch_staged<FORM, R, FO, 256, 4>(a, s, plan);
         } else {
+            if constexpr (sizeof(R) == 4) {
+                if (plan->vw == 2) {
+                    if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 10, 2>(a, s, plan);
+                    return launch_staged<FORM, R, FO, 256, 5, 2>(a, s, plan);
+                }
+            }
             if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 6>(a, s, plan);
             if (plan->block == 64) return launch_staged<FORM, R, FO, 64, 12>(a, s, plan);
             if (plan->minb == 3) return launch_staged<FORM, R, FO, 256, 3>(a, s, plan);
@@ -782,6 +820,12 @@ template int batch_persistent_grid<float>(int, int);
 cudaError_t launch_advance_many(int64_t *const *ctrs, int32_t n, int64_t by, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     advance_many_kernel<<<(n + 127) / 128, 128, 0, s>>>(ctrs, n, by);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(void *p, int64_t n, int is_double, float scale, uint32_t seed, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p, n, is_double, scale, seed);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,11 @@ from . import _lib
 
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
 FLAG_NO_AUTOTUNE, FLAG_UNSTAGED = 1, 2
+
+
+def FLAG_FORCE_VARIANT(k: int) -> int:
+    """Creation flag: use launch shape k (ens_info_t.kernel_variant) without autotuning."""
+    return (k + 1) << 8
 PRECISIONS = {"fp64": FP64, "fp32_force": FP32_FORCE, "kahan32": KAHAN32}
 LAYOUT_SNC, LAYOUT_NCS = 0, 1
 

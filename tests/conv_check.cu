@@ -55,6 +55,9 @@ int main() {
     long bad64 = 0, bad32 = 0, flushed = 0;
     for (int i = 0; i < n; i++) {
         if (memcmp(&o64[i], &r64[i], 8) != 0 && !(o64[i] != o64[i] && r64[i] != r64[i])) bad64++;
+        // NaN must stay NaN in both directions
+        if ((xf[i] != xf[i]) != (o64[i] != o64[i])) bad64++;
+        if ((xd[i] != xd[i]) != (o32[i] != o32[i])) bad32++;
         const double ad = xd[i] < 0 ? -xd[i] : xd[i];
         if (ad < 1.1754943508222875e-38) {   // below the binary32 normal range: signed zero
             uint32_t ob; memcpy(&ob, &o32[i], 4);

@@ -1,6 +1,7 @@
-"""The step kernels' integer-pipe binary32 <-> binary64 conversions agree bit for bit with
-the hardware conversions (binary64 -> binary32 rounds toward zero; magnitudes below the
-binary32 normal range become signed zero, by design)."""
+"""The step kernels' integer-only binary32 <-> binary64 conversions agree bit for bit with
+the hardware conversions on normal values, zeros, subnormals, Inf and overflow
+(binary64 -> binary32 rounds toward zero; magnitudes below the binary32 normal range
+become signed zero, by design); NaN stays NaN."""
 import os
 import subprocess
 
