@@ -242,6 +242,29 @@ def cpu_baseline(case, S, budget_s=15.0):
             "sample": f"{n} time steps x {S} samples of the same {case['mesh'].n_nodes}-node workload"}
 
 
+def bench_tiny(args, local, stream):
+    """The 40 x 40 tube at S = 8 (12,800 node-samples): launch-bound; time-loop graph
+    replays against one launch per step."""
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+    case = synth.make_case("tube_40x40", n_steps=4000)
+    out = {"workload": "tube R=1 cm L=10 cm, 1600 nodes, 3120 triangles, S=8, 10 kPa step, 2000 steps"}
+    for label, flags in (("graph", 0), ("direct", pkg.ensemble.FLAG_NO_GRAPH)):
+        e = pkg.Ensemble.from_case(case, precision=HEADLINE, stream=stream, device=local, flags=flags)
+        e.step(1000)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        e.step(2000)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        out[label] = {"sample_steps_per_s": 8 * 2000 / t, "us_per_step": 1e6 * t / 2000}
+        e.close()
+    return out
+
+
 def bench_batched(args, local, stream, world):
     """Five clamped tubes (20k, 50k, 100k, 200k, 400k nodes; S = 256, 128, 64, 32, 16; each
     with its own CFL time step; 10 kPa step load) advanced by one batched launch per step
@@ -504,6 +527,7 @@ def main():
                "h2d_bytes_per_step": int(C * case["amp"].shape[1] * 8),
                "d2h_bytes_per_step": int(2 * N * 3 * 8 + 4)}
 
+    tiny = bench_tiny(args, local, stream) if rank == 0 else None
     batched = None if args.no_batched else bench_batched(args, local, stream, world)
     surrogate = None if (args.no_surrogate or rank != 0) else bench_surrogate(args, local, stream)
 
@@ -543,6 +567,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "forms": results,
+        "tiny_tube_40x40": tiny,
         "batched_uneven": batched,
         "surrogate": surrogate,
         "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,

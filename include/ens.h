@@ -24,7 +24,9 @@
  *    Output arrays are caller-allocated.
  *  - Device work runs on the stream given at creation. Calls that return host data
  *    synchronise that stream; ens_step synchronises it once at the end to report
- *    non-finite values.
+ *    non-finite values. Long ens_step calls replay a CUDA graph of 32 step launches
+ *    (captured on a private stream on first use), so the first such call must not be
+ *    made while the context's stream is being captured.
  *  - A context is not thread-safe; distinct contexts are independent.
  */
 #ifndef ENS_H
@@ -62,6 +64,9 @@ typedef enum { ENS_FP64 = 0, ENS_FP32_FORCE = 1, ENS_KAHAN32 = 2 } ens_precision
  * ENS_FLAG_UNSTAGED    : use the kernel without shared-memory staging.              */
 #define ENS_FLAG_NO_AUTOTUNE 1
 #define ENS_FLAG_UNSTAGED 2
+/* Launch every step directly instead of replaying the captured time-loop graph (by
+ * default ens_step replays a graph of 32 step launches when n allows).                */
+#define ENS_FLAG_NO_GRAPH 4
 /* Use launch shape k of ens_info_t.kernel_variant (when it applies to the context's
  * sizes; otherwise the unstaged kernel) instead of timing candidates.                 */
 #define ENS_FLAG_FORCE_VARIANT(k) (((k) + 1) << 8)

@@ -296,6 +296,8 @@ const char *ens_last_error(const ens_ctx *c) { return c ? c->err.c_str() : g_cre
 void ens_destroy(ens_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap) cudaStreamDestroy(c->cap);
     while (!c->bufs.empty()) dev_free(c, c->bufs.back().first);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     delete c;
@@ -313,7 +315,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         !(p->alpha >= 0.0) || !(p->dt > 0.0) || !std::isfinite(p->rho) ||
         !std::isfinite(p->kshear) || !std::isfinite(p->alpha) || !std::isfinite(p->dt) ||
         p->precision < 0 || p->precision > 2 ||
-        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | 0xf00)) != 0 ||
+        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | ENS_FLAG_NO_GRAPH | 0xf00)) != 0 ||
         ((p->flags >> 8) & 0xf) > kVariants)
         return ENS_ERR_INVALID_ARG;
     if (alloc && (!alloc->alloc || !alloc->release)) return ENS_ERR_INVALID_ARG;
@@ -631,6 +633,44 @@ int ens_set_amplitudes(ens_ctx *c, int64_t first_row, int64_t n_rows, const doub
     return ENS_OK;
 }
 
+namespace {
+// Steps through a captured graph: kGraphSteps launches and one counter advance, replayed.
+// The graph bakes buffer pointers, the launch shape and the parity of the first step, so
+// it is rebuilt when any of them changed. Returns the number of steps done this way.
+int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
+    *done = 0;
+    const int K = kGraphSteps;
+    if (n < 2 * K || !c->started || (c->flags_in & ENS_FLAG_NO_GRAPH)) return ENS_OK;
+    std::vector<uintptr_t> key = {(uintptr_t)(c->cur & 1), (uintptr_t)c->amp, (uintptr_t)c->modes,
+                                  (uintptr_t)c->J, (uintptr_t)c->variant, (uintptr_t)c->plan.staged};
+    if (!c->graph || c->graph_key != key) {
+        if (c->graph) cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < K && e == cudaSuccess; k++) e = launch_chunk_step(c, k, false, c->cap);
+        if (e == cudaSuccess) e = launch_advance(c->step_ctr, K, c->cap);
+        cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(c, ENS_ERR_CUDA, "time-loop graph capture: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(c, ENS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        c->graph_key = key;
+    }
+    while (n - *done >= K) {  // K is even: the parity is the same after every replay
+        CK(cudaGraphLaunch(c->graph, c->stream));
+        *done += K;
+    }
+    return ENS_OK;
+}
+}  // namespace
+
 int ens_step(ens_ctx *c, int64_t n) {
     if (!c) return ENS_ERR_INVALID_ARG;
     if (n < 0) return fail(c, ENS_ERR_INVALID_ARG, "n = %lld", (long long)n);
@@ -640,14 +680,28 @@ int ens_step(ens_ctx *c, int64_t n) {
                     (long long)n, (long long)c->n_amp);
     if (n == 0) return ENS_OK;
     if (n > INT32_MAX) return fail(c, ENS_ERR_INVALID_ARG, "n too large for one call");
+    const int64_t step0 = c->step;
     CK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
-    int rc = run_steps(c, n);
+    int64_t left = n;
+    if (!c->started) {  // the start step never goes into a graph
+        int rc = run_steps(c, 1);
+        if (rc != ENS_OK) return rc;
+        CK(launch_advance(c->step_ctr, 1, c->stream));
+        c->started = true;
+        left -= 1;
+    }
+    int64_t done = 0;  // graph replays advance the device counter themselves
+    int rc = graph_steps(c, left, &done);
     if (rc != ENS_OK) return rc;
-    CK(launch_advance(c->step_ctr, n, c->stream));
+    left -= done;
+    if (left > 0) {
+        rc = run_steps(c, left);
+        if (rc != ENS_OK) return rc;
+        CK(launch_advance(c->step_ctr, left, c->stream));
+    }
     CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->step += n;
-    c->started = true;
+    c->step = step0 + n;
     if (c->h_flags[0] & 4)
         return fail(c, ENS_ERR_CUDA, "a staged block found its launch plan inconsistent");
     if (c->h_flags[0] & 2)

@@ -10,6 +10,7 @@
 
 namespace ens {
 constexpr int kVariants = 8;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
 }
 
 struct ens_ctx {
@@ -47,6 +48,10 @@ struct ens_ctx {
     int32_t variant = 0;
     float variant_us[ens::kVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
     int32_t flags_in = 0;
+    // time-loop graph of kGraphSteps launches + counter advance (see ens_step)
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<uintptr_t> graph_key;
 };
 
 

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
-FLAG_NO_AUTOTUNE, FLAG_UNSTAGED = 1, 2
+FLAG_NO_AUTOTUNE, FLAG_UNSTAGED, FLAG_NO_GRAPH = 1, 2, 4
 
 
 def FLAG_FORCE_VARIANT(k: int) -> int:
