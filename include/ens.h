@@ -278,6 +278,16 @@ int ens_batch_info(const ens_batch *b, ens_batch_info_t *info);
 const char *ens_batch_last_error(const ens_batch *b);
 void ens_batch_destroy(ens_batch *b);
 
+/* Merge per-dof ensemble statistics of disjoint sample shards (e.g. one per GPU, each
+ * from ens_stats): counts[k] samples with mean means[k][i] and sample variance vars[k][i]
+ * (divisor counts[k] - 1) give the statistics of the union, mean_out[i] and var_out[i]
+ * (divisor total - 1), for i < n. Host arrays; no device work. The mean is merged first
+ * and the squared deviations are then summed around it (Chan et al.'s parallel form).
+ * The paper's ensemble means and bands (Section 3) are of one ensemble; the merge lets
+ * the realisations of one ensemble live on several GPUs with no exchange until here.   */
+int ens_merge_stats(int32_t n_parts, const int64_t *counts, const double *const *means,
+                    const double *const *vars, int64_t n, double *mean_out, double *var_out);
+
 /* Sizes, step index and traffic model.                                               */
 int ens_info(const ens_ctx *ctx, ens_info_t *info);
 

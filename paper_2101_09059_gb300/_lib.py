@@ -152,6 +152,8 @@ def load(build_if_missing: bool = True):
         "ens_last_error": ([vp], ctypes.c_char_p),
         "ens_error_string": ([ctypes.c_int], ctypes.c_char_p),
         "ens_destroy": ([vp], None),
+        "ens_merge_stats": ([i32, ctypes.POINTER(i64), ctypes.POINTER(dp), ctypes.POINTER(dp), i64, dp, dp],
+                            ctypes.c_int),
         "ens_batch_create": ([ctypes.POINTER(vp), i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "ens_batch_step": ([vp, i64], ctypes.c_int),
         "ens_batch_info": ([vp, ctypes.POINTER(ens_batch_info_t)], ctypes.c_int),

@@ -1045,3 +1045,34 @@ extern "C" int ens_internal_force_noalloc(ens_ctx *c, const double *u_dev, doubl
                          c->stream));
     return ENS_OK;
 }
+
+// ---------------------------------------------------------------------------------
+// Merging ensemble statistics of sample shards (one shard per GPU or process).
+// ---------------------------------------------------------------------------------
+extern "C" int ens_merge_stats(int32_t n_parts, const int64_t *counts, const double *const *means,
+                               const double *const *vars, int64_t n, double *mean_out,
+                               double *var_out) {
+    if (n_parts < 1 || !counts || !means || !vars || n < 0 || !mean_out || !var_out)
+        return ENS_ERR_INVALID_ARG;
+    int64_t total = 0;
+    for (int32_t k = 0; k < n_parts; k++) {
+        if (counts[k] < 0 || (counts[k] > 0 && (!means[k] || !vars[k]))) return ENS_ERR_INVALID_ARG;
+        total += counts[k];
+    }
+    if (total < 1) return ENS_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; i++) {
+        double mu = 0.0;
+        for (int32_t k = 0; k < n_parts; k++)
+            if (counts[k] > 0) mu += (double)counts[k] * means[k][i];
+        mu /= (double)total;
+        double m2 = 0.0;
+        for (int32_t k = 0; k < n_parts; k++) {
+            if (counts[k] == 0) continue;
+            const double d = means[k][i] - mu;
+            m2 += vars[k][i] * (double)(counts[k] - 1) + (double)counts[k] * d * d;
+        }
+        mean_out[i] = mu;
+        var_out[i] = total > 1 ? m2 / (double)(total - 1) : 0.0;
+    }
+    return ENS_OK;
+}

@@ -272,3 +272,43 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def merge_stats(parts):
+    """Statistics of the union of disjoint sample shards: parts = [(count, mean, var), ...]
+    with mean/var arrays of one shape (var: divisor count - 1). Runs ens_merge_stats."""
+    L = _lib.load()
+    k = len(parts)
+    shape = np.shape(parts[0][1])
+    means = [np.ascontiguousarray(p[1], dtype=np.float64).ravel() for p in parts]
+    vars_ = [np.ascontiguousarray(p[2], dtype=np.float64).ravel() for p in parts]
+    n = means[0].size
+    counts = (ctypes.c_int64 * k)(*[int(p[0]) for p in parts])
+    mp = (ctypes.c_void_p * k)(*[m.ctypes.data for m in means])
+    vp = (ctypes.c_void_p * k)(*[v.ctypes.data for v in vars_])
+    mo = np.empty(n)
+    vo = np.empty(n)
+    rc = L.ens_merge_stats(k, counts, mp, vp, n, _ptr(mo), _ptr(vo))
+    if rc != 0:
+        raise EnsError(rc, L.ens_error_string(rc).decode())
+    return mo.reshape(shape), vo.reshape(shape)
+
+
+def sharded_stats(count, mean, var, group=None):
+    """Merge one rank's shard statistics with every other rank's: an all-gather of
+    (count, mean, var) over torch.distributed, then ens_merge_stats on every rank."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    m = torch.as_tensor(np.ascontiguousarray(mean, dtype=np.float64), device=dev)
+    v = torch.as_tensor(np.ascontiguousarray(var, dtype=np.float64), device=dev)
+    c = torch.tensor([int(count)], dtype=torch.int64, device=dev)
+    ms = [torch.empty_like(m) for _ in range(world)]
+    vs = [torch.empty_like(v) for _ in range(world)]
+    cs = [torch.empty_like(c) for _ in range(world)]
+    dist.all_gather(ms, m, group=group)
+    dist.all_gather(vs, v, group=group)
+    dist.all_gather(cs, c, group=group)
+    parts = [(int(cc.item()), mm.cpu().numpy(), vv.cpu().numpy()) for cc, mm, vv in zip(cs, ms, vs)]
+    return merge_stats(parts)
