@@ -144,6 +144,8 @@ cudaError_t launch_chunk_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s)
     a.k_off = k;
     a.c1 = c1;
     a.c2 = c2;
+    a.c1f = (float)c1;
+    a.c2f = (float)c2;
     return launch_step<float>(c->form, a, false, s, &c->plan);
 }
 
@@ -448,6 +450,10 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                 if (rcp == ENS_OK && c->form != kFP64) {  // two samples per thread: more warps
                     rcp = make_stage_plan(c, rowptr, 256, 5, &cand[5], 2);
                     if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 128, 10, &cand[6], 2);
+                    if (rcp == ENS_OK) {  // two incidences in flight per thread
+                        rcp = make_stage_plan(c, rowptr, 128, 8, &cand[7], 2);
+                        cand[7].pair = 1;
+                    }
                 }
             }
             if (rcp != ENS_OK) return rcp;

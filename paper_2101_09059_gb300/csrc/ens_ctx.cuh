@@ -86,6 +86,7 @@ StepArgs<R> make_args(ens_ctx *c) {
     a.step_ctr = c->step_ctr;
     a.J = c->J;
     a.dt = c->dt;
+    a.dtf = (float)c->dt;
     a.flags = c->flags;
     return a;
 }

@@ -63,6 +63,7 @@ struct StepArgs {
     int32_t k_off;    // this launch advances step (*step_ctr + k_off)
     int32_t J;
     double c1, c2, dt;  // v_new = c1 v + c2 a ; u_new = u + dt v_new
+    float c1f, c2f, dtf;  // the same constants rounded to binary32 (binary32 forms)
     double *force_out;  // force-only mode: [N][3][Sp] binary64
     int *flags;         // [0] bit 0: non-finite seen, bit 1: a bounded wait gave up
 };
@@ -79,6 +80,7 @@ struct StagePlan {
     uint32_t smem;    // dynamic shared memory per block
     int32_t minb;     // resident blocks per SM the register budget targets
     int32_t vw;       // samples per thread (the binary32 forms also have a 2-sample shape)
+    int32_t pair;     // gather two incidences per loop iteration
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or

@@ -232,7 +232,7 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
                 vv[q + 1] = h2[1];
             }
             float ug[V];
-            const float c2 = (float)a.c2;
+            const float c2 = a.c2f;
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float acc = (fe[d] - f[d][v]) * mi[v];
@@ -254,7 +254,7 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             float lo[V], vv[V], hi[V];
             ld_cs(a.ulo + row, lo);
             ld_cs(a.v32 + row, vv);
-            const float c1 = (float)a.c1, c2 = (float)a.c2, dt = (float)a.dt;
+            const float c1 = a.c1f, c2 = a.c2f, dt = a.dtf;
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float acc = (fe[d] - f[d][v]) * mi[v];
@@ -314,7 +314,41 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
 // block's remaining state rows, which are only read after the force loop. Every thread
 // then needs a single global round trip per incidence (the two other corners' rows and
 // (E h)), with its own rows, the entry and the 18 coefficients coming from shared memory.
-template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V>
+// One incidence of the force loop with everything it reads already in registers.
+template <typename R, int V>
+__device__ __forceinline__ void apply_incidence(const R (&ua)[3][V], const R (&ub)[3][V], const R (&e)[V],
+                                                const R *__restrict__ k, const R (&ui)[3][V],
+                                                R (&f)[3][V]) {
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        const R a0 = ua[0][v] - ui[0][v], a1 = ua[1][v] - ui[1][v], a2 = ua[2][v] - ui[2][v];
+        const R b0 = ub[0][v] - ui[0][v], b1 = ub[1][v] - ui[1][v], b2 = ub[2][v] - ui[2][v];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            R t = k[3 * d] * a0;
+            t = fma(k[3 * d + 1], a1, t);
+            t = fma(k[3 * d + 2], a2, t);
+            t = fma(k[9 + 3 * d], b0, t);
+            t = fma(k[9 + 3 * d + 1], b1, t);
+            t = fma(k[9 + 3 * d + 2], b2, t);
+            f[d][v] = fma(e[v], t, f[d][v]);
+        }
+    }
+}
+
+template <typename R, int V>
+__device__ __forceinline__ void load_incidence(const R *__restrict__ ug, const R *__restrict__ eh,
+                                               const int4 en, int64_t Sp, int32_t s0, R (&ua)[3][V],
+                                               R (&ub)[3][V], R (&e)[V]) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        ld_nc(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
+        ld_nc(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
+    }
+    ld_nc(eh + (int64_t)en.x * Sp + s0, e);
+}
+
+template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V, bool PAIR = false>
 __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs<R> a,
                                                                   const StagePlan pl) {
     const int32_t nb_block = pl.nb;
@@ -393,31 +427,23 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
 #pragma unroll
         for (int v = 0; v < V; v++) f[d][v] = R(0);
     const R *__restrict__ ug = a.ug_cur;
-    for (int32_t p = p0; p < p1; ++p) {
+    int32_t p = p0;
+    if constexpr (PAIR) {
+        // two incidences per iteration: their 2 x 7 global loads are in flight together
+        for (; p + 1 < p1; p += 2) {
+            const int4 e0 = ent_s[p], e1 = ent_s[p + 1];
+            R ua0[3][V], ub0[3][V], ev0[V], ua1[3][V], ub1[3][V], ev1[V];
+            load_incidence<R, V>(ug, a.fv.eh, e0, Sp, s0, ua0, ub0, ev0);
+            load_incidence<R, V>(ug, a.fv.eh, e1, Sp, s0, ua1, ub1, ev1);
+            apply_incidence<R, V>(ua0, ub0, ev0, kc_s + (size_t)p * KS, ui, f);
+            apply_incidence<R, V>(ua1, ub1, ev1, kc_s + (size_t)(p + 1) * KS, ui, f);
+        }
+    }
+    for (; p < p1; ++p) {
         const int4 en = ent_s[p];
-        R ua[3][V], ub[3][V], e[V];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            ld_nc(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
-            ld_nc(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
-        }
-        ld_nc(a.fv.eh + (int64_t)en.x * Sp + s0, e);
-        const R *k = kc_s + (size_t)p * KS;
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            const R a0 = ua[0][v] - ui[0][v], a1 = ua[1][v] - ui[1][v], a2 = ua[2][v] - ui[2][v];
-            const R b0 = ub[0][v] - ui[0][v], b1 = ub[1][v] - ui[1][v], b2 = ub[2][v] - ui[2][v];
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                R t = k[3 * d] * a0;
-                t = fma(k[3 * d + 1], a1, t);
-                t = fma(k[3 * d + 2], a2, t);
-                t = fma(k[9 + 3 * d], b0, t);
-                t = fma(k[9 + 3 * d + 1], b1, t);
-                t = fma(k[9 + 3 * d + 2], b2, t);
-                f[d][v] = fma(e[v], t, f[d][v]);
-            }
-        }
+        R ua[3][V], ub[3][V], ev[V];
+        load_incidence<R, V>(ug, a.fv.eh, en, Sp, s0, ua, ub, ev);
+        apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
     }
     if constexpr (FORCE_ONLY)
         store_force<R, V>(a, i, s0, f);
@@ -480,6 +506,9 @@ __device__ __forceinline__ void batch_tile(const MemberDev<R> *__restrict__ mem,
     a.c1 = start ? m.c1s : m.c1;
     a.c2 = start ? m.c2s : m.c2;
     a.dt = m.dt;
+    a.c1f = (float)a.c1;
+    a.c2f = (float)a.c2;
+    a.dtf = (float)a.dt;
     a.force_out = nullptr;
     a.flags = flags;
     const int32_t s0 = q * V;
@@ -664,9 +693,9 @@ void note_launch(const char *what, int block, int minb, uint32_t smem, cudaError
              block, minb, smem, cudaGetErrorString(e));
 }
 
-template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V>
+template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V, bool PAIR = false>
 cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
-    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V>;
+    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V, PAIR>;
     StepArgs<R> a = a0;
     a.fv.Q = a.fv.Sp / V;
     if (plan->smem > 48 * 1024) {
@@ -694,6 +723,7 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
         } else {
             if constexpr (sizeof(R) == 4) {
                 if (plan->vw == 2) {
+                    if (plan->pair) return launch_staged<FORM, R, FO, 128, 8, 2, true>(a, s, plan);
                     if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 10, 2>(a, s, plan);
                     return launch_staged<FORM, R, FO, 256, 5, 2>(a, s, plan);
                 }
