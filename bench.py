@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-chunk", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--drift", action="store_true", help="long-run drift study instead of the benchmark")
+    ap.add_argument("--drift-arch-elems", type=int, default=100_000)
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-val", type=int, default=512)
     ap.add_argument("--sur-epochs", type=int, default=400)
@@ -427,11 +429,63 @@ def bench_surrogate(args, local, stream):
     return out
 
 
+def run_drift(args, local):
+    """Drift of the binary32 forms against the binary64 GPU form over long runs, on the same
+    4 realisations (realisations are independent, so a 4-sample ensemble steps each of them
+    exactly as the full ensemble does): the aneurysm over one 0.8 s period and a reduced
+    synthetic arch over three periods. Prints one JSON line."""
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    out = {"drift": []}
+    studies = [("aneurysm", dict(name="aneurysm", S=64), [0, 21, 42, 63], 1),
+               ("arch", dict(name="arch", S=8, target_elems=args.drift_arch_elems), [0, 3, 5, 7], 3)]
+    for label, spec, picks, periods in studies:
+        name = spec.pop("name")
+        base = synth.make_case(name, n_steps=2, seed=0, **spec)
+        dt = base["dt"]
+        n_total = int(round(periods * 0.8 / dt))
+        case = synth.make_case(name, n_steps=n_total, seed=0, **spec)
+        sub = dict(case, E=case["E"][:, picks], h=case["h"][:, picks], S=len(picks))
+        checkpoints = 16
+        chunk = n_total // checkpoints
+        ctxs = {f: pkg.Ensemble.from_case(sub, precision=f, stream=stream, device=local)
+                for f in ("fp64", "fp32_force", "kahan32")}
+        curve = {"fp32_force": [], "kahan32": []}
+        t0 = time.perf_counter()
+        for k in range(checkpoints):
+            for e in ctxs.values():
+                e.step(chunk)
+            ref = ctxs["fp64"].displacement()
+            for f in curve:
+                u = ctxs[f].displacement()
+                curve[f].append(float(np.linalg.norm(u - ref) / np.linalg.norm(ref)))
+        for e in ctxs.values():
+            e.close()
+        m = case["mesh"]
+        out["drift"].append({
+            "workload": f"{label}: {m.n_nodes} nodes, {m.n_elems} triangles, {len(picks)} realisations, "
+                        f"{periods} period(s) of 0.8 s, dt {dt:.3e} s, {chunk * checkpoints} steps",
+            "steps_per_checkpoint": chunk,
+            "rel_l2_vs_fp64_gpu": curve,
+            "max_rel_l2": {f: max(c) for f, c in curve.items()},
+            "final_rel_l2": {f: c[-1] for f, c in curve.items()},
+            "seconds": time.perf_counter() - t0,
+        })
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.drift:
+        if rank == 0:
+            run_drift(args, local)
         return
     import torch
     import synth

@@ -137,8 +137,9 @@ typedef struct {
                                2 staged 256x3, 3 staged 128x6, 4 staged 64x12
                                (threads per block x blocks per SM), 5 staged 256x5
                                and 6 staged 128x10 with two samples per thread
-                               (binary32 forms), 7 staged 128x8 with two samples
-                               per thread and two incidences per loop iteration   */
+                               (binary32 forms), 7 staged 128x9 with two samples
+                               per thread and the traction loads issued before
+                               the force loop                                     */
     float variant_us[8];    /* autotuner's time per step of each shape (-1: n/a,
                                0: not timed)                                      */
 } ens_info_t;

@@ -450,9 +450,9 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                 if (rcp == ENS_OK && c->form != kFP64) {  // two samples per thread: more warps
                     rcp = make_stage_plan(c, rowptr, 256, 5, &cand[5], 2);
                     if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 128, 10, &cand[6], 2);
-                    if (rcp == ENS_OK) {  // two incidences in flight per thread
-                        rcp = make_stage_plan(c, rowptr, 128, 8, &cand[7], 2);
-                        cand[7].pair = 1;
+                    if (rcp == ENS_OK) {  // traction loads issued before the force loop
+                        rcp = make_stage_plan(c, rowptr, 128, 9, &cand[7], 2);
+                        cand[7].hoist = 1;
                     }
                 }
             }

@@ -80,7 +80,7 @@ struct StagePlan {
     uint32_t smem;    // dynamic shared memory per block
     int32_t minb;     // resident blocks per SM the register budget targets
     int32_t vw;       // samples per thread (the binary32 forms also have a 2-sample shape)
-    int32_t pair;     // gather two incidences per loop iteration
+    int32_t hoist;    // issue the traction loads before the force loop
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or

@@ -190,15 +190,19 @@ __device__ __forceinline__ void node_traction(const StepArgs<R> &a, int32_t i, i
     }
 }
 
+// Traction of node i at this launch's step (issued early so its loads overlap the gathers).
+template <typename R>
+__device__ __forceinline__ void step_traction(const StepArgs<R> &a, int32_t i, R (&fe)[3]) {
+    node_traction<R>(a, i, *a.step_ctr + a.k_off, fe);
+}
+
 // The fused update of node i, samples [s0, s0 + V): a = (f_ext - f_int) / m, then the
 // velocity form of Eq. (dynamicsCD) with the fixed-dof mask, stored per form.
 template <int FORM, typename R, int V>
 __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int32_t s0,
-                                            const R (&ui)[3][V], const R (&f)[3][V]) {
+                                            const R (&ui)[3][V], const R (&f)[3][V],
+                                            const R (&fe)[3]) {
     const int64_t Sp = a.fv.Sp;
-    const int64_t n = *a.step_ctr + a.k_off;
-    R fe[3];
-    node_traction<R>(a, i, n, fe);
     R mi[V];
     ld_nc(a.minv + (int64_t)i * Sp + s0, mi);
     const unsigned fx = __ldg(a.fix + i);
@@ -297,6 +301,8 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
     if (g >= (int64_t)a.fv.N * Q) return;
     const int32_t i = (int32_t)(g / Q);
     const int32_t s0 = (int32_t)(g - (int64_t)i * Q) * V;
+    R fe[3] = {R(0), R(0), R(0)};
+    if constexpr (!FORCE_ONLY) step_traction<R>(a, i, fe);
     R ui[3][V];
 #pragma unroll
     for (int d = 0; d < 3; d++) ld_nc(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
     if constexpr (FORCE_ONLY)
         store_force<R, V>(a, i, s0, f);
     else
-        node_update<FORM, R, V>(a, i, s0, ui, f);
+        node_update<FORM, R, V>(a, i, s0, ui, f, fe);
 }
 
 // Staged kernel. Block b owns nodes [b nb, b nb + nb). One thread issues bulk copies
@@ -348,7 +354,8 @@ __device__ __forceinline__ void load_incidence(const R *__restrict__ ug, const R
     ld_nc(eh + (int64_t)en.x * Sp + s0, e);
 }
 
-template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V, bool PAIR = false>
+template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V,
+          bool HOIST = false>
 __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs<R> a,
                                                                   const StagePlan pl) {
     const int32_t nb_block = pl.nb;
@@ -406,6 +413,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
         }
     }
     __syncthreads();
+    // HOIST: issue the traction loads now so they overlap the staging and the gathers
+    R fe[3] = {R(0), R(0), R(0)};
+    if constexpr (!FORCE_ONLY && HOIST)
+        if (valid) step_traction<R>(a, i, fe);
     if (!mbar_wait(bar, 0, kWaitLimit)) {
         // Report, then give the copies in flight one more bounded wait before leaving.
         if (threadIdx.x == 0) atomicOr(a.flags, 2);
@@ -427,28 +438,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
 #pragma unroll
         for (int v = 0; v < V; v++) f[d][v] = R(0);
     const R *__restrict__ ug = a.ug_cur;
-    int32_t p = p0;
-    if constexpr (PAIR) {
-        // two incidences per iteration: their 2 x 7 global loads are in flight together
-        for (; p + 1 < p1; p += 2) {
-            const int4 e0 = ent_s[p], e1 = ent_s[p + 1];
-            R ua0[3][V], ub0[3][V], ev0[V], ua1[3][V], ub1[3][V], ev1[V];
-            load_incidence<R, V>(ug, a.fv.eh, e0, Sp, s0, ua0, ub0, ev0);
-            load_incidence<R, V>(ug, a.fv.eh, e1, Sp, s0, ua1, ub1, ev1);
-            apply_incidence<R, V>(ua0, ub0, ev0, kc_s + (size_t)p * KS, ui, f);
-            apply_incidence<R, V>(ua1, ub1, ev1, kc_s + (size_t)(p + 1) * KS, ui, f);
-        }
-    }
-    for (; p < p1; ++p) {
+    for (int32_t p = p0; p < p1; ++p) {
         const int4 en = ent_s[p];
         R ua[3][V], ub[3][V], ev[V];
         load_incidence<R, V>(ug, a.fv.eh, en, Sp, s0, ua, ub, ev);
         apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
     }
-    if constexpr (FORCE_ONLY)
+    if constexpr (FORCE_ONLY) {
         store_force<R, V>(a, i, s0, f);
-    else
-        node_update<FORM, R, V>(a, i, s0, ui, f);
+    } else {
+        if constexpr (!HOIST) step_traction<R>(a, i, fe);
+        node_update<FORM, R, V>(a, i, s0, ui, f, fe);
+    }
 }
 
 __global__ void advance_kernel(int64_t *ctr, int64_t n) { *ctr += n; }
@@ -516,9 +517,11 @@ __device__ __forceinline__ void batch_tile(const MemberDev<R> *__restrict__ mem,
     R ui[3][V];
 #pragma unroll
     for (int d = 0; d < 3; d++) ld_state<COH, R, V>(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
+    R fe[3];
+    step_traction<R>(a, i, fe);
     R f[3][V];
     node_force<R, V, COH>(a.fv, a.ug_cur, i, s0, ui, f);
-    node_update<FORM, R, V>(a, i, s0, ui, f);
+    node_update<FORM, R, V>(a, i, s0, ui, f, fe);
 }
 
 // Batched step: one launch advances every member one step (graph-captured in chunks).
@@ -693,9 +696,9 @@ void note_launch(const char *what, int block, int minb, uint32_t smem, cudaError
              block, minb, smem, cudaGetErrorString(e));
 }
 
-template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V, bool PAIR = false>
+template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V, bool HOIST = false>
 cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
-    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V, PAIR>;
+    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V, HOIST>;
     StepArgs<R> a = a0;
     a.fv.Q = a.fv.Sp / V;
     if (plan->smem > 48 * 1024) {
@@ -723,7 +726,7 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
         } else {
             if constexpr (sizeof(R) == 4) {
                 if (plan->vw == 2) {
-                    if (plan->pair) return launch_staged<FORM, R, FO, 128, 8, 2, true>(a, s, plan);
+                    if (plan->hoist) return launch_staged<FORM, R, FO, 128, 9, 2, true>(a, s, plan);
                     if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 10, 2>(a, s, plan);
                     return launch_staged<FORM, R, FO, 256, 5, 2>(a, s, plan);
                 }
