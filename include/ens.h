@@ -139,8 +139,9 @@ typedef struct {
                                and 6 staged 128x10 with two samples per thread
                                (binary32 forms), 7 staged 128x9 with two samples
                                per thread and the traction loads issued before
-                               the force loop                                     */
-    float variant_us[8];    /* autotuner's time per step of each shape (-1: n/a,
+                               the force loop, 8 and 9 persistent double-buffered
+                               forms of 5 and 6                                   */
+    float variant_us[10];   /* autotuner's time per step of each shape (-1: n/a,
                                0: not timed)                                      */
 } ens_info_t;
 

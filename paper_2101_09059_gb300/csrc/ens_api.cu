@@ -194,8 +194,19 @@ int make_stage_plan(ens_ctx *c, const std::vector<int32_t> &rowptr, int32_t bloc
     p.nb = nb;
     p.cnt_max = cmax;
     p.smem = (uint32_t)((bytes + 127) / 128 * 128);
+    // one staging buffer without the barrier: entries, coupling blocks, own rows
+    p.stage = (uint32_t)(((bytes - 16) + 127) / 128 * 128);
     *out = p;
     return ENS_OK;
+}
+
+// The pipelined (persistent, double-buffered) form of a staged plan.
+StagePlan pipelined_plan(StagePlan p) {
+    if (!p.staged) return p;
+    p.pipelined = 1;
+    p.smem = 16 + 2 * p.stage;
+    if (p.smem > 160 * 1024) p.staged = 0;
+    return p;
 }
 
 // Launch-shape autotuner: time a few steps of every candidate shape on this context's
@@ -454,6 +465,9 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                         rcp = make_stage_plan(c, rowptr, 128, 9, &cand[7], 2);
                         cand[7].hoist = 1;
                     }
+                    // persistent CTAs with a double-buffered staging ring
+                    cand[8] = pipelined_plan(cand[5]);
+                    cand[9] = pipelined_plan(cand[6]);
                 }
             }
             if (rcp != ENS_OK) return rcp;

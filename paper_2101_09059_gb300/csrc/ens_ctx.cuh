@@ -9,7 +9,7 @@
 #include "ens_internal.cuh"
 
 namespace ens {
-constexpr int kVariants = 8;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kVariants = 10;  // launch shapes the autotuner can time (see ens_info_t)
 constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
 }
 
@@ -46,7 +46,7 @@ struct ens_ctx {
     ens::StagePlan plan{};     // launch shape of the step kernel
     ens::StagePlan plan_fo{};  // launch shape of force-only evaluations
     int32_t variant = 0;
-    float variant_us[ens::kVariants] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float variant_us[ens::kVariants] = {};
     int32_t flags_in = 0;
     // time-loop graph of kGraphSteps launches + counter advance (see ens_step)
     cudaStream_t cap = nullptr;

@@ -81,6 +81,9 @@ struct StagePlan {
     int32_t minb;     // resident blocks per SM the register budget targets
     int32_t vw;       // samples per thread (the binary32 forms also have a 2-sample shape)
     int32_t hoist;    // issue the traction loads before the force loop
+    int32_t pipelined;  // persistent CTAs with a double-buffered staging ring
+    uint32_t stage;     // bytes of one staging buffer (pipelined plans)
+    int32_t grid;       // CTAs of a pipelined launch (0: computed at first launch)
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or

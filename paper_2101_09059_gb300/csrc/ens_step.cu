@@ -452,6 +452,124 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     }
 }
 
+// Persistent, double-buffered form of the staged kernel. Each CTA walks the node tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps the bulk copies (TMA) of the
+// tile after next in flight in the other half of a two-buffer shared-memory ring while the
+// block computes the current tile, so no block waits for its own staging after the first
+// tile. Waits are bounded; all threads agree on the outcome through a block vote.
+template <int FORM, typename R, int BLOCK, int MINB, int V>
+__global__ void __launch_bounds__(BLOCK, MINB) step_pipelined_kernel(const StepArgs<R> a,
+                                                                     const StagePlan pl,
+                                                                     const int32_t n_tiles) {
+    constexpr int KS = Kc<R>::stride;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    const int32_t Sp = a.fv.Sp, Q = a.fv.Q, N = a.fv.N;
+    const int32_t nb_block = pl.nb, cnt_max = pl.cnt_max;
+    const int32_t li = threadIdx.x / Q;
+    const int32_t s0 = (threadIdx.x - li * Q) * V;
+    auto stage_of = [&](int b) { return smem + 16 + (size_t)b * pl.stage; };
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    // thread 0: stage tile `tile` into buffer `b` (entries, coupling blocks, own rows)
+    auto issue = [&](int32_t tile, int b) -> bool {
+        const int32_t n0 = tile * nb_block;
+        const int32_t nb = min(nb_block, N - n0);
+        const int32_t pb = __ldg(a.fv.rowptr + n0);
+        const int32_t cnt = __ldg(a.fv.rowptr + n0 + nb) - pb;
+        if (cnt < 1 || cnt > cnt_max) return false;
+        // the block's generic-proxy reads of this buffer precede the bulk copies into it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        unsigned char *st = stage_of(b);
+        int4 *ent_s = reinterpret_cast<int4 *>(st);
+        R *kc_s = reinterpret_cast<R *>(ent_s + cnt_max);
+        R *ug_s = kc_s + (size_t)cnt_max * KS;
+        const uint32_t row_bytes = (uint32_t)(nb * 3 * Sp * sizeof(R));
+        const uint32_t b_ent = (uint32_t)cnt * 16u;
+        const uint32_t b_kc = (uint32_t)cnt * KS * (uint32_t)sizeof(R);
+        mbar_expect_tx(&bars[b], b_ent + b_kc + row_bytes);
+        bulk_g2s(ent_s, a.fv.ent + pb, b_ent, &bars[b]);
+        bulk_g2s(kc_s, a.fv.kc + (size_t)pb * KS, b_kc, &bars[b]);
+        bulk_g2s(ug_s, a.ug_cur + (size_t)n0 * 3 * Sp, row_bytes, &bars[b]);
+        const size_t r0 = (size_t)n0 * 3 * Sp;
+        const uint32_t rows = (uint32_t)nb * 3u * (uint32_t)Sp;
+        bulk_prefetch_l2(a.minv + (size_t)n0 * Sp, (uint32_t)(nb * Sp * sizeof(R)));
+        if constexpr (FORM == kKahan32) {
+            bulk_prefetch_l2(a.ulo + r0, rows * 4u);
+            bulk_prefetch_l2(a.v32 + r0, rows * 4u);
+        } else if constexpr (FORM == kFP32Force) {
+            bulk_prefetch_l2(a.u64 + r0, rows * 8u);
+            bulk_prefetch_l2(a.v64 + r0, rows * 8u);
+        } else {
+            bulk_prefetch_l2(a.v64 + r0, rows * 8u);
+        }
+        return true;
+    };
+    __shared__ int issued[2];
+    if (threadIdx.x == 0) {
+        issued[0] = blockIdx.x < n_tiles ? (issue(blockIdx.x, 0) ? 1 : -1) : 0;
+        issued[1] = blockIdx.x + (int)gridDim.x < n_tiles ? (issue(blockIdx.x + gridDim.x, 1) ? 1 : -1) : 0;
+    }
+    __syncthreads();
+    uint32_t uses[2] = {0u, 0u};
+    int b = 0;
+    for (int32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        bool ok = issued[b] == 1 && mbar_wait(&bars[b], uses[b] & 1u, kWaitLimit);
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            // report, then give every copy in flight one more bounded wait before leaving
+            if (threadIdx.x == 0) atomicOr(a.flags, issued[b] == -1 ? 4 : 2);
+            for (int k = 0; k < 2; k++)
+                if (issued[k] == 1) mbar_wait(&bars[k], uses[k] & 1u, kWaitLimit);
+            return;
+        }
+        uses[b]++;
+        const int32_t n0 = t * nb_block;
+        const int32_t nb = min(nb_block, N - n0);
+        const int32_t i = n0 + li;
+        if (li < nb) {
+            unsigned char *st = stage_of(b);
+            const int4 *ent_s = reinterpret_cast<const int4 *>(st);
+            const R *kc_s = reinterpret_cast<const R *>(ent_s + cnt_max);
+            const R *ug_s = kc_s + (size_t)cnt_max * KS;
+            const int32_t pb = __ldg(a.fv.rowptr + n0);
+            const int32_t p0 = __ldg(a.fv.rowptr + i) - pb, p1 = __ldg(a.fv.rowptr + i + 1) - pb;
+            R ui[3][V];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const R *src = ug_s + ((size_t)li * 3 + d) * Sp + s0;
+#pragma unroll
+                for (int v = 0; v < V; v++) ui[d][v] = src[v];
+            }
+            R f[3][V];
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int v = 0; v < V; v++) f[d][v] = R(0);
+            for (int32_t p = p0; p < p1; ++p) {
+                const int4 en = ent_s[p];
+                R ua[3][V], ub[3][V], ev[V];
+                load_incidence<R, V>(a.ug_cur, a.fv.eh, en, Sp, s0, ua, ub, ev);
+                apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
+            }
+            R fe[3];
+            step_traction<R>(a, i, fe);
+            node_update<FORM, R, V>(a, i, s0, ui, f, fe);
+        }
+        __syncthreads();  // the whole block is done with buffer b
+        if (threadIdx.x == 0) {
+            const int32_t next = t + 2 * (int32_t)gridDim.x;
+            issued[b] = next < n_tiles ? (issue(next, b) ? 1 : -1) : 0;
+        }
+        __syncthreads();
+        b ^= 1;
+    }
+}
+
 __global__ void advance_kernel(int64_t *ctr, int64_t n) { *ctr += n; }
 
 // Deterministic non-zero values of magnitude <= scale (an integer hash of the index).
@@ -716,6 +834,34 @@ cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan
     return e;
 }
 
+template <int FORM, typename R, int BLOCK, int MINB, int V>
+cudaError_t launch_pipelined(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
+    auto *k = step_pipelined_kernel<FORM, R, BLOCK, MINB, V>;
+    StepArgs<R> a = a0;
+    a.fv.Q = a.fv.Sp / V;
+    if (plan->smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+        if (e != cudaSuccess) {
+            note_launch("cudaFuncSetAttribute", BLOCK, MINB, plan->smem, e);
+            return e;
+        }
+    }
+    const int32_t n_tiles = (a.fv.N + plan->nb - 1) / plan->nb;
+    int grid = plan->grid;
+    if (grid <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLOCK, plan->smem);
+        grid = sms * (per > 0 ? per : 1);
+    }
+    if (grid > n_tiles) grid = n_tiles;
+    k<<<grid, BLOCK, plan->smem, s>>>(a, *plan, n_tiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) note_launch("pipelined launch", BLOCK, MINB, plan->smem, e);
+    return e;
+}
+
 template <int FORM, typename R, bool FO>
 cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
     const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
@@ -725,6 +871,10 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
             if (plan->block == 256 && plan->minb == 4) return launch_staged<FORM, R, FO, 256, 4>(a, s, plan);
         } else {
             if constexpr (sizeof(R) == 4) {
+                if (plan->pipelined) {
+                    if (plan->block == 128) return launch_pipelined<FORM, R, 128, 8, 2>(a, s, plan);
+                    return launch_pipelined<FORM, R, 256, 4, 2>(a, s, plan);
+                }
                 if (plan->vw == 2) {
                     if (plan->hoist) return launch_staged<FORM, R, FO, 128, 9, 2, true>(a, s, plan);
                     if (plan->block == 128) return launch_staged<FORM, R, FO, 128, 10, 2>(a, s, plan);
