@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-chunk", type=int, default=100)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--force-variant", type=int, default=-1,
+                    help="use this step-kernel launch shape instead of autotuning (profiling)")
     ap.add_argument("--drift", action="store_true", help="long-run drift study instead of the benchmark")
     ap.add_argument("--drift-arch-elems", type=int, default=100_000)
     ap.add_argument("--sur-train", type=int, default=4096)
@@ -172,19 +174,19 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-def step_kernel_traffic(form):
-    """DRAM bytes per step-kernel launch from a committed ncu capture, if the kernel
-    source it was taken on is unchanged (else None)."""
+def step_kernel_traffic(form, variant):
+    """DRAM bytes per step-kernel launch of `form` in launch shape `variant`, from a
+    committed ncu capture, if the kernel source it was taken on is unchanged (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     src = os.path.join(ROOT, "paper_2101_09059_gb300", "csrc", "ens_step.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    ent = d.get(form)
-    if not ent or ent.get("source_sha") != sha:
+    if d.get("source_sha") != sha:
         return None
-    return ent.get("bytes_per_launch")
+    ent = d.get("forms", {}).get(form, {}).get(str(variant))
+    return None if not ent else ent.get("bytes_per_launch")
 
 
 def run_reference(args, world, rank):
@@ -502,8 +504,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     results, finals = {}, {}
     hbm_peak, peak_kind = peaks()
+    flags = pkg.ensemble.FLAG_FORCE_VARIANT(args.force_variant) if args.force_variant >= 0 else 0
     for form in forms:
-        e = pkg.Ensemble.from_case(case, precision=form, stream=stream, device=local)
+        e = pkg.Ensemble.from_case(case, precision=form, stream=stream, device=local, flags=flags)
         info = e.info()
         mean = torch.empty((N, 3), dtype=torch.float64, device=dev)
         var = torch.empty_like(mean)
@@ -589,7 +592,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case, S)
 
-    traffic = step_kernel_traffic(head)
+    traffic = step_kernel_traffic(head, h.get("kernel_variant"))
     info_bytes = BYTES_NS[head] * N * S + m.n_elems * 64.0 + N * (12.0 + 24.0 * case["modes"].shape[0])
     achieved = info_bytes / (h["kernel_us"] * 1e-6) / 1e9
     out = {

@@ -45,15 +45,20 @@ extern "C" {
 #define ENS_ERR_ALLOC (-2)       /* device allocation failed                           */
 #define ENS_ERR_CUDA (-3)        /* a CUDA runtime call failed (message has the name)  */
 #define ENS_ERR_UNSTABLE_DT (-4) /* dt is above the central-difference stability limit */
-#define ENS_ERR_NONFINITE (-5)   /* a displacement became Inf or NaN                   */
+#define ENS_ERR_NONFINITE (-5)   /* a displacement became Inf or NaN (FP32-force: left
+                                    the binary32 range)                                 */
 #define ENS_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up                 */
 #define ENS_ERR_RANGE (-7)       /* stepping past the end of the traction table        */
 #define ENS_ERR_STATE (-8)       /* call not valid in the current state                */
 
 /* ---- precision forms ------------------------------------------------------------
  * ENS_FP64       : every operation in IEEE binary64.
- * ENS_FP32_FORCE : element forces K_s u in binary32 from a binary32 copy of u; the
- *                  displacement and velocity state and their update stay binary64.
+ * ENS_FP32_FORCE : element forces K_s u in binary32 from u truncated to binary32; the
+ *                  displacement and velocity state and their update stay binary64. The
+ *                  displacement is stored bit-split (its binary32 truncation, which the
+ *                  forces read, and the 29 mantissa bits below it), exact for magnitudes
+ *                  in [2^-126, 2^128); smaller magnitudes are held as zero and larger ones
+ *                  end the run with ENS_ERR_NONFINITE.
  * ENS_KAHAN32    : forces in binary32; the displacement is a compensated pair of
  *                  binary32 values (hi + lo) updated with an error-free sum, the
  *                  velocity is binary32.                                              */

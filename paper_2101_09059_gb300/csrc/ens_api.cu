@@ -218,7 +218,8 @@ int autotune(ens_ctx *c, const StagePlan *cand, int n) {
     const int dbl = c->form == kFP64;
     CK(launch_fill(c->ug[0], ns, dbl, 1e-4f, 1u, c->stream));
     CK(launch_fill(c->ug[1], ns, dbl, 1e-4f, 2u, c->stream));
-    if (c->u64) CK(launch_fill(c->u64, ns, 1, 1e-4f, 3u, c->stream));
+    // FP32-force tails: any 29-bit pattern is a valid state; zeros do the same work
+    if (c->utail) CK(cudaMemsetAsync(c->utail, 0, 4 * ns, c->stream));
     if (c->v64) CK(launch_fill(c->v64, ns, 1, 1e-2f, 4u, c->stream));
     if (c->ulo) CK(launch_fill(c->ulo, ns, 0, 1e-11f, 5u, c->stream));
     if (c->v32) CK(launch_fill(c->v32, ns, 0, 1e-2f, 6u, c->stream));
@@ -270,9 +271,13 @@ int autotune(ens_ctx *c, const StagePlan *cand, int n) {
     return rc;
 }
 
-const void *state_main(const ens_ctx *c) {
-    if (c->form == kFP32Force) return c->u64;
-    return c->ug[c->cur];
+const void *state_main(const ens_ctx *c) { return c->ug[c->cur]; }
+
+// The second state word array of the binary32 forms (compensated low parts or FP32-force
+// tails), nullptr for FP64.
+const void *state_aux(const ens_ctx *c) {
+    if (c->form == kFP32Force) return c->utail;
+    return c->ulo;
 }
 
 }  // namespace
@@ -534,7 +539,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         } else if (c->form == kFP32Force) {
             c->ug[0] = dev_alloc(c, srow);
             c->ug[1] = dev_alloc(c, srow);
-            ALLOC(c->u64, double, (int64_t)N * 3 * c->Sp);
+            ALLOC(c->utail, uint32_t, (int64_t)N * 3 * c->Sp);
             ALLOC(c->v64, double, (int64_t)N * 3 * c->Sp);
         } else {
             c->ug[0] = dev_alloc(c, srow);
@@ -569,7 +574,7 @@ int ens_reset(ens_ctx *c) {
     const size_t es = c->form == kFP64 ? 8 : 4;
     CK(cudaMemsetAsync(c->ug[0], 0, es * n, c->stream));
     CK(cudaMemsetAsync(c->ug[1], 0, es * n, c->stream));
-    if (c->u64) CK(cudaMemsetAsync(c->u64, 0, 8 * n, c->stream));
+    if (c->utail) CK(cudaMemsetAsync(c->utail, 0, 4 * n, c->stream));
     if (c->v64) CK(cudaMemsetAsync(c->v64, 0, 8 * n, c->stream));
     if (c->ulo) CK(cudaMemsetAsync(c->ulo, 0, 4 * n, c->stream));
     if (c->v32) CK(cudaMemsetAsync(c->v32, 0, 4 * n, c->stream));
@@ -736,7 +741,7 @@ int ens_get_displacement_device(ens_ctx *c, double *out, int32_t layout) {
     if (!c) return ENS_ERR_INVALID_ARG;
     if (!out || (layout != ENS_LAYOUT_SNC && layout != ENS_LAYOUT_NCS))
         return fail(c, ENS_ERR_INVALID_ARG, "output pointer or layout");
-    CK(launch_export(c->form, state_main(c), c->ulo, c->N, c->S, c->Sp, out, layout, c->stream));
+    CK(launch_export(c->form, state_main(c), state_aux(c), c->N, c->S, c->Sp, out, layout, c->stream));
     return ENS_OK;
 }
 
@@ -759,7 +764,7 @@ int ens_get_displacement(ens_ctx *c, double *out, int32_t layout) {
 int ens_stats_device(ens_ctx *c, double *mean, double *var) {
     if (!c) return ENS_ERR_INVALID_ARG;
     if (!mean || !var) return fail(c, ENS_ERR_INVALID_ARG, "null output");
-    CK(launch_stats(c->form, state_main(c), c->ulo, c->N, c->S, c->Sp, mean, var, c->stream));
+    CK(launch_stats(c->form, state_main(c), state_aux(c), c->N, c->S, c->Sp, mean, var, c->stream));
     return ENS_OK;
 }
 
@@ -789,7 +794,7 @@ int ens_internal_force(ens_ctx *c, const double *u, double *f) {
     cudaError_t e = cudaSuccess;
     if (rc == ENS_OK) {
         e = cudaMemcpyAsync(in_d, u, 8 * n, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = launch_import(c->form, in_d, c->N, c->S, c->Sp, ug, nullptr, nullptr, c->stream);
+        if (e == cudaSuccess) e = launch_import(c->form, in_d, c->N, c->S, c->Sp, ug, c->stream);
         if (e == cudaSuccess) {
             if (c->form == kFP64) {
                 StepArgs<double> a = make_args<double>(c);
@@ -884,13 +889,13 @@ struct StateHeader {
     int64_t step;
     int64_t reserved[3];
 };
-const uint64_t kMagic = 0x31534e4557435345ull;  // "ESCWENS1"
+const uint64_t kMagic = 0x32534e4557435345ull;  // "ESCWENS2"
 
 size_t state_bytes(const ens_ctx *c) {
     const size_t n = (size_t)c->N * 3 * c->Sp;
     size_t b = sizeof(StateHeader);
     if (c->form == kFP64) b += 16 * n;                // u, v
-    else if (c->form == kFP32Force) b += 20 * n;      // u64, v64, u32 copy
+    else if (c->form == kFP32Force) b += 16 * n;      // binary32 heads, tails, v64
     else b += 12 * n;                                 // hi, lo, v
     return b;
 }
@@ -918,7 +923,7 @@ int ens_get_state(ens_ctx *c, void *buf, size_t bytes) {
     if (c->form == kFP64) {
         if ((rc = get(c->ug[c->cur], 8 * n)) || (rc = get(c->v64, 8 * n))) return rc;
     } else if (c->form == kFP32Force) {
-        if ((rc = get(c->u64, 8 * n)) || (rc = get(c->v64, 8 * n)) || (rc = get(c->ug[c->cur], 4 * n)))
+        if ((rc = get(c->ug[c->cur], 4 * n)) || (rc = get(c->utail, 4 * n)) || (rc = get(c->v64, 8 * n)))
             return rc;
     } else {
         if ((rc = get(c->ug[c->cur], 4 * n)) || (rc = get(c->ulo, 4 * n)) || (rc = get(c->v32, 4 * n)))
@@ -949,7 +954,7 @@ int ens_set_state(ens_ctx *c, const void *buf, size_t bytes) {
     if (c->form == kFP64) {
         if ((rc = put(c->ug[0], 8 * n)) || (rc = put(c->v64, 8 * n))) return rc;
     } else if (c->form == kFP32Force) {
-        if ((rc = put(c->u64, 8 * n)) || (rc = put(c->v64, 8 * n)) || (rc = put(c->ug[0], 4 * n)))
+        if ((rc = put(c->ug[0], 4 * n)) || (rc = put(c->utail, 4 * n)) || (rc = put(c->v64, 8 * n)))
             return rc;
     } else {
         if ((rc = put(c->ug[0], 4 * n)) || (rc = put(c->ulo, 4 * n)) || (rc = put(c->v32, 4 * n)))
@@ -1046,7 +1051,7 @@ extern "C" int ens_internal_force_noalloc(ens_ctx *c, const double *u_dev, doubl
     if (rc != ENS_OK) return rc;
     void *ug = base;
     double *f_pad = (double *)((char *)base + gbytes);
-    CK(launch_import(c->form, u_dev, c->N, c->S, c->Sp, ug, nullptr, nullptr, c->stream));
+    CK(launch_import(c->form, u_dev, c->N, c->S, c->Sp, ug, c->stream));
     cudaError_t e;
     if (c->form == kFP64) {
         StepArgs<double> a = make_args<double>(c);

@@ -67,7 +67,7 @@ MemberDev<R> member_of(ens_ctx *c, bool tuning) {
     d.fv.Q = c->Q;
     d.ug[0] = (const R *)c->ug[0];
     d.ug[1] = (const R *)c->ug[1];
-    d.u64 = c->u64;
+    d.utail = c->utail;
     d.v64 = c->v64;
     d.ulo = c->ulo;
     d.v32 = c->v32;
@@ -276,7 +276,7 @@ std::vector<std::pair<void *, size_t>> state_buffers(ens_ctx *c) {
     const size_t n = (size_t)c->N * 3 * c->Sp;
     const size_t es = elem_size(c->form);
     std::vector<std::pair<void *, size_t>> v = {{c->ug[0], es * n}, {c->ug[1], es * n}};
-    if (c->u64) v.push_back({c->u64, 8 * n});
+    if (c->utail) v.push_back({c->utail, 4 * n});
     if (c->v64) v.push_back({c->v64, 8 * n});
     if (c->ulo) v.push_back({c->ulo, 4 * n});
     if (c->v32) v.push_back({c->v32, 4 * n});

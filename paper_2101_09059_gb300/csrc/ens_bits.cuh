@@ -60,6 +60,41 @@ __device__ __forceinline__ float f64_to_f32_rz(double d) {
     return __uint_as_float(out);
 }
 
+// ---- bit-split binary64 state ---------------------------------------------------------
+// The FP32-force form keeps each binary64 displacement u as two 32-bit words:
+//   head = u truncated to binary32 (the value neighbours gather for the forces), and
+//   tail = the 29 low mantissa bits of u that the truncation drops.
+// For |u| in [2^-126, 2^128) the pair holds u exactly (binary32 and binary64 mantissas
+// differ by 29 bits); smaller magnitudes are stored as signed zero, and larger ones or
+// non-finite u are reported as out of range. The state then needs 8 bytes per dof with
+// no separate binary32 copy for the gather.
+
+// Split u into (head, tail); returns false when |u| >= 2^128 or u is not finite.
+__device__ __forceinline__ bool split_state(double u, float &head, uint32_t &tail) {
+    const uint32_t hw = (uint32_t)((uint64_t)__double_as_longlong(u) >> 32);
+    const uint32_t lw = (uint32_t)__double_as_longlong(u);
+    const uint32_t mag = hw & 0x7fffffffu;
+    const uint32_t sign = hw & 0x80000000u;
+    // binary64 exponent field e in [897, 1150] <=> mag in [897 << 20, 1151 << 20)
+    const bool normal = mag - (897u << 20) < ((1151u - 897u) << 20);
+    // (e mod 2^9, top 23 mantissa bits), then the exponent rebiased by 896: subtracting
+    // 896 * 2^23 mod 2^32 = 0xC0000000 leaves e - 896 in bits 23..31, exact for e in
+    // range since 1 <= e - 896 < 2^8
+    const uint32_t hb = (__funnelshift_l(lw, hw, 3) - 0xC0000000u) & 0x7fffffffu;
+    head = __uint_as_float(normal ? (sign | hb) : sign);
+    tail = normal ? (lw & 0x1fffffffu) : 0u;
+    return mag < (1151u << 20);
+}
+
+// Rebuild u from (head, tail) written by split_state (head is a normal binary32 or zero).
+__device__ __forceinline__ double join_state(float head, uint32_t tail) {
+    const uint32_t b = __float_as_uint(head);
+    const uint32_t mag = b & 0x7fffffffu;
+    const uint32_t hw = mag ? ((b & 0x80000000u) | ((mag >> 3) + (896u << 20))) : b;
+    const uint32_t lw = (b << 29) | tail;
+    return __longlong_as_double((long long)(((uint64_t)hw << 32) | lw));
+}
+
 // ---- mbarrier and bulk copies (PTX ISA: mbarrier, cp.async.bulk) --------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);

@@ -36,7 +36,8 @@ struct ens_ctx {
     int32_t *ec2ent_d = nullptr;
     void *kc = nullptr, *eh = nullptr, *minv = nullptr, *modes = nullptr, *amp = nullptr;
     void *ug[2] = {nullptr, nullptr};
-    double *u64 = nullptr, *v64 = nullptr;
+    uint32_t *utail = nullptr;  // FP32-force: low mantissa bits of the binary64 state
+    double *v64 = nullptr;
     float *ulo = nullptr, *v32 = nullptr;
     int *flags = nullptr;
     int64_t *step_ctr = nullptr;
@@ -75,7 +76,7 @@ StepArgs<R> make_args(ens_ctx *c) {
     a.fv.N = c->N;
     a.fv.Sp = c->Sp;
     a.fv.Q = c->Q;
-    a.u64 = c->u64;
+    a.utail = c->utail;
     a.v64 = c->v64;
     a.ulo = c->ulo;
     a.v32 = c->v32;

@@ -44,14 +44,15 @@ struct ForceView {
 
 // Arguments of one step (or one force evaluation) for every form.
 //   kFP64      : ug = u (double, ping-pong), v (double, in place)
-//   kFP32Force : ug = binary32 copy of u (ping-pong), u64 / v64 binary64 (in place)
+//   kFP32Force : binary64 u stored bit-split: ug = its binary32 truncation (ping-pong),
+//                utail = the 29 mantissa bits below it (in place); v64 binary64 (in place)
 //   kKahan32   : ug = hi part of u (ping-pong), ulo (in place), v32 (in place)
 template <typename R>
 struct StepArgs {
     ForceView<R> fv;
     const R *ug_cur;  // gathered displacement at step n
     R *ug_next;       // written: displacement at step n + 1 (gather precision)
-    double *u64;      // kFP32Force state
+    uint32_t *utail;  // kFP32Force low mantissa bits of the binary64 state
     double *v64;      // kFP64 / kFP32Force velocity
     float *ulo;       // kKahan32 low part
     float *v32;       // kKahan32 velocity
@@ -92,7 +93,8 @@ template <typename R>
 struct MemberDev {
     ForceView<R> fv;
     const R *ug[2];         // ping-pong gathered displacement buffers
-    double *u64, *v64;
+    uint32_t *utail;
+    double *v64;
     float *ulo, *v32;
     const R *minv;
     const uint8_t *fix;
@@ -131,12 +133,14 @@ int batch_persistent_grid(int form, int block);  // co-resident blocks of the pe
 cudaError_t launch_advance_many(int64_t *const *ctrs, int32_t n, int64_t by, cudaStream_t s);
 cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s);
 cudaError_t launch_fill(void *p, int64_t n, int is_double, float scale, uint32_t seed, cudaStream_t s);
-cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
+// u_main: the state's gathered buffer (binary64 u for the FP64 form); aux: the compensated
+// form's low parts or the FP32-force form's tails (unused for FP64).
+cudaError_t launch_stats(int form, const void *u_main, const void *aux, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s);
-cudaError_t launch_export(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
+cudaError_t launch_export(int form, const void *u_main, const void *aux, int32_t N, int32_t S,
                           int32_t Sp, double *out, int layout, cudaStream_t s);
 cudaError_t launch_import(int form, const double *in_ncs, int32_t N, int32_t S, int32_t Sp,
-                          void *ug, double *u64, float *ulo, cudaStream_t s);
+                          void *ug, cudaStream_t s);
 
 // Setup launchers (ens_setup.cu).
 cudaError_t launch_setup_elements(const double *xyz, const int32_t *tri, const int32_t *ec2ent,

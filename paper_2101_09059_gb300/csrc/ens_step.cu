@@ -84,6 +84,25 @@ __device__ __forceinline__ void st_wb(float *p, const float (&x)[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
 }
 
+__device__ __forceinline__ void ld_cs(const uint32_t *p, uint32_t (&x)[2]) {
+    uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+}
+__device__ __forceinline__ void ld_cs(const uint32_t *p, uint32_t (&x)[4]) {
+    uint4 t = __ldcs(reinterpret_cast<const uint4 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+}
+__device__ __forceinline__ void st_cs(uint32_t *p, const uint32_t (&x)[2]) {
+    __stcs(reinterpret_cast<uint2 *>(p), make_uint2(x[0], x[1]));
+}
+__device__ __forceinline__ void st_cs(uint32_t *p, const uint32_t (&x)[4]) {
+    __stcs(reinterpret_cast<uint4 *>(p), make_uint4(x[0], x[1], x[2], x[3]));
+}
+
 // Coupling blocks of one incidence: 18 values.
 __device__ __forceinline__ void ld_kc(const double *p, double (&k)[18]) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
@@ -225,12 +244,13 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             st_cs(a.v64 + row, vv);
             st_wb(a.ug_next + row, un);
         } else if constexpr (FORM == kFP32Force) {
-            double uu[V], vv[V], h2[2];
+            // binary64 u = (head ui, tail); the update runs in binary64, the bit splits and
+            // the conversion of the binary32 acceleration on the integer pipe
+            double vv[V], h2[2];
+            uint32_t tl[V];
+            ld_cs(a.utail + row, tl);
 #pragma unroll
             for (int q = 0; q < V; q += 2) {
-                ld_cs(a.u64 + row + q, h2);
-                uu[q] = h2[0];
-                uu[q + 1] = h2[1];
                 ld_cs(a.v64 + row + q, h2);
                 vv[q] = h2[0];
                 vv[q + 1] = h2[1];
@@ -240,19 +260,14 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float acc = (fe[d] - f[d][v]) * mi[v];
-                // binary64 state update; the conversions run on the integer pipe
                 const double vn = held ? 0.0 : fma(a.c1, vv[v], f32_to_f64(c2 * acc));
-                const double un = held ? 0.0 : fma(a.dt, vn, uu[v]);
+                const double un = held ? 0.0 : fma(a.dt, vn, join_state(ui[d][v], tl[v]));
                 vv[v] = vn;
-                uu[v] = un;
-                ug[v] = f64_to_f32_rz(un);
-                bad |= !isfinite(ug[v]);
+                bad |= !split_state(un, ug[v], tl[v]);
             }
+            st_cs(a.utail + row, tl);
 #pragma unroll
-            for (int q = 0; q < V; q += 2) {
-                st_cs(a.u64 + row + q, {uu[q], uu[q + 1]});
-                st_cs(a.v64 + row + q, {vv[q], vv[q + 1]});
-            }
+            for (int q = 0; q < V; q += 2) st_cs(a.v64 + row + q, {vv[q], vv[q + 1]});
             st_wb(a.ug_next + row, ug);
         } else {  // kKahan32
             float lo[V], vv[V], hi[V];
@@ -405,7 +420,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
                 bulk_prefetch_l2(a.ulo + r0, (uint32_t)(nb * 3 * Sp * 4));
                 bulk_prefetch_l2(a.v32 + r0, (uint32_t)(nb * 3 * Sp * 4));
             } else if constexpr (FORM == kFP32Force) {
-                bulk_prefetch_l2(a.u64 + r0, (uint32_t)(nb * 3 * Sp * 8));
+                bulk_prefetch_l2(a.utail + r0, (uint32_t)(nb * 3 * Sp * 4));
                 bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
             } else {
                 bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
@@ -502,7 +517,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_pipelined_kernel(const StepA
             bulk_prefetch_l2(a.ulo + r0, rows * 4u);
             bulk_prefetch_l2(a.v32 + r0, rows * 4u);
         } else if constexpr (FORM == kFP32Force) {
-            bulk_prefetch_l2(a.u64 + r0, rows * 8u);
+            bulk_prefetch_l2(a.utail + r0, rows * 4u);
             bulk_prefetch_l2(a.v64 + r0, rows * 8u);
         } else {
             bulk_prefetch_l2(a.v64 + r0, rows * 8u);
@@ -610,7 +625,7 @@ __device__ __forceinline__ void batch_tile(const MemberDev<R> *__restrict__ mem,
     const int par = m.cur ^ (k_off & 1);
     a.ug_cur = m.ug[par];
     a.ug_next = const_cast<R *>(m.ug[par ^ 1]);
-    a.u64 = m.u64;
+    a.utail = m.utail;
     a.v64 = m.v64;
     a.ulo = m.ulo;
     a.v32 = m.v32;
@@ -697,18 +712,22 @@ __global__ void __launch_bounds__(BLOCK) batch_persistent_kernel(
 constexpr int kStatLanes = 8;
 constexpr int kStatRegs = 16;
 
+// Value of sample s of state row `row` as binary64, for any form (aux: the compensated
+// form's low parts, or the FP32-force form's tails), integer-pipe conversions.
 template <int FORM>
-__device__ __forceinline__ double state_value_fast(const void *u_main, const float *ulo,
+__device__ __forceinline__ double state_value_fast(const void *u_main, const void *aux,
                                                    int64_t idx) {
     if constexpr (FORM == kKahan32)
-        return f32_to_f64(((const float *)u_main)[idx]) + f32_to_f64(ulo[idx]);
+        return f32_to_f64(((const float *)u_main)[idx]) + f32_to_f64(((const float *)aux)[idx]);
+    else if constexpr (FORM == kFP32Force)
+        return join_state(((const float *)u_main)[idx], ((const uint32_t *)aux)[idx]);
     else
         return ((const double *)u_main)[idx];
 }
 
 template <int FORM>
 __global__ void __launch_bounds__(256) stats_kernel(const void *__restrict__ u_main,
-                                                    const float *__restrict__ ulo, int32_t N,
+                                                    const void *__restrict__ aux, int32_t N,
                                                     int32_t S, int32_t Sp, double inv_s,
                                                     double inv_s1, double *__restrict__ mean,
                                                     double *__restrict__ var) {
@@ -725,11 +744,11 @@ __global__ void __launch_bounds__(256) stats_kernel(const void *__restrict__ u_m
 #pragma unroll
             for (int k = 0; k < kStatRegs; k++) {
                 const int32_t j = g + k * kStatLanes;
-                x[k] = j < S ? state_value_fast<FORM>(u_main, ulo, base + j) : 0.0;
+                x[k] = j < S ? state_value_fast<FORM>(u_main, aux, base + j) : 0.0;
                 s += x[k];
             }
         } else {
-            for (int32_t j = g; j < S; j += kStatLanes) s += state_value_fast<FORM>(u_main, ulo, base + j);
+            for (int32_t j = g; j < S; j += kStatLanes) s += state_value_fast<FORM>(u_main, aux, base + j);
         }
     }
 #pragma unroll
@@ -746,7 +765,7 @@ __global__ void __launch_bounds__(256) stats_kernel(const void *__restrict__ u_m
             }
         } else {
             for (int32_t j = g; j < S; j += kStatLanes) {
-                const double d = state_value_fast<FORM>(u_main, ulo, base + j) - mu;
+                const double d = state_value_fast<FORM>(u_main, aux, base + j) - mu;
                 q = fma(d, d, q);
             }
         }
@@ -759,50 +778,35 @@ __global__ void __launch_bounds__(256) stats_kernel(const void *__restrict__ u_m
     }
 }
 
-// Value of sample s of state row `row` as binary64, for any form.
 template <int FORM>
-__device__ __forceinline__ double state_value(const void *u_main, const float *ulo, int64_t idx) {
-    if constexpr (FORM == kKahan32)
-        return (double)((const float *)u_main)[idx] + (double)ulo[idx];
-    else
-        return ((const double *)u_main)[idx];
-}
-
-template <int FORM>
-__global__ void export_kernel(const void *__restrict__ u_main, const float *__restrict__ ulo,
+__global__ void export_kernel(const void *__restrict__ u_main, const void *__restrict__ aux,
                               int32_t N, int32_t S, int32_t Sp, double *__restrict__ out,
                               int layout) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * 3 * S) return;
     const int64_t row = t / S;
     const int32_t s = (int32_t)(t - row * S);
-    const double x = state_value<FORM>(u_main, ulo, row * Sp + s);
+    const double x = state_value_fast<FORM>(u_main, aux, row * Sp + s);
     if (layout == 0)
         out[(int64_t)s * N * 3 + row] = x;
     else
         out[t] = x;
 }
 
-// Load a binary64 [N][3][S] field into the gathered buffer (and the binary64 / low part
-// state of the forms that keep one); padding samples are zero.
+// Load a binary64 [N][3][S] field into a gathered-precision buffer (force-only
+// evaluations); padding samples are zero.
 template <int FORM>
 __global__ void import_kernel(const double *__restrict__ in, int32_t N, int32_t S, int32_t Sp,
-                              void *ug, double *u64, float *ulo) {
+                              void *ug) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * 3 * Sp) return;
     const int64_t row = t / Sp;
     const int32_t s = (int32_t)(t - row * Sp);
     const double x = s < S ? in[row * S + s] : 0.0;
-    if constexpr (FORM == kFP64) {
+    if constexpr (FORM == kFP64)
         ((double *)ug)[t] = x;
-    } else if constexpr (FORM == kFP32Force) {
+    else
         ((float *)ug)[t] = (float)x;
-        if (u64) u64[t] = x;
-    } else {
-        const float hi = (float)x;
-        ((float *)ug)[t] = hi;
-        if (ulo) ulo[t] = (float)(x - (double)hi);
-    }
 }
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -1017,43 +1021,45 @@ cudaError_t launch_advance(int64_t *step_ctr, int64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
+cudaError_t launch_stats(int form, const void *u_main, const void *aux, int32_t N, int32_t S,
                          int32_t Sp, double *mean, double *var, cudaStream_t s) {
     const int64_t threads = (int64_t)N * 3 * kStatLanes;
     if (threads == 0) return cudaSuccess;
     const unsigned grid = blocks_for(threads, 256);
     const double inv_s = 1.0 / (double)S, inv_s1 = S > 1 ? 1.0 / (double)(S - 1) : 0.0;
     if (form == kKahan32)
-        stats_kernel<kKahan32><<<grid, 256, 0, s>>>(u_main, ulo, N, S, Sp, inv_s, inv_s1, mean, var);
+        stats_kernel<kKahan32><<<grid, 256, 0, s>>>(u_main, aux, N, S, Sp, inv_s, inv_s1, mean, var);
+    else if (form == kFP32Force)
+        stats_kernel<kFP32Force><<<grid, 256, 0, s>>>(u_main, aux, N, S, Sp, inv_s, inv_s1, mean,
+                                                      var);
     else
-        stats_kernel<kFP64><<<grid, 256, 0, s>>>(u_main, ulo, N, S, Sp, inv_s, inv_s1, mean, var);
+        stats_kernel<kFP64><<<grid, 256, 0, s>>>(u_main, aux, N, S, Sp, inv_s, inv_s1, mean, var);
     return cudaGetLastError();
 }
 
-cudaError_t launch_export(int form, const void *u_main, const float *ulo, int32_t N, int32_t S,
+cudaError_t launch_export(int form, const void *u_main, const void *aux, int32_t N, int32_t S,
                           int32_t Sp, double *out, int layout, cudaStream_t s) {
     const int64_t n = (int64_t)N * 3 * S;
     if (n == 0) return cudaSuccess;
+    const unsigned grid = blocks_for(n, 256);
     if (form == kKahan32)
-        export_kernel<kKahan32><<<blocks_for(n, 256), 256, 0, s>>>(u_main, ulo, N, S, Sp, out,
-                                                                   layout);
+        export_kernel<kKahan32><<<grid, 256, 0, s>>>(u_main, aux, N, S, Sp, out, layout);
+    else if (form == kFP32Force)
+        export_kernel<kFP32Force><<<grid, 256, 0, s>>>(u_main, aux, N, S, Sp, out, layout);
     else
-        export_kernel<kFP64><<<blocks_for(n, 256), 256, 0, s>>>(u_main, ulo, N, S, Sp, out,
-                                                                layout);
+        export_kernel<kFP64><<<grid, 256, 0, s>>>(u_main, aux, N, S, Sp, out, layout);
     return cudaGetLastError();
 }
 
 cudaError_t launch_import(int form, const double *in_ncs, int32_t N, int32_t S, int32_t Sp,
-                          void *ug, double *u64, float *ulo, cudaStream_t s) {
+                          void *ug, cudaStream_t s) {
     const int64_t n = (int64_t)N * 3 * Sp;
     if (n == 0) return cudaSuccess;
     const unsigned grid = blocks_for(n, 256);
     if (form == kFP64)
-        import_kernel<kFP64><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug, u64, ulo);
-    else if (form == kFP32Force)
-        import_kernel<kFP32Force><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug, u64, ulo);
+        import_kernel<kFP64><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug);
     else
-        import_kernel<kKahan32><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug, u64, ulo);
+        import_kernel<kFP32Force><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug);
     return cudaGetLastError();
 }
 

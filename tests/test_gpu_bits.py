@@ -1,7 +1,10 @@
 """The step kernels' integer-only binary32 <-> binary64 conversions agree bit for bit with
 the hardware conversions on normal values, zeros, subnormals, Inf and overflow
 (binary64 -> binary32 rounds toward zero; magnitudes below the binary32 normal range
-become signed zero, by design); NaN stays NaN."""
+become signed zero, by design); NaN stays NaN. The FP32-force form's bit-split binary64
+state (binary32 truncation + the 29 dropped mantissa bits) rebuilds every binary64 in
+[2^-126, 2^128) exactly, holds smaller magnitudes as signed zero and reports the rest as
+out of range."""
 import os
 import subprocess
 
