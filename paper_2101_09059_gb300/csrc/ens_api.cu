@@ -210,8 +210,8 @@ StagePlan pipelined_plan(StagePlan p) {
 }
 
 // Launch-shape autotuner: time a few steps of every candidate shape on this context's
-// own data (state at rest, no traction, so every value stays exactly zero) and keep the
-// fastest. Candidate 0 is the unstaged kernel.
+// own mesh and coefficients, with the state filled with small non-zero values, and keep
+// the fastest; the state is zeroed again afterwards. Candidate 0 is the unstaged kernel.
 int autotune(ens_ctx *c, const StagePlan *cand, int n) {
     // time on non-zero data (zeros take shortcuts in some arithmetic); reset afterwards
     const int64_t ns = (int64_t)c->N * 3 * c->Sp;

@@ -60,6 +60,18 @@ __device__ __forceinline__ float f64_to_f32_rz(double d) {
     return __uint_as_float(out);
 }
 
+// binary32 -> binary64 for normal values and zeros (exact), integer operations only, in
+// fewer steps than f32_to_f64: subnormal inputs become signed zero, and Inf / NaN map to
+// finite magnitudes >= 2^128, which split_state below reports as out of range.
+__device__ __forceinline__ double f32_to_f64_ftz(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t mag = b & 0x7fffffffu;
+    const bool normal = mag >= 0x00800000u;
+    const uint32_t hw = (b & 0x80000000u) | (normal ? (mag >> 3) + (896u << 20) : 0u);
+    const uint32_t lw = normal ? (b << 29) : 0u;
+    return __longlong_as_double((long long)(((uint64_t)hw << 32) | lw));
+}
+
 // ---- bit-split binary64 state ---------------------------------------------------------
 // The FP32-force form keeps each binary64 displacement u as two 32-bit words:
 //   head = u truncated to binary32 (the value neighbours gather for the forces), and

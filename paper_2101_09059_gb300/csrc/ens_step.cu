@@ -245,25 +245,36 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             st_wb(a.ug_next + row, un);
         } else if constexpr (FORM == kFP32Force) {
             // binary64 u = (head ui, tail); the update runs in binary64, the bit splits and
-            // the conversion of the binary32 acceleration on the integer pipe
+            // the conversion of the binary32 velocity increment on the integer pipe. A held
+            // dof is the same for every sample of the node, so the branch is uniform across
+            // the node's threads.
             double vv[V], h2[2];
             uint32_t tl[V];
-            ld_cs(a.utail + row, tl);
-#pragma unroll
-            for (int q = 0; q < V; q += 2) {
-                ld_cs(a.v64 + row + q, h2);
-                vv[q] = h2[0];
-                vv[q + 1] = h2[1];
-            }
             float ug[V];
-            const float c2 = a.c2f;
+            if (held) {
 #pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float acc = (fe[d] - f[d][v]) * mi[v];
-                const double vn = held ? 0.0 : fma(a.c1, vv[v], f32_to_f64(c2 * acc));
-                const double un = held ? 0.0 : fma(a.dt, vn, join_state(ui[d][v], tl[v]));
-                vv[v] = vn;
-                bad |= !split_state(un, ug[v], tl[v]);
+                for (int v = 0; v < V; v++) {
+                    vv[v] = 0.0;
+                    tl[v] = 0u;
+                    ug[v] = 0.0f;
+                }
+            } else {
+                ld_cs(a.utail + row, tl);
+#pragma unroll
+                for (int q = 0; q < V; q += 2) {
+                    ld_cs(a.v64 + row + q, h2);
+                    vv[q] = h2[0];
+                    vv[q + 1] = h2[1];
+                }
+                const float c2 = a.c2f;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const float acc = (fe[d] - f[d][v]) * mi[v];
+                    const double vn = fma(a.c1, vv[v], f32_to_f64_ftz(c2 * acc));
+                    const double un = fma(a.dt, vn, join_state(ui[d][v], tl[v]));
+                    vv[v] = vn;
+                    bad |= !split_state(un, ug[v], tl[v]);
+                }
             }
             st_cs(a.utail + row, tl);
 #pragma unroll
@@ -271,22 +282,26 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             st_wb(a.ug_next + row, ug);
         } else {  // kKahan32
             float lo[V], vv[V], hi[V];
-            ld_cs(a.ulo + row, lo);
-            ld_cs(a.v32 + row, vv);
-            const float c1 = a.c1f, c2 = a.c2f, dt = a.dtf;
+            if (held) {  // uniform across the node's threads
 #pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float acc = (fe[d] - f[d][v]) * mi[v];
-                const float vn = held ? 0.0f : fmaf(c1, vv[v], c2 * acc);
-                // (hi, lo) += dt * vn as an error-free sum of hi and the small part.
-                const float y = fmaf(dt, vn, lo[v]);
-                const float s = ui[d][v] + y;
-                const float bb = s - ui[d][v];
-                const float err = (ui[d][v] - (s - bb)) + (y - bb);
-                hi[v] = held ? 0.0f : s;
-                lo[v] = held ? 0.0f : err;
-                vv[v] = vn;
-                bad |= !isfinite(s);
+                for (int v = 0; v < V; v++) lo[v] = vv[v] = hi[v] = 0.0f;
+            } else {
+                ld_cs(a.ulo + row, lo);
+                ld_cs(a.v32 + row, vv);
+                const float c1 = a.c1f, c2 = a.c2f, dt = a.dtf;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const float acc = (fe[d] - f[d][v]) * mi[v];
+                    const float vn = fmaf(c1, vv[v], c2 * acc);
+                    // (hi, lo) += dt * vn as an error-free sum of hi and the small part.
+                    const float y = fmaf(dt, vn, lo[v]);
+                    const float s = ui[d][v] + y;
+                    const float bb = s - ui[d][v];
+                    hi[v] = s;
+                    lo[v] = (ui[d][v] - (s - bb)) + (y - bb);
+                    vv[v] = vn;
+                    bad |= !isfinite(s);
+                }
             }
             st_cs(a.ulo + row, lo);
             st_cs(a.v32 + row, vv);

@@ -9,10 +9,12 @@
 #include "../paper_2101_09059_gb300/csrc/ens_bits.cuh"
 
 __global__ void conv(const float *xf, const double *xd, int n, double *o64, double *r64,
-                     float *o32, float *r32, float *head, double *joined, int *in_range) {
+                     float *o32, float *r32, float *head, double *joined, int *in_range,
+                     double *ftz) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     o64[i] = ens::f32_to_f64(xf[i]);
+    ftz[i] = ens::f32_to_f64_ftz(xf[i]);
     r64[i] = (double)xf[i];
     o32[i] = ens::f64_to_f32_rz(xd[i]);
     r32[i] = __double2float_rz(xd[i]);
@@ -47,15 +49,18 @@ int main() {
     float *dxf, *do32, *dr32, *dhead;
     double *dxd, *do64, *dr64, *djoin;
     int *drange;
+    double *dftz;
+    cudaMalloc(&dftz, 8 * n);
     cudaMalloc(&dxf, 4 * n); cudaMalloc(&do32, 4 * n); cudaMalloc(&dr32, 4 * n);
     cudaMalloc(&dxd, 8 * n); cudaMalloc(&do64, 8 * n); cudaMalloc(&dr64, 8 * n);
     cudaMalloc(&dhead, 4 * n); cudaMalloc(&djoin, 8 * n); cudaMalloc(&drange, 4 * n);
     cudaMemcpy(dxf, xf.data(), 4 * n, cudaMemcpyHostToDevice);
     cudaMemcpy(dxd, xd.data(), 8 * n, cudaMemcpyHostToDevice);
-    conv<<<(n + 255) / 256, 256>>>(dxf, dxd, n, do64, dr64, do32, dr32, dhead, djoin, drange);
+    conv<<<(n + 255) / 256, 256>>>(dxf, dxd, n, do64, dr64, do32, dr32, dhead, djoin, drange, dftz);
     std::vector<double> o64(n), r64(n), joined(n);
     std::vector<float> o32(n), r32(n), head(n);
     std::vector<int> in_range(n);
+    std::vector<double> ftz(n);
     cudaMemcpy(o64.data(), do64, 8 * n, cudaMemcpyDeviceToHost);
     cudaMemcpy(r64.data(), dr64, 8 * n, cudaMemcpyDeviceToHost);
     cudaMemcpy(o32.data(), do32, 4 * n, cudaMemcpyDeviceToHost);
@@ -63,6 +68,7 @@ int main() {
     cudaMemcpy(head.data(), dhead, 4 * n, cudaMemcpyDeviceToHost);
     cudaMemcpy(joined.data(), djoin, 8 * n, cudaMemcpyDeviceToHost);
     cudaMemcpy(in_range.data(), drange, 4 * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(ftz.data(), dftz, 8 * n, cudaMemcpyDeviceToHost);
     if (cudaGetLastError() != cudaSuccess) { printf("cuda error\n"); return 2; }
     long bad64 = 0, bad32 = 0, flushed = 0;
     for (int i = 0; i < n; i++) {
@@ -101,6 +107,24 @@ int main() {
             split_exact++;
         }
     }
+    // flush-to-zero form: exact for normal values and zeros, signed zero for subnormals,
+    // a finite magnitude >= 2^128 for Inf and NaN
+    long bad_ftz = 0;
+    for (int i = 0; i < n; i++) {
+        uint32_t b; memcpy(&b, &xf[i], 4);
+        const uint32_t e = (b >> 23) & 0xffu;
+        uint64_t fb, rb; memcpy(&fb, &ftz[i], 8); memcpy(&rb, &r64[i], 8);
+        if (e == 0xffu) {
+            const double a = ftz[i] < 0 ? -ftz[i] : ftz[i];
+            if (!(a >= 3.4028236692093846e38 && a < 1e300)) bad_ftz++;
+        } else if (e == 0u) {
+            if (fb != (uint64_t)(b >> 31) << 63) bad_ftz++;
+        } else if (fb != rb) {
+            bad_ftz++;
+        }
+    }
+    printf("f32->f64 (flush-to-zero form) mismatches %ld\n", bad_ftz);
+    bad64 += bad_ftz;
     printf("f32->f64 mismatches %ld, f64->f32 mismatches %ld (of %d; %ld below the normal range)\n",
            bad64, bad32, n, flushed);
     printf("split/join mismatches %ld (%ld values rebuilt exactly)\n", bad_split, split_exact);
