@@ -157,6 +157,28 @@ __device__ __forceinline__ void ld_state(const R *p, R (&x)[V]) {
         ld_nc(p, x);
 }
 
+// Per-thread bases of the gathered arrays: the thread's own column within node 0 of u and
+// within (E h) row 0, so that a neighbour costs one 32 x 32 -> 64-bit multiply-add on its
+// node (element) index, and its other two dof rows one row stride each.
+template <typename R>
+struct GatherBase {
+    const char *u;   // ug + s0
+    const char *eh;  // (E h) + s0
+    int32_t node_b;  // 3 Sp sizeof(R)
+    int32_t row_b;   // Sp sizeof(R)
+    __device__ __forceinline__ GatherBase(const R *ug, const R *eh_, int32_t Sp, int32_t s0)
+        : u(reinterpret_cast<const char *>(ug + s0)),
+          eh(reinterpret_cast<const char *>(eh_ + s0)),
+          node_b(3 * Sp * (int32_t)sizeof(R)),
+          row_b(Sp * (int32_t)sizeof(R)) {}
+    __device__ __forceinline__ const R *row(int32_t k, int d) const {
+        return reinterpret_cast<const R *>(u + (int64_t)k * node_b + d * row_b);
+    }
+    __device__ __forceinline__ const R *ehrow(int32_t e) const {
+        return reinterpret_cast<const R *>(eh + (int64_t)e * row_b);
+    }
+};
+
 template <typename R, int V, bool COH = false>
 __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__restrict__ ug,
                                            int32_t i, int32_t s0, const R (&ui)[3][V],
@@ -166,6 +188,7 @@ __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__res
     for (int d = 0; d < 3; d++)
 #pragma unroll
         for (int v = 0; v < V; v++) f[d][v] = R(0);
+    const GatherBase<R> g(ug, w.eh, (int32_t)Sp, s0);
     const int32_t p0 = __ldg(w.rowptr + i);
     const int32_t p1 = __ldg(w.rowptr + i + 1);
     for (int32_t p = p0; p < p1; ++p) {
@@ -173,10 +196,10 @@ __device__ __forceinline__ void node_force(const ForceView<R> &w, const R *__res
         R ua[3][V], ub[3][V], e[V], k[18];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            ld_state<COH, R, V>(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
-            ld_state<COH, R, V>(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
+            ld_state<COH, R, V>(g.row(en.y, d), ua[d]);
+            ld_state<COH, R, V>(g.row(en.z, d), ub[d]);
         }
-        ld_nc(w.eh + (int64_t)en.x * Sp + s0, e);
+        ld_nc(g.ehrow(en.x), e);
         ld_kc(w.kc + (int64_t)p * Kc<R>::stride, k);
 #pragma unroll
         for (int v = 0; v < V; v++) {
@@ -373,15 +396,14 @@ __device__ __forceinline__ void apply_incidence(const R (&ua)[3][V], const R (&u
 }
 
 template <typename R, int V>
-__device__ __forceinline__ void load_incidence(const R *__restrict__ ug, const R *__restrict__ eh,
-                                               const int4 en, int64_t Sp, int32_t s0, R (&ua)[3][V],
-                                               R (&ub)[3][V], R (&e)[V]) {
+__device__ __forceinline__ void load_incidence(const GatherBase<R> &g, const int4 en,
+                                               R (&ua)[3][V], R (&ub)[3][V], R (&e)[V]) {
 #pragma unroll
     for (int d = 0; d < 3; d++) {
-        ld_nc(ug + ((int64_t)en.y * 3 + d) * Sp + s0, ua[d]);
-        ld_nc(ug + ((int64_t)en.z * 3 + d) * Sp + s0, ub[d]);
+        ld_nc(g.row(en.y, d), ua[d]);
+        ld_nc(g.row(en.z, d), ub[d]);
     }
-    ld_nc(eh + (int64_t)en.x * Sp + s0, e);
+    ld_nc(g.ehrow(en.x), e);
 }
 
 template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V,
@@ -467,11 +489,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     for (int d = 0; d < 3; d++)
 #pragma unroll
         for (int v = 0; v < V; v++) f[d][v] = R(0);
-    const R *__restrict__ ug = a.ug_cur;
+    const GatherBase<R> g(a.ug_cur, a.fv.eh, (int32_t)Sp, s0);
     for (int32_t p = p0; p < p1; ++p) {
         const int4 en = ent_s[p];
         R ua[3][V], ub[3][V], ev[V];
-        load_incidence<R, V>(ug, a.fv.eh, en, Sp, s0, ua, ub, ev);
+        load_incidence<R, V>(g, en, ua, ub, ev);
         apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
     }
     if constexpr (FORCE_ONLY) {
@@ -580,10 +602,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_pipelined_kernel(const StepA
             for (int d = 0; d < 3; d++)
 #pragma unroll
                 for (int v = 0; v < V; v++) f[d][v] = R(0);
+            const GatherBase<R> g(a.ug_cur, a.fv.eh, Sp, s0);
             for (int32_t p = p0; p < p1; ++p) {
                 const int4 en = ent_s[p];
                 R ua[3][V], ub[3][V], ev[V];
-                load_incidence<R, V>(a.ug_cur, a.fv.eh, en, Sp, s0, ua, ub, ev);
+                load_incidence<R, V>(g, en, ua, ub, ev);
                 apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
             }
             R fe[3];
