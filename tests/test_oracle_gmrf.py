@@ -1,0 +1,108 @@
+"""Pins of the Matérn field-sampler oracle (Section 2.1), fixed by geometry, the P1
+finite-element identities, the paper's Q_2 formula and the Matérn covariance."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+from scipy.special import gamma
+
+import oracle.gmrf as og
+import synth
+from synth.fields import surface_mass_stiffness
+from synth.fields import matern_correlation
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+
+def test_lumped_mass_is_the_polygonal_surface_area():
+    m = synth.tube_mesh(nc=24, na=7, radius=0.01, length=0.05)
+    area = 24 * 2.0 * 0.01 * np.sin(np.pi / 24) * 0.05   # planar rectangles between rings
+    Cl = og.lumped_mass(m.xyz, m.tri)
+    assert Cl.sum() == pytest.approx(area, rel=1e-13)
+    assert np.all(Cl > 0)
+
+
+def test_stiffness_annihilates_constants_and_is_symmetric_psd():
+    m = synth.aneurysm_mesh(nc=20, na=15)
+    G = og.stiffness(m.xyz, m.tri).toarray()
+    assert np.abs(G @ np.ones(m.n_nodes)).max() < 1e-12 * np.abs(G).max()
+    assert np.allclose(G, G.T, atol=1e-14 * np.abs(G).max())
+    w = np.linalg.eigvalsh(G)
+    assert w.min() > -1e-10 * w.max()
+    assert np.sum(np.abs(w) < 1e-10 * w.max()) == 1   # connected surface: one zero mode
+
+
+def test_plate_energy_of_linear_fields_is_exact():
+    """P1 reproduces linear functions: f^T G f = area |grad f|^2, 1^T C 1 = area."""
+    m = synth.plate_mesh(nx=9, ny=7, lx=0.04, ly=0.03, jitter=0.3, seed=3)
+    area = 0.04 * 0.03
+    G = og.stiffness(m.xyz, m.tri)
+    C = og.consistent_mass(m.xyz, m.tri)
+    a = np.array([0.7, -1.3])
+    f = m.xyz[:, :2] @ a
+    assert f @ (G @ f) == pytest.approx(area * (a @ a), rel=1e-12)
+    one = np.ones(m.n_nodes)
+    assert one @ (C @ one) == pytest.approx(area, rel=1e-13)
+    # interior rows of G f vanish for linear f (patch test)
+    nx, ny = 9, 7
+    inner = [j * nx + i for j in range(1, ny - 1) for i in range(1, nx - 1)]
+    assert np.abs((G @ f)[inner]).max() < 1e-12 * np.abs(G @ f).max()
+
+
+def test_cotangent_stiffness_matches_the_gradient_definition():
+    """Two independent formulas for G_ij = <grad psi_i, grad psi_j> on a curved surface."""
+    m = synth.aneurysm_mesh(nc=16, na=12)
+    G1 = og.stiffness(m.xyz, m.tri).toarray()
+    Cl2, G2 = surface_mass_stiffness(m.xyz, m.tri)
+    assert np.abs(G1 - G2.toarray()).max() < 1e-12 * np.abs(G1).max()
+    assert np.abs(og.lumped_mass(m.xyz, m.tri) - Cl2).max() < 1e-15
+
+
+def test_two_stage_draw_has_the_papers_precision():
+    """Cov(K^-1 C~^(1/2) z) = K^-1 C~ K^-1 is the inverse of Q_2 = K^T C~^-1 K."""
+    m = synth.tube_mesh(nc=10, na=8, radius=0.01, length=0.04)
+    kappa = og.kappa_of(0.02)
+    K, Cl = og.operator(m.xyz, m.tri, kappa)
+    Kd = K.toarray()
+    Ki = np.linalg.inv(Kd)
+    cov = Ki @ np.diag(Cl) @ Ki
+    Q = og.precision(m.xyz, m.tri, kappa).toarray()
+    assert np.abs(Q @ cov - np.eye(m.n_nodes)).max() < 1e-9
+
+
+def test_marginal_scale_is_the_papers_variance_formula():
+    nu, d, kappa = 1.0, 2, og.kappa_of(0.02)
+    var = gamma(nu) / (gamma(nu + d / 2) * (4 * np.pi) ** (d / 2) * kappa ** (2 * nu))
+    assert og.marginal_scale(kappa, 0.1) == pytest.approx(0.1 / np.sqrt(var), rel=1e-14)
+    assert og.kappa_of(0.02) * 0.02 == pytest.approx(np.sqrt(8.0))
+
+
+def test_discrete_covariance_follows_matern():
+    """Exact covariance column of the centre node of a fine plate (far from the edges)
+    against sigma^2 M(d): the scale, kappa and the discretisation together."""
+    n, L, rho, sigma = 121, 0.24, 0.02, 0.1
+    m = synth.plate_mesh(nx=n, ny=n, lx=L, ly=L)
+    kappa = og.kappa_of(rho)
+    K, Cl = og.operator(m.xyz, m.tri, kappa)
+    lu = spla.splu(K.tocsc())
+    c = (n // 2) * n + n // 2
+    e = np.zeros(m.n_nodes)
+    e[c] = 1.0
+    col = lu.solve(Cl * lu.solve(e)) * og.marginal_scale(kappa, sigma) ** 2
+    d = np.linalg.norm(m.xyz - m.xyz[c], axis=1)
+    ref = sigma ** 2 * matern_correlation(d, rho)
+    # P1 variance at h = rho / 10 is a few per cent high; away from the node the
+    # covariance matches to well under 1 % of sigma^2
+    assert col[c] == pytest.approx(sigma ** 2, rel=0.05)
+    ring = (d >= 0.2 * rho) & (d <= 1.5 * rho)
+    assert np.abs(col[ring] - ref[ring]).max() < 0.01 * sigma ** 2
+
+
+def test_sample_solves_the_spde_system():
+    m = synth.aneurysm_mesh(nc=24, na=20)
+    kappa = og.kappa_of(0.02)
+    rng = np.random.Generator(np.random.Philox(key=11))
+    z = rng.standard_normal((m.n_nodes, 5))
+    x = og.sample(m.xyz, m.tri, kappa, z)
+    K, Cl = og.operator(m.xyz, m.tri, kappa)
+    r = K @ x - np.sqrt(Cl)[:, None] * z
+    assert np.abs(r).max() < 1e-12 * np.abs(np.sqrt(Cl)[:, None] * z).max()
