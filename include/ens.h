@@ -75,6 +75,10 @@ typedef enum { ENS_FP64 = 0, ENS_FP32_FORCE = 1, ENS_KAHAN32 = 2 } ens_precision
 /* Use launch shape k of ens_info_t.kernel_variant (when it applies to the context's
  * sizes; otherwise the unstaged kernel) instead of timing candidates.                 */
 #define ENS_FLAG_FORCE_VARIANT(k) (((k) + 1) << 8)
+/* E_node and h_node of ens_create are device pointers (binary64 [n_nodes][S] on the
+ * context's device, e.g. written by gmrf_sample) instead of host pointers; they are
+ * checked on the device (every value finite and > 0) and copied.                     */
+#define ENS_FLAG_DEVICE_FIELDS 16
 
 /* ---- displacement layouts for the getters ---------------------------------------- */
 #define ENS_LAYOUT_SNC 0 /* out[s][node][dof]  */
@@ -156,7 +160,8 @@ typedef struct {
  * lumped masses (Section 2.3), and sets the state to rest (u_0 = v_0 = 0).
  * S       : ensemble width, >= 1.
  * E_node, h_node : host [n_nodes][S] nodal modulus and thickness of every
- *           realisation (sample index innermost), all > 0.
+ *           realisation (sample index innermost), all > 0 (device arrays with
+ *           ENS_FLAG_DEVICE_FIELDS).
  * stream  : cudaStream_t to run on (NULL = legacy default stream).
  * alloc   : device allocator or NULL.
  * out     : receives the context; on failure *out is NULL and the code is returned

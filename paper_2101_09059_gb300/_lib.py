@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libens.so")
-HEADERS = [os.path.join(ROOT, "include", "ens.h"), os.path.join(ROOT, "include", "sur.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ens.h", "sur.h", "gmrf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
@@ -74,7 +74,7 @@ def declared_functions():
     for h in HEADERS:
         txt = open(h).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-        for m in re.finditer(r"\b((?:ens|sur)_[a-z0-9_]+)\s*\(", txt):
+        for m in re.finditer(r"\b((?:ens|sur|gmrf)_[a-z0-9_]+)\s*\(", txt):
             names.append(m.group(1))
     return sorted(set(names))
 
@@ -114,6 +114,12 @@ class ens_batch_info_t(ctypes.Structure):
                 ("graph_steps", ctypes.c_int32), ("n_tiles", ctypes.c_int32),
                 ("persistent_grid", ctypes.c_int32), ("mode_us", ctypes.c_float * 5),
                 ("bytes_per_step", ctypes.c_double)]
+
+
+class gmrf_info_t(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("nnz", ctypes.c_int64), ("iterations", ctypes.c_int32),
+                ("max_relres", ctypes.c_double), ("bytes_per_iter", ctypes.c_double),
+                ("last_S", ctypes.c_int32)]
 
 
 _lib = None
@@ -174,6 +180,12 @@ def load(build_if_missing: bool = True):
         "sur_field_stats": ([dp, i32, i32, dp, dp, i64, dp, dp, dp, vp], ctypes.c_int),
         "sur_last_error": ([vp], ctypes.c_char_p),
         "sur_destroy": ([vp], None),
+        "gmrf_create": ([i32, i32, dp, dp, ctypes.c_double, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "gmrf_sample": ([vp, i32, dp, dp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, i32],
+                        ctypes.c_int),
+        "gmrf_info": ([vp, ctypes.POINTER(gmrf_info_t)], ctypes.c_int),
+        "gmrf_last_error": ([vp], ctypes.c_char_p),
+        "gmrf_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

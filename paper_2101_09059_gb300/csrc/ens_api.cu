@@ -333,12 +333,14 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         !(p->alpha >= 0.0) || !(p->dt > 0.0) || !std::isfinite(p->rho) ||
         !std::isfinite(p->kshear) || !std::isfinite(p->alpha) || !std::isfinite(p->dt) ||
         p->precision < 0 || p->precision > 2 ||
-        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | ENS_FLAG_NO_GRAPH | 0xf00)) != 0 ||
+        (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | ENS_FLAG_NO_GRAPH |
+                      ENS_FLAG_DEVICE_FIELDS | 0xf00)) != 0 ||
         ((p->flags >> 8) & 0xf) > kVariants)
         return ENS_ERR_INVALID_ARG;
     if (alloc && (!alloc->alloc || !alloc->release)) return ENS_ERR_INVALID_ARG;
     if (!finite_all(mesh->xyz, 3 * (size_t)N)) return ENS_ERR_INVALID_ARG;
-    if (!finite_pos(E_node, (size_t)N * S) || !finite_pos(h_node, (size_t)N * S))
+    const bool dev_fields = (p->flags & ENS_FLAG_DEVICE_FIELDS) != 0;
+    if (!dev_fields && (!finite_pos(E_node, (size_t)N * S) || !finite_pos(h_node, (size_t)N * S)))
         return ENS_ERR_INVALID_ARG;
 
     ens_ctx *c = new (std::nothrow) ens_ctx();
@@ -419,13 +421,17 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         CK(cudaMemsetAsync(c->step_ctr, 0, sizeof(int64_t), c->stream));
 
         // padded nodal fields: padding samples repeat sample 0 (finite, never reported)
-        std::vector<double> Ep((size_t)NSp), hp((size_t)NSp);
-        for (int64_t i = 0; i < N; i++)
-            for (int32_t s = 0; s < c->Sp; s++) {
-                int32_t src = s < S ? s : 0;
-                Ep[i * c->Sp + s] = E_node[i * S + src];
-                hp[i * c->Sp + s] = h_node[i * S + src];
-            }
+        std::vector<double> Ep, hp;
+        if (!dev_fields) {
+            Ep.resize((size_t)NSp);
+            hp.resize((size_t)NSp);
+            for (int64_t i = 0; i < N; i++)
+                for (int32_t s = 0; s < c->Sp; s++) {
+                    int32_t src = s < S ? s : 0;
+                    Ep[i * c->Sp + s] = E_node[i * S + src];
+                    hp[i * c->Sp + s] = h_node[i * S + src];
+                }
+        }
         double *En_d, *hn_d, *kc64, *area, *laml, *lamh, *xsq, *eh64, *m64, *w2lo, *w2hi;
         int *bad;
         ALLOC(En_d, double, NSp);
@@ -440,8 +446,18 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         ALLOC(w2lo, double, E);
         ALLOC(w2hi, double, E);
         ALLOC(bad, int, 1);
-        CK(cudaMemcpyAsync(En_d, Ep.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(hn_d, hp.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
+        if (dev_fields) {
+            CK(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+            CK(launch_pad_fields(E_node, N, S, c->Sp, En_d, bad, c->stream));
+            CK(launch_pad_fields(h_node, N, S, c->Sp, hn_d, bad, c->stream));
+            int nbad = 0;
+            CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (nbad) return fail(c, ENS_ERR_INVALID_ARG, "%d device field values not finite and > 0", nbad);
+        } else {
+            CK(cudaMemcpyAsync(En_d, Ep.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(hn_d, hp.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
+        }
         const int big = 0x7fffffff;
         CK(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, c->stream));
 

@@ -159,6 +159,8 @@ cudaError_t launch_setup_stability(const int32_t *tri, const double *eh64, const
                                    double rho, double *w2lo, double *w2hi, cudaStream_t s);
 cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
                            cudaStream_t s);
+cudaError_t launch_pad_fields(const double *src, int32_t N, int32_t S, int32_t Sp, double *dst,
+                              int *bad, cudaStream_t s);
 cudaError_t launch_convert(const double *in, int64_t n, void *out, int to_float, int invert,
                            cudaStream_t s);
 

@@ -270,6 +270,19 @@ __global__ void convert_kernel(const double *__restrict__ in, int64_t n, void *o
         ((double *)out)[t] = x;
 }
 
+// dst [N][Sp] = src [N][S], padding samples repeating sample 0; counts entries of src
+// that are not finite and > 0 into *bad.
+__global__ void pad_fields_kernel(const double *__restrict__ src, int32_t N, int32_t S, int32_t Sp,
+                                  double *__restrict__ dst, int *bad) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * Sp) return;
+    const int64_t i = t / Sp;
+    const int32_t s = (int32_t)(t - i * Sp);
+    const double x = src[i * S + (s < S ? s : 0)];
+    if (s < S && !(isfinite(x) && x > 0.0)) atomicAdd(bad, 1);
+    dst[t] = x;
+}
+
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -319,6 +332,14 @@ cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to
                            cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     pack_kc_kernel<<<blocks_for(nnz * 20, 256), 256, 0, s>>>(kc64, nnz, kc_out, to_float);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_fields(const double *src, int32_t N, int32_t S, int32_t Sp, double *dst,
+                              int *bad, cudaStream_t s) {
+    const int64_t n = (int64_t)N * Sp;
+    if (n == 0) return cudaSuccess;
+    pad_fields_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, N, S, Sp, dst, bad);
     return cudaGetLastError();
 }
 

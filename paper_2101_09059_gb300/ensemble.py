@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
-FLAG_NO_AUTOTUNE, FLAG_UNSTAGED, FLAG_NO_GRAPH = 1, 2, 4
+FLAG_NO_AUTOTUNE, FLAG_UNSTAGED, FLAG_NO_GRAPH, FLAG_DEVICE_FIELDS = 1, 2, 4, 16
 
 
 def FLAG_FORCE_VARIANT(k: int) -> int:
@@ -76,7 +76,8 @@ def _check(L, ctx, rc):
 class Ensemble:
     """S realisations of the wall model advanced together on one GPU.
 
-    xyz [N][3], tri [E][3], fixed [N][3] (uint8), E_node / h_node [N][S] (float64),
+    xyz [N][3], tri [E][3], fixed [N][3] (uint8), E_node / h_node [N][S] (float64 host
+    arrays, or float64 CUDA tensors on the context's device, e.g. from FieldSampler),
     material constants and dt as in ens_params; precision: "fp64", "fp32_force",
     "kahan32" or the ENS_* value. stream: a torch.cuda.Stream (default: current).
     """
@@ -89,8 +90,17 @@ class Ensemble:
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self.tri = np.ascontiguousarray(tri, dtype=np.int32)
         self.fixed = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
-        E_node = np.ascontiguousarray(E_node, dtype=np.float64)
-        h_node = np.ascontiguousarray(h_node, dtype=np.float64)
+        on_device = isinstance(E_node, torch.Tensor) and E_node.is_cuda
+        if on_device:
+            for t in (E_node, h_node):
+                assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                assert t.is_contiguous() and t.device.index == device and t.shape == E_node.shape
+            flags |= FLAG_DEVICE_FIELDS
+            fields = (ctypes.c_void_p(E_node.data_ptr()), ctypes.c_void_p(h_node.data_ptr()))
+        else:
+            E_node = np.ascontiguousarray(E_node, dtype=np.float64)
+            h_node = np.ascontiguousarray(h_node, dtype=np.float64)
+            fields = (_ptr(E_node), _ptr(h_node))
         self.N, self.E = self.xyz.shape[0], self.tri.shape[0]
         self.S = int(E_node.shape[1])
         self.precision = PRECISIONS.get(precision, precision)
@@ -104,7 +114,9 @@ class Ensemble:
         out = ctypes.c_void_p()
         alloc_p = ctypes.byref(self._allocator.struct) if self._allocator else None
         with torch.cuda.device(device):
-            rc = self._L.ens_create(ctypes.byref(mesh), self.S, _ptr(E_node), _ptr(h_node),
+            if on_device:
+                torch.cuda.current_stream(device).synchronize()  # the fields are written
+            rc = self._L.ens_create(ctypes.byref(mesh), self.S, fields[0], fields[1],
                                     ctypes.byref(params), ctypes.c_void_p(self.stream.cuda_stream),
                                     alloc_p, ctypes.byref(out))
         if rc != 0:
