@@ -301,6 +301,65 @@ void ens_batch_destroy(ens_batch *b);
 int ens_merge_stats(int32_t n_parts, const int64_t *counts, const double *const *means,
                     const double *const *vars, int64_t n, double *mean_out, double *var_out);
 
+/* ---- output statistics (Section 3: mean displacement magnitude with 5 %-95 % bands,
+ * displacement and stress time histories at chosen locations, stress in the local
+ * cylindrical frame) ----------------------------------------------------------------
+ * A quantity is a set of rows, each with one binary64 value per realisation, formed on
+ * the device from the current state of any precision form:
+ *   ENS_QTY_DISPLACEMENT    rows (node, dof)        n_nodes * 3 rows
+ *   ENS_QTY_DISP_MAGNITUDE  rows node, |u|          n_nodes rows
+ *   ENS_QTY_STRESS          rows (element, k)       n_elems * 6 rows, k = rr, tt, zz, rt, rz, tz
+ * Stress follows Section 2.2.1 and the frame of Section 2.2.3: sigma_l = C(E) B u_l in the
+ * element frame with E the element mean of the nodal modulus (the average of the linear
+ * field over the three Gauss points), the plane-stress tensor (sigma_nn = 0) expressed in
+ * r = the element's outward normal, t = (r x a) / |r x a|, z = a projected on the wall and
+ * normalised, where a is the tangent of the centreline segment closest to the element
+ * centroid.                                                                           */
+#define ENS_QTY_DISPLACEMENT 0
+#define ENS_QTY_DISP_MAGNITUDE 1
+#define ENS_QTY_STRESS 2
+
+/* Centreline polyline for the stress frame: pts host [n_pts][3], n_pts >= 2. Builds the
+ * per-element stress operators on the device (6 x 9 binary64 values per element).
+ * ENS_ERR_INVALID_ARG if an element's normal is parallel to its centreline tangent.    */
+int ens_set_centerline(ens_ctx *ctx, int32_t n_pts, const double *pts);
+
+/* Rows of a quantity at the current step: out device [rows][S] binary64 (sample index
+ * innermost). Runs on the context stream (asynchronous). ENS_ERR_STATE for stress
+ * without a centreline.                                                               */
+int ens_quantity_device(ens_ctx *ctx, int32_t qty, double *out);
+
+/* Per-row statistics of a quantity at the current step: mean [rows], sample variance
+ * [rows] (divisor S - 1; 0 when S = 1) and quantiles quant [rows][n_q] of type 7:
+ * with the row's samples sorted ascending x_0 <= ... <= x_{S-1}, h = q_k (S - 1),
+ * j = floor(h), quant = x_j + (h - j) (x_{j+1} - x_j) (x_j itself when j = S - 1),
+ * evaluated without fused multiply-adds. Host outputs; any of mean, var may be NULL;
+ * quant may be NULL only when n_q = 0. q host [n_q], each in [0, 1]; n_q <= 1024;
+ * S <= 16384. Synchronises the context stream.                                         */
+int ens_quantity_stats(ens_ctx *ctx, int32_t qty, int32_t n_q, const double *q, double *mean,
+                       double *var, double *quant);
+
+/* The same statistics for caller rows: rows device [n_rows][S] binary64, outputs device
+ * (mean [n_rows], var [n_rows], quant [n_rows][n_q]; mean and var may be NULL), q host.
+ * No context; runs on stream and synchronises it. 1 <= S <= 16384.                     */
+int ens_row_stats_device(int64_t n_rows, int32_t S, const double *rows, int32_t n_q,
+                         const double *q, double *mean, double *var, double *quant,
+                         void *stream);
+
+/* Probe time histories: after every ens_step segment that ends on a step index that is
+ * a multiple of stride, record the displacement of n_nodes probe nodes (all dofs, all
+ * samples) and the stress of n_elems probe elements (needs a centreline), up to
+ * capacity records (further records are dropped). stride = 0 switches probes off and
+ * drops the history; ens_reset empties it. ids host arrays, copied.                    */
+int ens_set_probes(ens_ctx *ctx, int32_t n_nodes, const int32_t *nodes, int32_t n_elems,
+                   const int32_t *elems, int32_t stride, int64_t capacity);
+
+/* Copy the history: u_out host [n_rec][n_nodes][3][S], sigma_out host
+ * [n_rec][n_elems][6][S] (either may be NULL), steps_out host [n_rec] (the step index of
+ * each record, may be NULL); *n_rec receives the number of records.                    */
+int ens_get_probes(ens_ctx *ctx, double *u_out, double *sigma_out, int64_t *steps_out,
+                   int64_t *n_rec);
+
 /* Sizes, step index and traffic model.                                               */
 int ens_info(const ens_ctx *ctx, ens_info_t *info);
 

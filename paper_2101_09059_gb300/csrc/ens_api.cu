@@ -450,7 +450,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
             CK(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
             CK(launch_pad_fields(E_node, N, S, c->Sp, En_d, bad, c->stream));
             CK(launch_pad_fields(h_node, N, S, c->Sp, hn_d, bad, c->stream));
-            int nbad = 0;
+            int nbad = 0;  // (checked before anything else reads the fields)
             CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             if (nbad) return fail(c, ENS_ERR_INVALID_ARG, "%d device field values not finite and > 0", nbad);
@@ -513,6 +513,9 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         } else {
             c->eh = eh64;
         }
+        // element-mean modulus for the stress output
+        ALLOC(c->ebar, double, (int64_t)E * c->Sp);
+        CK(launch_element_mean(c->tri_d, En_d, E, c->Sp, c->ebar, c->stream));
         int hbad = 0;
         std::vector<double> h_lo(E), h_hi(E);
         CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -600,6 +603,8 @@ int ens_reset(ens_ctx *c) {
     c->cur = 0;
     c->step = 0;
     c->started = false;
+    c->probe_rec = 0;
+    c->probe_steps.clear();
     return ENS_OK;
 }
 
@@ -712,17 +717,9 @@ int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
 }
 }  // namespace
 
-int ens_step(ens_ctx *c, int64_t n) {
-    if (!c) return ENS_ERR_INVALID_ARG;
-    if (n < 0) return fail(c, ENS_ERR_INVALID_ARG, "n = %lld", (long long)n);
-    if (c->J == 0) return fail(c, ENS_ERR_STATE, "no traction table (call ens_set_traction)");
-    if (c->step + n > c->n_amp)
-        return fail(c, ENS_ERR_RANGE, "step %lld + %lld > %lld table rows", (long long)c->step,
-                    (long long)n, (long long)c->n_amp);
-    if (n == 0) return ENS_OK;
-    if (n > INT32_MAX) return fail(c, ENS_ERR_INVALID_ARG, "n too large for one call");
-    const int64_t step0 = c->step;
-    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+namespace {
+// Launch n >= 1 steps from the current state (the start step first if not started).
+int advance(ens_ctx *c, int64_t n) {
     int64_t left = n;
     if (!c->started) {  // the start step never goes into a graph
         int rc = run_steps(c, 1);
@@ -740,9 +737,34 @@ int ens_step(ens_ctx *c, int64_t n) {
         if (rc != ENS_OK) return rc;
         CK(launch_advance(c->step_ctr, left, c->stream));
     }
+    return ENS_OK;
+}
+}  // namespace
+
+int ens_step(ens_ctx *c, int64_t n) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (n < 0) return fail(c, ENS_ERR_INVALID_ARG, "n = %lld", (long long)n);
+    if (c->J == 0) return fail(c, ENS_ERR_STATE, "no traction table (call ens_set_traction)");
+    if (c->step + n > c->n_amp)
+        return fail(c, ENS_ERR_RANGE, "step %lld + %lld > %lld table rows", (long long)c->step,
+                    (long long)n, (long long)c->n_amp);
+    if (n == 0) return ENS_OK;
+    if (n > INT32_MAX) return fail(c, ENS_ERR_INVALID_ARG, "n too large for one call");
+    CK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
+    // with probes, advance in segments that end on the recording steps
+    int64_t left = n;
+    while (left > 0) {
+        int64_t seg = left;
+        if (c->probe_stride > 0) seg = std::min(left, c->probe_stride - c->step % c->probe_stride);
+        int rc = advance(c, seg);
+        if (rc != ENS_OK) return rc;
+        c->step += seg;
+        left -= seg;
+        rc = probe_record(c);
+        if (rc != ENS_OK) return rc;
+    }
     CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->step = step0 + n;
     if (c->h_flags[0] & 4)
         return fail(c, ENS_ERR_CUDA, "a staged block found its launch plan inconsistent");
     if (c->h_flags[0] & 2)

@@ -53,6 +53,18 @@ struct ens_ctx {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::vector<uintptr_t> graph_key;
+    // output statistics: element-mean modulus [E][Sp], stress operators [E][6][9] (after
+    // ens_set_centerline), the quantity buffer, and the probe histories
+    double *ebar = nullptr;
+    double *stress_w = nullptr;
+    bool has_centerline = false;
+    double *qty_buf = nullptr;
+    size_t qty_cap = 0;
+    int32_t *probe_nodes = nullptr, *probe_elems = nullptr;
+    double *probe_hu = nullptr, *probe_hs = nullptr;
+    int32_t probe_stride = 0, probe_nn = 0, probe_ne = 0;
+    int64_t probe_rec = 0, probe_cap = 0;
+    std::vector<int64_t> probe_steps;
 };
 
 
@@ -64,6 +76,8 @@ void *ctx_alloc(ens_ctx *c, size_t bytes);
 void ctx_free(ens_ctx *c, void *p);
 // Launch step k of a chunk starting at the context's current buffer (context unchanged).
 cudaError_t ctx_launch_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s);
+// Record the probes if the current step is due (ens_outputs.cu).
+int probe_record(ens_ctx *c);
 inline size_t elem_size(int form) { return form == kFP64 ? 8 : 4; }
 
 template <typename R>

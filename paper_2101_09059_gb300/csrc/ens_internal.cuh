@@ -159,6 +159,11 @@ cudaError_t launch_setup_stability(const int32_t *tri, const double *eh64, const
                                    double rho, double *w2lo, double *w2hi, cudaStream_t s);
 cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
                            cudaStream_t s);
+// Output statistics (ens_outputs.cu).
+cudaError_t launch_element_mean(const int32_t *tri, const double *En, int32_t E, int32_t Sp, double *ebar,
+                                cudaStream_t s);
+cudaError_t launch_row_stats(const double *rows, int64_t n_rows, int32_t S, int32_t n_q, const double *q_dev,
+                             double *mean, double *var, double *quant, cudaStream_t s);
 cudaError_t launch_pad_fields(const double *src, int32_t N, int32_t S, int32_t Sp, double *dst,
                               int *bad, cudaStream_t s);
 cudaError_t launch_convert(const double *in, int64_t n, void *out, int to_float, int invert,

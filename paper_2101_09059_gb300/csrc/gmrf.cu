@@ -45,7 +45,7 @@ struct gmrf_ctx {
     // work vectors, sized for cap_sp samples
     int32_t cap_sp = 0;
     double *x = nullptr, *r = nullptr, *zv = nullptr, *p = nullptr, *q = nullptr;
-    double *part = nullptr;  // [2][kMaxBlocks][Sp]
+    double *part = nullptr;  // [2][Sp][G]: per-sample partial sums, contiguous over blocks
     double *scal = nullptr;  // [6][Sp]: rz, alpha, beta, bb, relres2, active
     int *n_active = nullptr;
     int *h_active = nullptr;  // pinned
@@ -94,7 +94,7 @@ Geo geometry(int32_t N, int32_t Sp) {
 }
 
 // Sum the per-thread double2 partials of a block over its rows (fixed pairwise tree) and
-// write them to part[w][blockIdx.x][s].
+// write them to part[w][s][blockIdx.x].
 __device__ __forceinline__ void block_partial(double2 v, double2 *sm, double *part, int w,
                                               int G, int32_t Sp, int lane_q) {
     const int R = blockDim.y, Qt = blockDim.x;
@@ -112,9 +112,9 @@ __device__ __forceinline__ void block_partial(double2 v, double2 *sm, double *pa
     }
     if (y == 0 && lane_q < Sp / 2) {
         double2 t = sm[xq];
-        double *dst = part + ((size_t)w * G + blockIdx.x) * Sp + 2 * lane_q;
+        double *dst = part + ((size_t)w * Sp + 2 * lane_q) * G + blockIdx.x;
         dst[0] = t.x;
-        dst[1] = t.y;
+        dst[G] = t.y;
     }
     __syncthreads();
 }
@@ -169,7 +169,24 @@ __global__ void spmv_dot_kernel(const int32_t *__restrict__ rowptr, const int32_
         const int s0 = 2 * lane_q;
         double2 acc = make_double2(0.0, 0.0);
         const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
-        for (int32_t k = k0; k < k1; k++) {
+        // the first kUnroll entries: all column indices first, then all vector loads, so a
+        // row costs two dependent round trips instead of one per entry
+        constexpr int kUnroll = 8;
+        int32_t cj[kUnroll];
+        double aj[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const bool ok = k0 + u < k1;
+            cj[u] = ok ? __ldg(col + k0 + u) : (int32_t)i;
+            aj[u] = ok ? __ldg(val + k0 + u) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(p + (size_t)cj[u] * Sp + s0));
+            acc.x = fma(aj[u], v.x, acc.x);
+            acc.y = fma(aj[u], v.y, acc.y);
+        }
+        for (int32_t k = k0 + kUnroll; k < k1; k++) {
             const double a = __ldg(val + k);
             const double2 v = __ldg(reinterpret_cast<const double2 *>(p + (size_t)__ldg(col + k) * Sp + s0));
             acc.x = fma(a, v.x, acc.x);
@@ -234,11 +251,12 @@ __global__ void pupdate_kernel(const double *__restrict__ beta, const double *__
     st2(p + 2 * t, pv);
 }
 
-// Sum of part[w][0..G)[s] by one warp per sample: fixed lane assignment, fixed tree.
+// Sum of part[w][s][0..G) by one warp per sample: fixed lane assignment, fixed tree.
 __device__ __forceinline__ double warp_total(const double *part, int w, int G, int32_t Sp, int s) {
     const int lane = threadIdx.x & 31;
+    const double *src = part + ((size_t)w * Sp + s) * G;
     double a = 0.0;
-    for (int b = lane; b < G; b += 32) a += part[((size_t)w * G + b) * Sp + s];
+    for (int b = lane; b < G; b += 32) a += src[b];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     return a;

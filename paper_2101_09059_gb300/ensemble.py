@@ -14,6 +14,7 @@ from . import _lib
 
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
 FLAG_NO_AUTOTUNE, FLAG_UNSTAGED, FLAG_NO_GRAPH, FLAG_DEVICE_FIELDS = 1, 2, 4, 16
+QTY_DISPLACEMENT, QTY_DISP_MAGNITUDE, QTY_STRESS = 0, 1, 2
 
 
 def FLAG_FORCE_VARIANT(k: int) -> int:
@@ -227,6 +228,57 @@ class Ensemble:
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._call("ens_set_state", buf, len(blob))
 
+    # -- output statistics (Section 3) -------------------------------------------
+    def set_centerline(self, pts):
+        """Centreline polyline [n][3] of the stress frame (Section 2.2.3)."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64)
+        assert pts.ndim == 2 and pts.shape[1] == 3
+        self._call("ens_set_centerline", pts.shape[0], _ptr(pts))
+
+    def quantity_rows(self, qty: int) -> int:
+        return {QTY_DISPLACEMENT: 3 * self.N, QTY_DISP_MAGNITUDE: self.N, QTY_STRESS: 6 * self.E}[qty]
+
+    def quantity_device(self, qty: int, out=None):
+        """Rows of a quantity at the current step as a CUDA float64 tensor [rows][S]."""
+        torch = _torch()
+        rows = self.quantity_rows(qty)
+        if out is None:
+            out = torch.empty((rows, self.S), dtype=torch.float64, device=f"cuda:{self.device}")
+        assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == rows * self.S
+        self._call("ens_quantity_device", int(qty), ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def quantity_stats(self, qty: int, q=()):
+        """(mean [rows], variance [rows], quantiles [rows][len(q)] or None) of a quantity."""
+        rows = self.quantity_rows(qty)
+        qa = np.ascontiguousarray(q, dtype=np.float64)
+        mean, var = np.empty(rows), np.empty(rows)
+        quant = np.empty((rows, len(qa))) if len(qa) else None
+        self._call("ens_quantity_stats", int(qty), len(qa), _ptr(qa) if len(qa) else None, _ptr(mean), _ptr(var),
+                   _ptr(quant) if quant is not None else None)
+        return mean, var, quant
+
+    def set_probes(self, nodes=(), elems=(), stride: int = 0, capacity: int = 0):
+        """Record displacement at probe nodes and stress at probe elements every stride steps."""
+        n = np.ascontiguousarray(nodes, dtype=np.int32)
+        e = np.ascontiguousarray(elems, dtype=np.int32)
+        self._probe_sizes = (n.size, e.size)
+        self._call("ens_set_probes", n.size, _ptr(n) if n.size else None, e.size, _ptr(e) if e.size else None,
+                   int(stride), int(capacity))
+
+    def probes(self):
+        """(steps [n_rec], u [n_rec][n_nodes][3][S], sigma [n_rec][n_elems][6][S])."""
+        nn, ne = getattr(self, "_probe_sizes", (0, 0))
+        n_rec = ctypes.c_int64()
+        self._call("ens_get_probes", None, None, None, ctypes.byref(n_rec))
+        r = n_rec.value
+        u = np.empty((r, nn, 3, self.S))
+        sig = np.empty((r, ne, 6, self.S))
+        steps = np.empty(r, dtype=np.int64)
+        self._call("ens_get_probes", _ptr(u) if u.size else None, _ptr(sig) if sig.size else None,
+                   _ptr(steps) if r else None, ctypes.byref(n_rec))
+        return steps, u, sig
+
     def info(self) -> dict:
         i = _lib.ens_info_t()
         self._call("ens_info", ctypes.byref(i))
@@ -324,3 +376,24 @@ def sharded_stats(count, mean, var, group=None):
     dist.all_gather(cs, c, group=group)
     parts = [(int(cc.item()), mm.cpu().numpy(), vv.cpu().numpy()) for cc, mm, vv in zip(cs, ms, vs)]
     return merge_stats(parts)
+
+
+def row_stats_device(rows, q=(), stream=None):
+    """Mean, sample variance and type-7 quantiles of every row of a CUDA float64 tensor
+    [n_rows][S] (ens_row_stats_device); returns CUDA tensors (mean, var, quant or None)."""
+    torch = _torch()
+    L = _lib.load()
+    assert rows.is_cuda and rows.dtype == torch.float64 and rows.is_contiguous() and rows.dim() == 2
+    n, S = rows.shape
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    mean = torch.empty(n, dtype=torch.float64, device=rows.device)
+    var = torch.empty_like(mean)
+    quant = torch.empty((n, len(qa)), dtype=torch.float64, device=rows.device) if len(qa) else None
+    st = stream if stream is not None else torch.cuda.current_stream(rows.device)
+    rc = L.ens_row_stats_device(n, S, ctypes.c_void_p(rows.data_ptr()), len(qa), _ptr(qa) if len(qa) else None,
+                                ctypes.c_void_p(mean.data_ptr()), ctypes.c_void_p(var.data_ptr()),
+                                ctypes.c_void_p(quant.data_ptr()) if quant is not None else None,
+                                ctypes.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise EnsError(rc, L.ens_error_string(rc).decode())
+    return mean, var, quant
