@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-fields", action="store_true")
+    ap.add_argument("--no-outputs", action="store_true")
+    ap.add_argument("--no-paper-tables", action="store_true")
     ap.add_argument("--force-variant", type=int, default=-1,
                     help="use this step-kernel launch shape instead of autotuning (profiling)")
     ap.add_argument("--drift", action="store_true", help="long-run drift study instead of the benchmark")
@@ -272,7 +274,8 @@ def bench_tiny(args, local, stream):
 
 def bench_fields(args, local, stream, hbm_peak):
     """Device Matérn field sampler on the 200k-node aneurysm: the E and h draws of S = 64
-    realisations (x = K^-1 C~^(1/2) z by conjugate gradients to rtol 1e-10), against the
+    realisations (x = K^-1 C~^(1/2) z by binary32 conjugate gradients with binary64
+    refinement to rtol 1e-10), against the
     oracle's direct sparse solve on the host cores (factorisation plus a bounded number of
     solves, scaled to S)."""
     import torch
@@ -286,7 +289,7 @@ def bench_fields(args, local, stream, hbm_peak):
     out = torch.empty_like(z[0])
     fs.sample(z[0], scale=fs.scale_for(sigma), mean=0.7e6, lognormal=True, rtol=rtol, out=out)  # warm-up
     torch.cuda.synchronize()
-    times, iters = [], []
+    times, iters, refs = [], [], []
     for k, mean in ((0, 0.7e6), (1, 1e-3)):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -295,15 +298,20 @@ def bench_fields(args, local, stream, hbm_peak):
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1) / 1e3)
         iters.append(fs.info()["iterations"])
+        refs.append(fs.info()["refinements"])
     info = fs.info()
     t = sum(times)
-    achieved = info["bytes_per_iter"] * sum(iters) / t / 1e9
+    # binary32 inner iterations plus the binary64 correction / residual steps
+    alg = info["bytes_per_iter"] * sum(iters) + info["bytes_per_refinement"] * sum(refs)
+    achieved = alg / t / 1e9
     res = {"workload": f"aneurysm tube, {m.n_nodes} nodes, {m.tri.shape[0]} triangles, E and h fields of S={S} realisations (Matern nu=1, rho=2 cm, std 0.1)",
            "rtol": rtol, "seconds": t, "iterations": iters, "max_relres": info["max_relres"],
            "fields_per_s": 2 * S / t,
+           "refinements": refs,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved / hbm_peak,
-                        "algorithmic_bytes_per_iter": info["bytes_per_iter"]}}
+                        "algorithmic_bytes_per_iter": info["bytes_per_iter"],
+                        "algorithmic_bytes_per_refinement": info["bytes_per_refinement"]}}
     fs.close()
     if not args.no_cpu_baseline:
         import time
@@ -322,6 +330,126 @@ def bench_fields(args, local, stream, hbm_peak):
                                          f"2 fields x {S} samples",
                                "seconds_scaled": t_host}
     return res
+
+
+def bench_outputs(args, local, stream, hbm_peak):
+    """Output statistics on the 200k-node aneurysm at S = 64 (FP32-force state after 200
+    steps): element stress in the cylindrical frame for every element and realisation,
+    and mean / variance / 5-50-95 % quantiles of |u| per node and of every stress row."""
+    import time
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+    from paper_2101_09059_gb300.ensemble import QTY_DISP_MAGNITUDE, QTY_STRESS
+    S = args.samples
+    case = synth.make_case("aneurysm", S=S, n_steps=210, seed=local)
+    m = case["mesh"]
+    axis = np.array([[0.0, 0.0, -0.01], [0.0, 0.0, 0.13]])
+    e = pkg.Ensemble.from_case(case, precision=HEADLINE, stream=stream, device=local)
+    e.set_centerline(axis)
+    e.step(200)
+    rows = e.quantity_device(QTY_STRESS)     # warm-up and buffer
+    q = [0.05, 0.5, 0.95]
+    e.quantity_stats(QTY_STRESS, q)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=5):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / reps
+
+    t_stress = timed(lambda: e.quantity_device(QTY_STRESS, out=rows))
+    t_rowstats = timed(lambda: pkg.ensemble.row_stats_device(rows, q, stream=stream))
+    t_sstats = timed(lambda: e.quantity_stats(QTY_STRESS, q))
+    t_ustats = timed(lambda: e.quantity_stats(QTY_DISP_MAGNITUDE, q))
+    E, N = m.n_elems, m.n_nodes
+    # stress kernel: the FP32-force state (head + tail, 8 B per dof) of every node once,
+    # the element-mean modulus, the 6 x 9 operators and the output rows
+    alg = N * 3 * S * 8.0 + E * S * 8.0 + E * 54 * 8.0 + E * 6 * S * 8.0
+    flops = E * S * (2.0 * 54 + 6)
+    res = {"workload": f"aneurysm tube, {N} nodes, {E} triangles, S={S}, FP32-force state after 200 steps",
+           "stress_rows_s": t_stress, "stress_row_stats_device_s": t_rowstats,
+           "stress_stats_to_host_s": t_sstats, "disp_magnitude_stats_to_host_s": t_ustats,
+           "quantiles": q,
+           "stress_kernel": {"achieved_gbs": alg / t_stress / 1e9, "hbm_frac": alg / t_stress / 1e9 / hbm_peak,
+                             "fp64_tflops": flops / t_stress / 1e12,
+                             "fp64_frac": flops / t_stress / 1e12 / FP64_PEAK_TFLOPS,
+                             "algorithmic_bytes": alg}}
+    if not args.no_cpu_baseline:
+        import oracle.outputs as oo
+        pick = [0, 1]
+        u = e.displacement()[pick]
+        t0 = time.perf_counter()
+        r = oo.element_stress(m.xyz, m.tri, u, case["E"][:, pick], case["nu"], case["kshear"], axis)
+        oo.row_stats(r, q)
+        t1 = time.perf_counter()
+        res["cpu_baseline"] = {"value": (t1 - t0) * S / len(pick), "unit": "s (stress rows + statistics)",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"{len(pick)} realisations timed, scaled to S={S}"}
+    e.close()
+    return res
+
+
+# Sample-steps/s the paper prints for its cylinder meshes (Tables 1-3, times read as
+# h:mm:ss over 1000 steps) on GeForce RTX 2080 Ti cards, FP64 implied: context only.
+PAPER_TABLES = {
+    0: {"elements": 5074, "S": 500, "paper": {"1 GPU (RTX 2080 Ti)": 2.5e4, "4 GPU": 5.6e4, "12 CPU": 870.0}},
+    1: {"elements": 15136, "S": 500, "paper": {"1 GPU (RTX 2080 Ti)": 8.9e3, "4 GPU": 2.6e4, "12 CPU": 431.0}},
+    3: {"elements": 131552, "S": 500, "paper": {"4 GPU": 3.7e3, "1 GPU at S = 200": 939.0}},
+}
+
+
+def bench_paper_tables(args, local, stream):
+    """The paper's own cylinder workloads (Section 3.1; Tables 1-3: meshes of 5,074,
+    15,136 and 131,552 elements, S = 500): E and h drawn on the device (Gaussian Matern
+    fields, correlation length 3.7 cm), the ensemble created from the device fields, and
+    200 steps timed after 50 in the binary64 form (the paper's precision) and the
+    FP32-force form."""
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+    rows = []
+    for level, ref in PAPER_TABLES.items():
+        S, steps, warm = ref["S"], 200, 50
+        case = synth.make_case("cylinder", level=level, S=S, n_steps=steps + warm + 2, host_fields=False)
+        m = case["mesh"]
+        fs = pkg.FieldSampler(m.xyz, m.tri, case["corr"], stream=stream)
+        rng = np.random.Generator(np.random.Philox(key=77 + level))
+        dev = f"cuda:{local}"
+        zE = torch.from_numpy(rng.standard_normal((m.n_nodes, S))).to(dev)
+        zh = torch.from_numpy(rng.standard_normal((m.n_nodes, S))).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E = fs.sample(zE, scale=fs.scale_for(0.07e6), mean=0.7e6, rtol=1e-8)
+        h = fs.sample(zh, scale=fs.scale_for(0.4e-3), mean=4.0e-3, rtol=1e-8)
+        torch.cuda.synchronize()
+        t_fields = time.perf_counter() - t0
+        fs.close()
+        row = {"elements": m.n_elems, "nodes": m.n_nodes, "S": S, "paper_elements": ref["elements"],
+               "fields_s": t_fields, "paper_sample_steps_per_s": ref["paper"]}
+        for form in ("fp64", HEADLINE):
+            e = pkg.Ensemble(m.xyz, m.tri, m.fixed, E, h, rho=case["rho"], nu=case["nu"], kshear=case["kshear"],
+                             alpha=case["alpha"], dt=case["dt"], precision=form, stream=stream, device=local)
+            e.set_traction(case["modes"], case["amp"])
+            e.step(warm)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            e.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t = ev0.elapsed_time(ev1) / 1e3
+            row[form] = {"sample_steps_per_s": S * steps / t, "node_sample_steps_per_s": m.n_nodes * S * steps / t}
+            e.close()
+        rows.append(row)
+        del E, h, zE, zh
+    return {"workload": "the paper's cylinder (D 4 cm, L 30 cm, Gaussian E 0.7 +- 0.07 MPa, h 4 +- 0.4 mm, "
+                        "corr 3.7 cm, 13 mmHg + Poiseuille load); fields drawn on the device",
+            "rows": rows}
 
 
 def bench_batched(args, local, stream, world):
@@ -643,6 +771,8 @@ def main():
     batched = None if args.no_batched else bench_batched(args, local, stream, world)
     surrogate = None if (args.no_surrogate or rank != 0) else bench_surrogate(args, local, stream)
     fields = None if (args.no_fields or rank != 0) else bench_fields(args, local, stream, hbm_peak)
+    outputs = None if (args.no_outputs or rank != 0) else bench_outputs(args, local, stream, hbm_peak)
+    tables = None if (args.no_paper_tables or rank != 0) else bench_paper_tables(args, local, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -684,6 +814,8 @@ def main():
         "batched_uneven": batched,
         "surrogate": surrogate,
         "field_sampler": fields,
+        "output_statistics": outputs,
+        "paper_tables": tables,
         "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
     }
     if rank == 0:

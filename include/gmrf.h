@@ -40,10 +40,13 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
  * innermost), read only. out: device [n_nodes][S] binary64, written with
  *     out = mean * exp(scale * x)   (lognormal = 1)   or   out = mean + scale * x   (0),
  * x = K^-1 C~^(1/2) z. For marginal standard deviation sigma of x (nu = 1, d = 2) pass
- * scale = sigma sqrt(4 pi) kappa. Conjugate gradients with Jacobi preconditioning run
- * from x = 0 until every sample has ||K x - b|| <= rtol ||b|| (b = C~^(1/2) z), or
- * max_iter iterations (then GMRF_ERR_NOT_CONVERGED, with out still written). Each
- * sample stops updating once it converges, so the result is deterministic.
+ * scale = sigma sqrt(4 pi) kappa. The solve is iterative refinement from x = 0: the
+ * residual b - K x (b = C~^(1/2) z) is formed in binary64, a Jacobi-preconditioned
+ * conjugate-gradient solve in binary32 reduces it by max(rtol, 1e-4), and x takes the
+ * correction in binary64, until every sample has ||K x - b|| <= rtol ||b|| in binary64,
+ * or max_iter binary32 iterations in all (then GMRF_ERR_NOT_CONVERGED, with out still
+ * written). Each sample stops updating once it converges, so the result is
+ * deterministic.
  * rtol in (0, 1), max_iter >= 1, S >= 1.                                            */
 int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double scale, double mean,
                 int32_t lognormal, double rtol, int32_t max_iter);
@@ -51,10 +54,12 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sca
 typedef struct {
     int32_t n_nodes;
     int64_t nnz;            /* stored entries of K                                  */
-    int32_t iterations;     /* CG iterations of the last gmrf_sample                */
-    double max_relres;      /* largest ||r|| / ||b|| over samples after it          */
+    int32_t iterations;     /* binary32 CG iterations of the last gmrf_sample       */
+    double max_relres;      /* largest binary64 ||b - K x|| / ||b|| over samples     */
     double bytes_per_iter;  /* algorithmic HBM bytes of one CG iteration at that S  */
     int32_t last_S;
+    int32_t refinements;    /* binary64 residual / correction steps it took         */
+    double bytes_per_refinement; /* algorithmic HBM bytes of one of those steps    */
 } gmrf_info_t;
 
 int gmrf_info(const gmrf_ctx *g, gmrf_info_t *info);

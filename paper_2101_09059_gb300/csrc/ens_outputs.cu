@@ -263,22 +263,33 @@ __global__ void probe_record_kernel(const void *u_main, const void *aux, const i
     for (int r = 0; r < 6; r++) hs[(p * 6 + r) * S + s] = sig[r];
 }
 
-// Mean, sample variance and type-7 quantiles of every row; one warp per row, the row
-// sorted in this warp's P doubles of shared memory (P = power of two >= S).
+// Order-preserving map of binary64 bit patterns to unsigned 64-bit keys (negative values
+// have every bit flipped, the others the sign bit), so the sort compares on the integer
+// pipe; GB300 issues binary64 comparisons at the binary64 rate.
+__device__ __forceinline__ uint64_t sort_key(double v) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    return b ^ ((b >> 63) ? ~0ull : 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(uint64_t k) {
+    return __longlong_as_double((long long)(k ^ ((k >> 63) ? 0x8000000000000000ull : ~0ull)));
+}
+
+// Mean, sample variance and type-7 quantiles of every row; one warp per row, the row's
+// sort keys in this warp's P words of shared memory (P = power of two >= S).
 __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows, int32_t S, int32_t P,
                                  int32_t n_q, const double *__restrict__ q, double *__restrict__ mean,
                                  double *__restrict__ var, double *__restrict__ quant) {
-    extern __shared__ double sm_rows[];
+    extern __shared__ uint64_t sm_keys[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    double *x = sm_rows + (size_t)wib * P;
+    uint64_t *x = sm_keys + (size_t)wib * P;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; row < n_rows; row += warps) {
         const double *src = rows + row * S;
         double sum = 0.0;
         for (int32_t i = lane; i < P; i += 32) {
             const double v = i < S ? src[i] : INFINITY;
-            x[i] = v;
+            x[i] = sort_key(v);
             if (i < S) sum += v;
         }
 #pragma unroll
@@ -286,7 +297,7 @@ __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows
         const double mu = sum / (double)S;
         double ss = 0.0;
         for (int32_t i = lane; i < S; i += 32) {
-            const double dlt = x[i] - mu;
+            const double dlt = src[i] - mu;
             ss = fma(dlt, dlt, ss);
         }
 #pragma unroll
@@ -302,7 +313,7 @@ __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows
                     for (int32_t i = lane; i < P; i += 32) {
                         const int32_t ixj = i ^ j;
                         if (ixj > i) {
-                            const double a = x[i], b = x[ixj];
+                            const uint64_t a = x[i], b = x[ixj];
                             if ((a > b) == ((i & k) == 0)) {
                                 x[i] = b;
                                 x[ixj] = a;
@@ -318,7 +329,8 @@ __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows
                 if (j < 0) j = 0;
                 const int32_t j1 = j + 1 < S ? j + 1 : S - 1;
                 const double g = __dsub_rn(h, (double)j);
-                quant[row * n_q + k] = __dadd_rn(x[j], __dmul_rn(g, __dsub_rn(x[j1], x[j])));
+                const double xj = key_value(x[j]), xj1 = key_value(x[j1]);
+                quant[row * n_q + k] = __dadd_rn(xj, __dmul_rn(g, __dsub_rn(xj1, xj)));
             }
         }
         __syncwarp();

@@ -1,17 +1,25 @@
 // Device Matérn random-field sampler (Section 2.1): x = K^-1 C~^(1/2) z with
-// K = kappa^2 C~ + G, all S right-hand sides at once by Jacobi-preconditioned conjugate
-// gradients, vectors stored [N][Sp] with the sample index innermost (Sp = S rounded up
-// to even; each thread owns one node row and two samples).
+// K = kappa^2 C~ + G, all S right-hand sides at once, vectors stored [N][Sp] with the
+// sample index innermost (Sp = S rounded up to even; each thread owns one node row and
+// two samples).
 //
-// One CG iteration is five kernels:
-//   spmv_dot   q = K p, and per-block partial sums of p.q for every sample;
+// GB300 issues binary64 arithmetic at about 1/64 of its binary32 rate, and a binary64 CG
+// iteration is bound by that pipe (13 binary64 FMAs per row and sample), so the solve is
+// mixed-precision iterative refinement:
+//   outer, binary64:  r = b - K x (true residual), stop per sample at ||r|| <= rtol ||b||;
+//   inner, binary32:  Jacobi-preconditioned CG on K d = r / ||r|| to relative tolerance
+//                     max(rtol, 1e-4), then x += ||r|| d.
+// Each refinement gains about four digits (K has condition ~1e3 on the workloads, so the
+// binary32 solve is accurate to ~1e-4), and the final residual is the binary64 one.
+// One inner iteration is five kernels:
+//   spmv_dot   q = K p (binary32 matrix), per-block partial sums of p.q;
 //   fin_alpha  alpha_s = rz_s / (p.q)_s (0 once sample s has converged);
-//   update     x += alpha p, r -= alpha q, z = M^-1 r, partial sums of r.z and r.r;
-//   fin_beta   beta_s = rz_new / rz, convergence test ||r|| <= rtol ||b||, active count;
-//   pupdate    p = z + beta p.
+//   update     d += alpha p, r -= alpha q, partial sums of r.z and r.r with z = M^-1 r;
+//   fin_beta   beta_s, convergence test, active count;
+//   pupdate    p = M^-1 r + beta p.
 // Every reduction has a fixed shape (fixed grid, fixed tree), so results are bitwise
 // reproducible; a converged sample takes alpha = beta = 0 from then on, so stopping a
-// few iterations later changes nothing. Iterations run as replays of a captured graph.
+// few iterations later changes nothing. Inner iterations run as replays of a graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,12 +31,15 @@
 #include <vector>
 
 #include "../../include/gmrf.h"
+#include "ens_bits.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 1216;  // 152 SMs x 8: fixed reduction shape
 constexpr int kGraphIters = 8;
+constexpr double kInnerTol = 1e-4;
+constexpr int kMaxRefinements = 16;
 
 thread_local char g_create_err[256] = "";
 
@@ -41,22 +52,28 @@ struct gmrf_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int32_t *rowptr = nullptr, *col = nullptr;
-    double *val = nullptr, *minv = nullptr, *sqrtc = nullptr;
+    double *val = nullptr, *sqrtc = nullptr;
+    float *val32 = nullptr, *minv32 = nullptr;
     // work vectors, sized for cap_sp samples
     int32_t cap_sp = 0;
-    double *x = nullptr, *r = nullptr, *zv = nullptr, *p = nullptr, *q = nullptr;
+    double *b = nullptr, *x = nullptr, *r = nullptr;       // binary64 [N][Sp]
+    float *d = nullptr, *ri = nullptr, *p = nullptr, *q = nullptr;  // binary32 [N][Sp]
     double *part = nullptr;  // [2][Sp][G]: per-sample partial sums, contiguous over blocks
-    double *scal = nullptr;  // [6][Sp]: rz, alpha, beta, bb, relres2, active
+    double *scal = nullptr;  // [kScal][Sp], rows below
+    float *scal32 = nullptr; // [2][Sp]: alpha, beta in binary32
     int *n_active = nullptr;
     int *h_active = nullptr;  // pinned
     cudaGraphExec_t graph = nullptr;
     int32_t graph_sp = -1;
-    double graph_rtol = -1.0;
+    double graph_tol = -1.0;
     gmrf_info_t info{};
     char err[256] = "";
 };
 
 namespace {
+
+// rows of scal
+enum { kRz = 0, kBbIn, kActIn, kBb, kRr, kScale, kActOut, kScal };
 
 int fail(gmrf_ctx *g, int code, const char *fmt, ...) {
     char *dst = g ? g->err : g_create_err;
@@ -93,8 +110,8 @@ Geo geometry(int32_t N, int32_t Sp) {
     return o;
 }
 
-// Sum the per-thread double2 partials of a block over its rows (fixed pairwise tree) and
-// write them to part[w][s][blockIdx.x].
+// Sum the per-thread partials of a block over its rows (fixed pairwise tree, binary64)
+// and write them to part[w][s][blockIdx.x].
 __device__ __forceinline__ void block_partial(double2 v, double2 *sm, double *part, int w,
                                               int G, int32_t Sp, int lane_q) {
     const int R = blockDim.y, Qt = blockDim.x;
@@ -119,136 +136,184 @@ __device__ __forceinline__ void block_partial(double2 v, double2 *sm, double *pa
     __syncthreads();
 }
 
+// binary32 pair -> binary64 pair on the integer pipe (exact)
+__device__ __forceinline__ double2 widen(float2 a) { return make_double2(ens::f32_to_f64(a.x), ens::f32_to_f64(a.y)); }
+
 __device__ __forceinline__ double2 ld2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
 __device__ __forceinline__ void st2(double *p, double2 v) { *reinterpret_cast<double2 *>(p) = v; }
+__device__ __forceinline__ float2 ldf2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void stf2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 
-// r = C~^(1/2) z (padding samples 0), x = 0, z = M^-1 r, p = z; partials r.z and r.r.
-__global__ void init_kernel(const double *__restrict__ zin, int32_t S, int32_t Sp, int32_t N,
-                            int64_t tiles, const double *__restrict__ sqrtc,
-                            const double *__restrict__ minv, double *x, double *r, double *zv,
-                            double *p, double *part) {
+#define ROW_LOOP                                                          \
+    const int lane_q = blockIdx.y * blockDim.x + threadIdx.x;             \
+    const bool lane_ok = lane_q < Sp / 2;                                 \
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {             \
+        const int64_t i = t * blockDim.y + threadIdx.y;                   \
+        if (i >= N || !lane_ok) continue;                                 \
+        const int s0 = 2 * lane_q;                                        \
+        const size_t o = (size_t)i * Sp + s0;
+
+// b = C~^(1/2) z (padding samples 0), x = 0, r = b; partials of r.r.
+__global__ void rhs_kernel(const double *__restrict__ zin, int32_t S, int32_t Sp, int32_t N, int64_t tiles,
+                           const double *__restrict__ sqrtc, double *b, double *x, double *r, double *part) {
     extern __shared__ double2 sm[];
-    const int lane_q = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool lane_ok = lane_q < Sp / 2;
-    double2 rz = make_double2(0.0, 0.0), rr = rz;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int64_t i = t * blockDim.y + threadIdx.y;
-        if (i >= N || !lane_ok) continue;
-        const int s0 = 2 * lane_q;
-        const double c = sqrtc[i], m = minv[i];
+    double2 rr = make_double2(0.0, 0.0);
+    ROW_LOOP
+        const double c = sqrtc[i];
         const double z0 = s0 < S ? zin[i * S + s0] : 0.0;
         const double z1 = s0 + 1 < S ? zin[i * S + s0 + 1] : 0.0;
-        const double2 rv = make_double2(c * z0, c * z1);
-        const double2 zz = make_double2(m * rv.x, m * rv.y);
-        const size_t o = (size_t)i * Sp + s0;
+        const double2 bv = make_double2(c * z0, c * z1);
+        st2(b + o, bv);
+        st2(r + o, bv);
         st2(x + o, make_double2(0.0, 0.0));
-        st2(r + o, rv);
-        st2(zv + o, zz);
-        st2(p + o, zz);
-        rz.x += rv.x * zz.x;
-        rz.y += rv.y * zz.y;
-        rr.x += rv.x * rv.x;
-        rr.y += rv.y * rv.y;
+        rr.x = fma(bv.x, bv.x, rr.x);
+        rr.y = fma(bv.y, bv.y, rr.y);
     }
-    block_partial(rz, sm, part, 0, gridDim.x, Sp, lane_q);
-    block_partial(rr, sm, part, 1, gridDim.x, Sp, lane_q);
+    block_partial(rr, sm, part, 0, gridDim.x, Sp, lane_q);
 }
 
-// q = K p and partials of p.q.
-__global__ void spmv_dot_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                const double *__restrict__ val, const double *__restrict__ p,
-                                double *__restrict__ q, int32_t N, int32_t Sp, int64_t tiles,
+// x += scale d (the inner correction, samples still active).
+__global__ void correct_kernel(const float *__restrict__ d, const double *__restrict__ scale, double *x,
+                               int32_t N, int32_t Sp) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * Sp / 2) return;
+    const int32_t s0 = (int32_t)(2 * (t % (Sp / 2)));
+    const double2 sc = ld2(scale + s0);
+    const double2 dv = widen(ldf2(d + 2 * t));
+    double2 xv = ld2(x + 2 * t);
+    xv.x = fma(sc.x, dv.x, xv.x);
+    xv.y = fma(sc.y, dv.y, xv.y);
+    st2(x + 2 * t, xv);
+}
+
+// r = b - K x in binary64, partials of r.r.
+__global__ void residual_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                const double *__restrict__ val, const double *__restrict__ x,
+                                const double *__restrict__ b, double *r, int32_t N, int32_t Sp, int64_t tiles,
                                 double *part) {
     extern __shared__ double2 sm[];
-    const int lane_q = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool lane_ok = lane_q < Sp / 2;
-    double2 pq = make_double2(0.0, 0.0);
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int64_t i = t * blockDim.y + threadIdx.y;
-        if (i >= N || !lane_ok) continue;
-        const int s0 = 2 * lane_q;
-        double2 acc = make_double2(0.0, 0.0);
+    double2 rr = make_double2(0.0, 0.0);
+    ROW_LOOP
+        double2 acc = ld2(b + o);
+        const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
+        for (int32_t k = k0; k < k1; k++) {
+            const double a = __ldg(val + k);
+            const double2 v = __ldg(reinterpret_cast<const double2 *>(x + (size_t)__ldg(col + k) * Sp + s0));
+            acc.x = fma(-a, v.x, acc.x);
+            acc.y = fma(-a, v.y, acc.y);
+        }
+        st2(r + o, acc);
+        rr.x = fma(acc.x, acc.x, rr.x);
+        rr.y = fma(acc.y, acc.y, rr.y);
+    }
+    block_partial(rr, sm, part, 0, gridDim.x, Sp, lane_q);
+}
+
+// Inner start: r_i = r / ||r|| (binary32, 0 for converged samples), d = 0, p = M^-1 r_i;
+// partials of r_i.z and r_i.r_i.
+__global__ void inner_init_kernel(const double *__restrict__ r, const double *__restrict__ inv_scale,
+                                  const float *__restrict__ minv, float *d, float *ri, float *p, int32_t N,
+                                  int32_t Sp, int64_t tiles, double *part) {
+    extern __shared__ double2 sm[];
+    float2 rz = make_float2(0.f, 0.f), rr = rz;
+    ROW_LOOP
+        const double2 is = ld2(inv_scale + s0);
+        const double2 rv = ld2(r + o);
+        const float2 rf = make_float2(ens::f64_to_f32_rz(rv.x * is.x), ens::f64_to_f32_rz(rv.y * is.y));
+        const float m = minv[i];
+        const float2 zz = make_float2(m * rf.x, m * rf.y);
+        stf2(ri + o, rf);
+        stf2(d + o, make_float2(0.f, 0.f));
+        stf2(p + o, zz);
+        rz.x = fmaf(rf.x, zz.x, rz.x);
+        rz.y = fmaf(rf.y, zz.y, rz.y);
+        rr.x = fmaf(rf.x, rf.x, rr.x);
+        rr.y = fmaf(rf.y, rf.y, rr.y);
+    }
+    block_partial(widen(rz), sm, part, 0, gridDim.x, Sp, lane_q);
+    block_partial(widen(rr), sm, part, 1, gridDim.x, Sp, lane_q);
+}
+
+// q = K p (binary32) and partials of p.q.
+__global__ void spmv_dot_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                const float *__restrict__ val, const float *__restrict__ p,
+                                float *__restrict__ q, int32_t N, int32_t Sp, int64_t tiles, double *part) {
+    extern __shared__ double2 sm[];
+    float2 pq = make_float2(0.f, 0.f);
+    ROW_LOOP
+        float2 acc = make_float2(0.f, 0.f);
         const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
         // the first kUnroll entries: all column indices first, then all vector loads, so a
         // row costs two dependent round trips instead of one per entry
-        constexpr int kUnroll = 8;
+        constexpr int kUnroll = 7;
         int32_t cj[kUnroll];
-        double aj[kUnroll];
+        float aj[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; u++) {
             const bool ok = k0 + u < k1;
             cj[u] = ok ? __ldg(col + k0 + u) : (int32_t)i;
-            aj[u] = ok ? __ldg(val + k0 + u) : 0.0;
+            aj[u] = ok ? __ldg(val + k0 + u) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; u++) {
-            const double2 v = __ldg(reinterpret_cast<const double2 *>(p + (size_t)cj[u] * Sp + s0));
-            acc.x = fma(aj[u], v.x, acc.x);
-            acc.y = fma(aj[u], v.y, acc.y);
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(p + (size_t)cj[u] * Sp + s0));
+            acc.x = fmaf(aj[u], v.x, acc.x);
+            acc.y = fmaf(aj[u], v.y, acc.y);
         }
         for (int32_t k = k0 + kUnroll; k < k1; k++) {
-            const double a = __ldg(val + k);
-            const double2 v = __ldg(reinterpret_cast<const double2 *>(p + (size_t)__ldg(col + k) * Sp + s0));
-            acc.x = fma(a, v.x, acc.x);
-            acc.y = fma(a, v.y, acc.y);
+            const float a = __ldg(val + k);
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(p + (size_t)__ldg(col + k) * Sp + s0));
+            acc.x = fmaf(a, v.x, acc.x);
+            acc.y = fmaf(a, v.y, acc.y);
         }
-        const size_t o = (size_t)i * Sp + s0;
-        st2(q + o, acc);
-        const double2 pv = ld2(p + o);
-        pq.x = fma(pv.x, acc.x, pq.x);
-        pq.y = fma(pv.y, acc.y, pq.y);
+        stf2(q + o, acc);
+        const float2 pv = ldf2(p + o);
+        pq.x = fmaf(pv.x, acc.x, pq.x);
+        pq.y = fmaf(pv.y, acc.y, pq.y);
     }
-    block_partial(pq, sm, part, 0, gridDim.x, Sp, lane_q);
+    block_partial(widen(pq), sm, part, 0, gridDim.x, Sp, lane_q);
 }
 
-// x += alpha p, r -= alpha q, z = M^-1 r; partials of r.z and r.r.
-__global__ void update_kernel(const double *__restrict__ minv, const double *__restrict__ alpha,
-                              double *x, double *r, double *zv, const double *__restrict__ p,
-                              const double *__restrict__ q, int32_t N, int32_t Sp, int64_t tiles,
-                              double *part) {
+// d += alpha p, r -= alpha q; partials of r.z (z = M^-1 r) and r.r.
+__global__ void update_kernel(const float *__restrict__ minv, const float *__restrict__ alpha, float *d,
+                              float *ri, const float *__restrict__ p, const float *__restrict__ q, int32_t N,
+                              int32_t Sp, int64_t tiles, double *part) {
     extern __shared__ double2 sm[];
-    const int lane_q = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool lane_ok = lane_q < Sp / 2;
-    double2 rz = make_double2(0.0, 0.0), rr = rz;
-    double2 al = make_double2(0.0, 0.0);
-    if (lane_ok) al = ld2(alpha + 2 * lane_q);
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int64_t i = t * blockDim.y + threadIdx.y;
-        if (i >= N || !lane_ok) continue;
-        const size_t o = (size_t)i * Sp + 2 * lane_q;
-        const double2 pv = ld2(p + o), qv = ld2(q + o);
-        double2 xv = ld2(x + o), rv = ld2(r + o);
-        xv.x = fma(al.x, pv.x, xv.x);
-        xv.y = fma(al.y, pv.y, xv.y);
-        rv.x = fma(-al.x, qv.x, rv.x);
-        rv.y = fma(-al.y, qv.y, rv.y);
-        const double m = minv[i];
-        const double2 zz = make_double2(m * rv.x, m * rv.y);
-        st2(x + o, xv);
-        st2(r + o, rv);
-        st2(zv + o, zz);
-        rz.x = fma(rv.x, zz.x, rz.x);
-        rz.y = fma(rv.y, zz.y, rz.y);
-        rr.x = fma(rv.x, rv.x, rr.x);
-        rr.y = fma(rv.y, rv.y, rr.y);
+    float2 rz = make_float2(0.f, 0.f), rr = rz;
+    const int lq = blockIdx.y * blockDim.x + threadIdx.x;
+    const float2 al = lq < Sp / 2 ? ldf2(alpha + 2 * lq) : make_float2(0.f, 0.f);
+    ROW_LOOP
+        const float2 pv = ldf2(p + o), qv = ldf2(q + o);
+        float2 dv = ldf2(d + o), rv = ldf2(ri + o);
+        dv.x = fmaf(al.x, pv.x, dv.x);
+        dv.y = fmaf(al.y, pv.y, dv.y);
+        rv.x = fmaf(-al.x, qv.x, rv.x);
+        rv.y = fmaf(-al.y, qv.y, rv.y);
+        stf2(d + o, dv);
+        stf2(ri + o, rv);
+        const float m = minv[i];
+        rz.x = fmaf(rv.x, m * rv.x, rz.x);
+        rz.y = fmaf(rv.y, m * rv.y, rz.y);
+        rr.x = fmaf(rv.x, rv.x, rr.x);
+        rr.y = fmaf(rv.y, rv.y, rr.y);
     }
-    block_partial(rz, sm, part, 0, gridDim.x, Sp, lane_q);
-    block_partial(rr, sm, part, 1, gridDim.x, Sp, lane_q);
+    block_partial(widen(rz), sm, part, 0, gridDim.x, Sp, lane_q);
+    block_partial(widen(rr), sm, part, 1, gridDim.x, Sp, lane_q);
 }
 
-// p = z + beta p.
-__global__ void pupdate_kernel(const double *__restrict__ beta, const double *__restrict__ zv,
-                               double *p, int32_t N, int32_t Sp) {
+// p = M^-1 r + beta p.
+__global__ void pupdate_kernel(const float *__restrict__ beta, const float *__restrict__ minv,
+                               const float *__restrict__ ri, float *p, int32_t N, int32_t Sp) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t n2 = (int64_t)N * Sp / 2;
-    if (t >= n2) return;
+    if (t >= (int64_t)N * Sp / 2) return;
     const int32_t s0 = (int32_t)(2 * (t % (Sp / 2)));
-    const double2 b = ld2(beta + s0);
-    const double2 zz = ld2(zv + 2 * t);
-    double2 pv = ld2(p + 2 * t);
-    pv.x = fma(b.x, pv.x, zz.x);
-    pv.y = fma(b.y, pv.y, zz.y);
-    st2(p + 2 * t, pv);
+    const float m = minv[t / (Sp / 2)];
+    const float2 b = ldf2(beta + s0);
+    const float2 rv = ldf2(ri + 2 * t);
+    float2 pv = ldf2(p + 2 * t);
+    pv.x = fmaf(b.x, pv.x, m * rv.x);
+    pv.y = fmaf(b.y, pv.y, m * rv.y);
+    stf2(p + 2 * t, pv);
 }
 
 // Sum of part[w][s][0..G) by one warp per sample: fixed lane assignment, fixed tree.
@@ -262,57 +327,71 @@ __device__ __forceinline__ double warp_total(const double *part, int w, int G, i
     return a;
 }
 
-// scal rows: 0 rz, 1 alpha, 2 beta, 3 bb, 4 relres^2, 5 active
-__global__ void fin_init_kernel(const double *part, int G, int32_t Sp, double *scal, int *n_active) {
-    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (s >= Sp) return;
-    const double rz = warp_total(part, 0, G, Sp, s);
-    const double bb = warp_total(part, 1, G, Sp, s);
-    if ((threadIdx.x & 31) == 0) {
-        const bool act = bb > 0.0;
-        scal[0 * Sp + s] = rz;
-        scal[1 * Sp + s] = 0.0;
-        scal[2 * Sp + s] = 0.0;
-        scal[3 * Sp + s] = bb;
-        scal[4 * Sp + s] = act ? 1.0 : 0.0;
-        scal[5 * Sp + s] = act ? 1.0 : 0.0;
+#define FIN_SAMPLE                                                     \
+    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   \
+    if (s >= Sp) return;                                               \
+    const bool lead = (threadIdx.x & 31) == 0;
+#define SC(row) scal[(size_t)(row) * Sp + s]
+
+// Outer test after a residual: rr = ||r||^2 (first: also ||b||^2); a sample stays active
+// while rr > rtol^2 bb; the inner right-hand side is r / ||r||.
+__global__ void fin_outer_kernel(const double *part, int G, int32_t Sp, double rtol2, int first, double *scal,
+                                 double *inv_scale, int *n_active) {
+    FIN_SAMPLE
+    const double rr = warp_total(part, 0, G, Sp, s);
+    if (lead) {
+        if (first) SC(kBb) = rr;
+        const double bb = SC(kBb);
+        const bool act = bb > 0.0 && rr > rtol2 * bb && (first || SC(kActOut) != 0.0);
+        SC(kRr) = rr;
+        SC(kActOut) = act ? 1.0 : 0.0;
+        SC(kScale) = act ? sqrt(rr) : 0.0;
+        inv_scale[s] = act ? 1.0 / sqrt(rr) : 0.0;
         if (act) atomicAdd(n_active, 1);
     }
 }
 
-__global__ void fin_alpha_kernel(const double *part, int G, int32_t Sp, double *scal, int *n_active) {
-    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_active = 0;
-    if (s >= Sp) return;
-    const double pq = warp_total(part, 0, G, Sp, s);
-    if ((threadIdx.x & 31) == 0) {
-        const bool act = scal[5 * Sp + s] != 0.0;
-        scal[1 * Sp + s] = (act && pq > 0.0) ? scal[0 * Sp + s] / pq : 0.0;
+__global__ void fin_inner_init_kernel(const double *part, int G, int32_t Sp, double *scal, int *n_active) {
+    FIN_SAMPLE
+    const double rz = warp_total(part, 0, G, Sp, s);
+    const double bb = warp_total(part, 1, G, Sp, s);
+    if (lead) {
+        const bool act = bb > 0.0;
+        SC(kRz) = rz;
+        SC(kBbIn) = bb;
+        SC(kActIn) = act ? 1.0 : 0.0;
+        if (act) atomicAdd(n_active, 1);
     }
 }
 
-__global__ void fin_beta_kernel(const double *part, int G, int32_t Sp, double rtol2, double *scal,
+__global__ void fin_alpha_kernel(const double *part, int G, int32_t Sp, double *scal, float *alpha32,
+                                 int *n_active) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_active = 0;
+    FIN_SAMPLE
+    const double pq = warp_total(part, 0, G, Sp, s);
+    if (lead) {
+        const bool act = SC(kActIn) != 0.0;
+        alpha32[s] = (act && pq > 0.0) ? ens::f64_to_f32_rz(SC(kRz) / pq) : 0.f;
+    }
+}
+
+__global__ void fin_beta_kernel(const double *part, int G, int32_t Sp, double tol2, double *scal, float *beta32,
                                 int *n_active) {
-    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (s >= Sp) return;
+    FIN_SAMPLE
     const double rz = warp_total(part, 0, G, Sp, s);
     const double rr = warp_total(part, 1, G, Sp, s);
-    if ((threadIdx.x & 31) == 0) {
-        const bool act = scal[5 * Sp + s] != 0.0;
-        if (act) {
-            const double bb = scal[3 * Sp + s];
-            const bool done = rr <= rtol2 * bb;
-            scal[2 * Sp + s] = (done || !(scal[0 * Sp + s] > 0.0)) ? 0.0 : rz / scal[0 * Sp + s];
-            scal[0 * Sp + s] = rz;
-            scal[4 * Sp + s] = rr / bb;
-            if (done) {
-                scal[5 * Sp + s] = 0.0;
-            } else {
+    if (lead) {
+        float beta = 0.f;
+        if (SC(kActIn) != 0.0) {
+            const bool done = rr <= tol2 * SC(kBbIn);
+            if (!done && SC(kRz) > 0.0) beta = ens::f64_to_f32_rz(rz / SC(kRz));
+            SC(kRz) = rz;
+            if (done)
+                SC(kActIn) = 0.0;
+            else
                 atomicAdd(n_active, 1);
-            }
-        } else {
-            scal[2 * Sp + s] = 0.0;
         }
+        beta32[s] = beta;
     }
 }
 
@@ -328,21 +407,26 @@ __global__ void transform_kernel(const double *__restrict__ x, int32_t N, int32_
 
 int alloc_work(gmrf_ctx *g, int32_t Sp) {
     if (Sp <= g->cap_sp) return GMRF_OK;
-    double **v[5] = {&g->x, &g->r, &g->zv, &g->p, &g->q};
-    for (double **pp : v) {
-        if (*pp) cudaFree(*pp);
-        *pp = nullptr;
-    }
-    if (g->part) cudaFree(g->part);
-    if (g->scal) cudaFree(g->scal);
+    void *old[] = {g->b, g->x, g->r, g->d, g->ri, g->p, g->q, g->part, g->scal, g->scal32};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    g->b = g->x = g->r = nullptr;
+    g->d = g->ri = g->p = g->q = nullptr;
     g->part = g->scal = nullptr;
+    g->scal32 = nullptr;
     g->cap_sp = 0;
     const size_t n = (size_t)g->N * Sp;
-    for (double **pp : v)
+    double **v64[3] = {&g->b, &g->x, &g->r};
+    float **v32[4] = {&g->d, &g->ri, &g->p, &g->q};
+    for (double **pp : v64)
         if (cudaMalloc((void **)pp, 8 * n) != cudaSuccess)
             return fail(g, GMRF_ERR_ALLOC, "%zu bytes for a work vector", 8 * n);
+    for (float **pp : v32)
+        if (cudaMalloc((void **)pp, 4 * n) != cudaSuccess)
+            return fail(g, GMRF_ERR_ALLOC, "%zu bytes for a work vector", 4 * n);
     if (cudaMalloc((void **)&g->part, 8 * (size_t)2 * kMaxBlocks * Sp) != cudaSuccess ||
-        cudaMalloc((void **)&g->scal, 8 * (size_t)6 * Sp) != cudaSuccess)
+        cudaMalloc((void **)&g->scal, 8 * (size_t)(kScal + 1) * Sp) != cudaSuccess ||
+        cudaMalloc((void **)&g->scal32, 4 * (size_t)2 * Sp) != cudaSuccess)
         return fail(g, GMRF_ERR_ALLOC, "reduction buffers");
     g->cap_sp = Sp;
     if (g->graph) cudaGraphExecDestroy(g->graph);
@@ -351,22 +435,28 @@ int alloc_work(gmrf_ctx *g, int32_t Sp) {
     return GMRF_OK;
 }
 
-// One CG iteration (five launches) on g's stream.
-cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double rtol2) {
+// One inner (binary32) CG iteration: five launches on g's stream.
+cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double tol2) {
     const Geo o = geometry(g->N, Sp);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
     const size_t sm = sizeof(double2) * o.Qt * o.R;
     const int fin_blocks = (Sp + 7) / 8;
-    double *alpha = g->scal + 1 * (size_t)Sp, *beta = g->scal + 2 * (size_t)Sp;
-    spmv_dot_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val, g->p, g->q, g->N, Sp,
-                                                    o.tiles, g->part);
-    fin_alpha_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, g->scal, g->n_active);
-    update_kernel<<<grid, block, sm, g->stream>>>(g->minv, alpha, g->x, g->r, g->zv, g->p, g->q, g->N,
-                                                  Sp, o.tiles, g->part);
-    fin_beta_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, rtol2, g->scal, g->n_active);
+    float *alpha = g->scal32, *beta = g->scal32 + Sp;
+    spmv_dot_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val32, g->p, g->q, g->N, Sp, o.tiles,
+                                                    g->part);
+    fin_alpha_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, g->scal, alpha, g->n_active);
+    update_kernel<<<grid, block, sm, g->stream>>>(g->minv32, alpha, g->d, g->ri, g->p, g->q, g->N, Sp, o.tiles,
+                                                  g->part);
+    fin_beta_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, tol2, g->scal, beta, g->n_active);
     const int64_t n2 = (int64_t)g->N * Sp / 2;
-    pupdate_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, g->stream>>>(beta, g->zv, g->p, g->N, Sp);
+    pupdate_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, g->stream>>>(beta, g->minv32, g->ri, g->p, g->N, Sp);
     return cudaGetLastError();
+}
+
+int read_active(gmrf_ctx *g) {
+    CKG(cudaMemcpyAsync(g->h_active, g->n_active, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CKG(cudaStreamSynchronize(g->stream));
+    return GMRF_OK;
 }
 
 }  // namespace
@@ -464,11 +554,13 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
         }
         rowptr[i + 1] = (int32_t)col.size();
     }
-    std::vector<double> minv(N), sqrtc(N);
+    std::vector<float> minv32(N), val32(val.size());
+    std::vector<double> sqrtc(N);
     for (int32_t i = 0; i < N; i++) {
-        minv[i] = 1.0 / diag[i];
+        minv32[i] = (float)(1.0 / diag[i]);
         sqrtc[i] = std::sqrt(cl[i]);
     }
+    for (size_t k = 0; k < val.size(); k++) val32[k] = (float)val[k];
 
     g = new (std::nothrow) gmrf_ctx();
     if (!g) return fail(nullptr, GMRF_ERR_ALLOC, "context");
@@ -485,7 +577,8 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
     if (cudaMalloc((void **)&g->rowptr, 4 * (size_t)(N + 1)) != cudaSuccess ||
         cudaMalloc((void **)&g->col, 4 * (size_t)g->nnz) != cudaSuccess ||
         cudaMalloc((void **)&g->val, 8 * (size_t)g->nnz) != cudaSuccess ||
-        cudaMalloc((void **)&g->minv, 8 * (size_t)N) != cudaSuccess ||
+        cudaMalloc((void **)&g->val32, 4 * (size_t)g->nnz) != cudaSuccess ||
+        cudaMalloc((void **)&g->minv32, 4 * (size_t)N) != cudaSuccess ||
         cudaMalloc((void **)&g->sqrtc, 8 * (size_t)N) != cudaSuccess ||
         cudaMalloc((void **)&g->n_active, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&g->h_active, sizeof(int)) != cudaSuccess)
@@ -493,7 +586,8 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
     cudaError_t e = cudaMemcpyAsync(g->rowptr, rowptr.data(), 4 * (size_t)(N + 1), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->col, col.data(), 4 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->val, val.data(), 8 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->minv, minv.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->val32, val32.data(), 4 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->minv32, minv32.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->sqrtc, sqrtc.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return bail(fail(g, GMRF_ERR_CUDA, "copying the operator: %s", cudaGetErrorString(e)));
@@ -516,69 +610,95 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sca
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
     const size_t sm = sizeof(double2) * o.Qt * o.R;
     const int fin_blocks = (Sp + 7) / 8;
-    const double rtol2 = rtol * rtol;
+    const double tol = std::max(rtol, kInnerTol);
+    double *inv_scale = g->scal + (size_t)kScal * Sp;
+    // binary64 right-hand side and residual
     CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
-    init_kernel<<<grid, block, sm, g->stream>>>(z, S, Sp, g->N, o.tiles, g->sqrtc, g->minv, g->x, g->r,
-                                                g->zv, g->p, g->part);
-    fin_init_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, g->scal, g->n_active);
+    rhs_kernel<<<grid, block, sm, g->stream>>>(z, S, Sp, g->N, o.tiles, g->sqrtc, g->b, g->x, g->r, g->part);
+    fin_outer_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, rtol * rtol, 1, g->scal, inv_scale,
+                                                        g->n_active);
     CKG(cudaGetLastError());
-    CKG(cudaMemcpyAsync(g->h_active, g->n_active, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-    CKG(cudaStreamSynchronize(g->stream));
-    int iters = 0;
-    if (g->graph && (g->graph_sp != Sp || g->graph_rtol != rtol)) {
+    if ((rc = read_active(g)) != GMRF_OK) return rc;
+    if (g->graph && (g->graph_sp != Sp || g->graph_tol != tol)) {
         cudaGraphExecDestroy(g->graph);
         g->graph = nullptr;
     }
-    while (*g->h_active > 0 && iters < max_iter) {
-        const int k = std::min(kGraphIters, max_iter - iters);
-        if (k == kGraphIters) {
-            if (!g->graph) {
-                cudaStream_t cap;
-                CKG(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-                cudaStream_t keep = g->stream;
-                g->stream = cap;
-                cudaGraph_t gr = nullptr;
-                cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-                for (int it = 0; it < kGraphIters && e == cudaSuccess; it++) e = launch_iteration(g, Sp, rtol2);
-                cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
-                g->stream = keep;
-                cudaStreamDestroy(cap);
-                if (e == cudaSuccess) e = e2;
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, gr, 0);
-                if (gr) cudaGraphDestroy(gr);
-                if (e != cudaSuccess) {
-                    g->graph = nullptr;
-                    return fail(g, GMRF_ERR_CUDA, "iteration graph: %s", cudaGetErrorString(e));
+    int iters = 0, refinements = 0;
+    while (*g->h_active > 0 && iters < max_iter && refinements < kMaxRefinements) {
+        // inner binary32 solve of K d = r / ||r||
+        CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
+        inner_init_kernel<<<grid, block, sm, g->stream>>>(g->r, inv_scale, g->minv32, g->d, g->ri, g->p, g->N, Sp,
+                                                          o.tiles, g->part);
+        fin_inner_init_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, g->scal, g->n_active);
+        CKG(cudaGetLastError());
+        if ((rc = read_active(g)) != GMRF_OK) return rc;
+        while (*g->h_active > 0 && iters < max_iter) {
+            const int k = std::min(kGraphIters, max_iter - iters);
+            if (k == kGraphIters) {
+                if (!g->graph) {
+                    cudaStream_t cap;
+                    CKG(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+                    cudaStream_t keep = g->stream;
+                    g->stream = cap;
+                    cudaGraph_t gr = nullptr;
+                    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                    for (int it = 0; it < kGraphIters && e == cudaSuccess; it++) e = launch_iteration(g, Sp, tol * tol);
+                    cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
+                    g->stream = keep;
+                    cudaStreamDestroy(cap);
+                    if (e == cudaSuccess) e = e2;
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, gr, 0);
+                    if (gr) cudaGraphDestroy(gr);
+                    if (e != cudaSuccess) {
+                        g->graph = nullptr;
+                        return fail(g, GMRF_ERR_CUDA, "iteration graph: %s", cudaGetErrorString(e));
+                    }
+                    g->graph_sp = Sp;
+                    g->graph_tol = tol;
                 }
-                g->graph_sp = Sp;
-                g->graph_rtol = rtol;
+                CKG(cudaGraphLaunch(g->graph, g->stream));
+            } else {
+                for (int it = 0; it < k; it++) CKG(launch_iteration(g, Sp, tol * tol));
             }
-            CKG(cudaGraphLaunch(g->graph, g->stream));
-        } else {
-            for (int it = 0; it < k; it++) CKG(launch_iteration(g, Sp, rtol2));
+            iters += k;
+            if ((rc = read_active(g)) != GMRF_OK) return rc;
         }
-        iters += k;
-        CKG(cudaMemcpyAsync(g->h_active, g->n_active, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-        CKG(cudaStreamSynchronize(g->stream));
+        // binary64 correction and true residual
+        const int64_t n2 = (int64_t)g->N * Sp / 2;
+        correct_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, g->stream>>>(g->d, g->scal + (size_t)kScale * Sp, g->x,
+                                                                           g->N, Sp);
+        residual_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val, g->x, g->b, g->r, g->N, Sp,
+                                                        o.tiles, g->part);
+        CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
+        fin_outer_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, rtol * rtol, 0, g->scal, inv_scale,
+                                                            g->n_active);
+        CKG(cudaGetLastError());
+        refinements++;
+        if ((rc = read_active(g)) != GMRF_OK) return rc;
     }
     const int64_t n = (int64_t)g->N * S;
     transform_kernel<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(g->x, g->N, S, Sp, scale, mean,
                                                                          lognormal, out);
     CKG(cudaGetLastError());
-    std::vector<double> rel2(Sp);
-    CKG(cudaMemcpyAsync(rel2.data(), g->scal + 4 * (size_t)Sp, 8 * (size_t)Sp, cudaMemcpyDeviceToHost, g->stream));
+    std::vector<double> rr(Sp), bb(Sp);
+    CKG(cudaMemcpyAsync(rr.data(), g->scal + (size_t)kRr * Sp, 8 * (size_t)Sp, cudaMemcpyDeviceToHost, g->stream));
+    CKG(cudaMemcpyAsync(bb.data(), g->scal + (size_t)kBb * Sp, 8 * (size_t)Sp, cudaMemcpyDeviceToHost, g->stream));
     CKG(cudaStreamSynchronize(g->stream));
     double worst = 0.0;
-    for (int32_t s = 0; s < S; s++) worst = std::max(worst, std::sqrt(rel2[s]));
+    for (int32_t s = 0; s < S; s++)
+        if (bb[s] > 0.0) worst = std::max(worst, std::sqrt(rr[s] / bb[s]));
     g->info.iterations = iters;
+    g->info.refinements = refinements;
     g->info.max_relres = worst;
     g->info.last_S = S;
-    // per iteration: 12 passes over [N][Sp] binary64 vectors, the matrix (8 + 4 B per entry),
-    // row pointers and the diagonal preconditioner
-    g->info.bytes_per_iter = 12.0 * 8.0 * (double)g->N * Sp + 12.0 * (double)g->nnz + 12.0 * g->N;
+    // per inner iteration: 11 passes over binary32 [N][Sp] vectors, the binary32 matrix
+    // (4 + 4 B per entry), row pointers and the binary32 preconditioner
+    g->info.bytes_per_iter = 11.0 * 4.0 * (double)g->N * Sp + 8.0 * (double)g->nnz + 8.0 * g->N;
+    // per refinement: correction (x, d) and residual (x gathered, b, r) in binary64
+    g->info.bytes_per_refinement = (8.0 * 2 + 4.0 + 8.0 * 3) * (double)g->N * Sp + 12.0 * (double)g->nnz;
     if (*g->h_active > 0)
-        return fail(g, GMRF_ERR_NOT_CONVERGED, "%d samples above rtol after %d iterations (max relres %.3e)",
-                    *g->h_active, iters, worst);
+        return fail(g, GMRF_ERR_NOT_CONVERGED, "%d samples above rtol after %d iterations, %d refinements "
+                    "(max relres %.3e)", *g->h_active, iters, refinements, worst);
     return GMRF_OK;
 }
 
@@ -593,8 +713,8 @@ const char *gmrf_last_error(const gmrf_ctx *g) { return g ? g->err : g_create_er
 void gmrf_destroy(gmrf_ctx *g) {
     if (!g) return;
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void *dev[] = {g->rowptr, g->col, g->val, g->minv, g->sqrtc, g->x, g->r, g->zv, g->p, g->q,
-                   g->part, g->scal, g->n_active};
+    void *dev[] = {g->rowptr, g->col, g->val, g->val32, g->minv32, g->sqrtc, g->b, g->x, g->r, g->d, g->ri,
+                   g->p, g->q, g->part, g->scal, g->scal32, g->n_active};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (g->h_active) cudaFreeHost(g->h_active);

@@ -9,8 +9,8 @@ import math
 import numpy as np
 
 from .mesh import tube_mesh, aneurysm_mesh, tube_for_nodes, plate_mesh, single_triangle, arch_mesh
-from .fields import lognormal_fields
-from .loads import pressure_shear_modes, step_amplitudes, pulsatile_amplitudes, delayed_pressure
+from .fields import lognormal_fields, gaussian_fields
+from .loads import pressure_shear_modes, step_amplitudes, pulsatile_amplitudes, delayed_pressure, ramp
 
 RHO = 1060.0        # kg/m^3 (the paper's 1.06 is read as g/cm^3)
 NU = 0.5            # Poisson ratio
@@ -65,6 +65,13 @@ def make_case(name: str, S: int | None = None, n_steps: int | None = None, seed:
     tube_<n>k    : clamped straight tube with about n thousand nodes, step load.
     arch         : synthetic arch with three branches, travelling-wave pressure.
     small tests  : one_triangle, plate, tube_small (12 x 8 nodes).
+    cylinder     : the paper's ideal cylinder (Section 3.1): D = 4 cm, L = 30 cm, ends fully
+                   fixed, Gaussian marginals E = 0.7 +- 0.07 MPa and h = 4 +- 0.4 mm with
+                   correlation length corr (0.95, 3.7 or 7.2 cm), S = 100, mesh level 0 / 1 / 2
+                   with 5,074 / 15,136 / 32,994 triangles (level 3: 131,648, near the
+                   131,552 of the paper's Table 3); 13 mmHg plus the steady
+                   Poiseuille pressure drop and wall shear of 66.59 mL/s (mu = 4 mPa s),
+                   ramped in over 5 ms and held.
     """
     if name == "tube_40x40":
         return _case(tube_mesh(40, 40), S or 8, seed, n_steps or 2000, "step", **kw)
@@ -85,6 +92,30 @@ def make_case(name: str, S: int | None = None, n_steps: int | None = None, seed:
     if name.startswith("tube_") and name.endswith("k"):
         n = int(name[5:-1]) * 1000
         return _case(tube_for_nodes(n), S or 16, seed, n_steps or 1000, "step", **kw)
+    if name == "cylinder":
+        level = int(kw.pop("level", 2))
+        corr = float(kw.pop("corr", 0.037))
+        nc, na = [(43, 60), (88, 87), (117, 142), (176, 375)][level]
+        R, L = 0.02, 0.30
+        m = tube_mesh(nc, na, radius=R, length=L)
+        S = 100 if S is None else S
+        if kw.pop("host_fields", True):
+            E, h = gaussian_fields(m, S, 0.7e6, 0.07e6, 4.0e-3, 0.4e-3, corr, seed)
+            E_max = np.max(E)
+        else:   # fields drawn elsewhere (e.g. on the device); dt at mean + 6 std
+            E, h, E_max = None, None, 0.7e6 + 6 * 0.07e6
+        dt = kw.pop("dt", None) or cfl_dt(m, np.array([E_max]))
+        n = n_steps or 2000
+        mu, Q = 4.0e-3, 66.59e-6
+        p0 = 13.0 * 133.322387415                      # 13 mmHg in Pa
+        dp = 8.0 * mu * L * Q / (np.pi * R ** 4)       # Poiseuille pressure drop over L
+        tau = 4.0 * mu * Q / (np.pi * R ** 3)          # wall shear stress
+        zc = m.xyz[m.tri].mean(axis=1)[:, 2]
+        modes = pressure_shear_modes(m, delay_modes=[np.ones(m.n_elems), 1.0 - zc / L], with_shear=True)
+        r = ramp(dt * np.arange(n), 5.0e-3)
+        amp = np.ascontiguousarray(np.stack([r * p0, r * dp, r * tau], axis=1))
+        return dict(mesh=m, S=S, E=E, h=h, rho=RHO, nu=NU, kshear=KSHEAR, alpha=kw.pop("alpha", ALPHA),
+                    dt=dt, modes=modes, amp=amp, n_steps=n, seed=seed, corr=corr, pressure=p0)
     if name == "tube_small":
         return _case(tube_mesh(12, 8, length=0.03), S or 3, seed, n_steps or 200, "step", **kw)
     if name == "plate":

@@ -92,6 +92,15 @@ def lognormal_fields(mesh, n_samples: int, E_mean: float = 0.7e6, h_mean: float 
     return E_mean * np.exp(gE), h_mean * np.exp(gh)
 
 
+def gaussian_fields(mesh, n_samples: int, E_mean: float, E_std: float, h_mean: float, h_std: float,
+                    corr_length: float, seed: int = 0):
+    """Nodal E = E_mean + g_E, h = h_mean + g_h with independent Matern fields of marginal
+    standard deviations E_std and h_std (the Gaussian marginals of the paper's cylinder
+    benchmark). Returns (E, h), each [N][S] float64."""
+    gE, gh = gmrf_fields(mesh.xyz, mesh.tri, n_samples, corr_length, 1.0, seed, streams=(1, 2))
+    return E_mean + E_std * gE, h_mean + h_std * gh
+
+
 def matern_correlation(d, corr_length: float, nu: float = 1.0):
     """Matern correlation r(d)/sigma^2 = 2^(1-nu)/Gamma(nu) (kappa d)^nu K_nu(kappa d), Eq. 1."""
     d = np.asarray(d, dtype=np.float64)
