@@ -276,8 +276,11 @@ __device__ __forceinline__ double key_value(uint64_t k) {
 
 // Mean, sample variance and type-7 quantiles of every row; one warp per row, the row's
 // sort keys in this warp's P words of shared memory (P = power of two >= S).
+// inv_s = 1 / S, inv_s1 = 1 / (S - 1) (0 when S = 1) and s1 = S - 1 come from the host,
+// which keeps divisions and conversions off GB300's binary64 pipe.
 __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows, int32_t S, int32_t P,
-                                 int32_t n_q, const double *__restrict__ q, double *__restrict__ mean,
+                                 double inv_s, double inv_s1, double s1, int32_t n_q,
+                                 const double *__restrict__ q, double *__restrict__ mean,
                                  double *__restrict__ var, double *__restrict__ quant) {
     extern __shared__ uint64_t sm_keys[];
     const int lane = threadIdx.x & 31;
@@ -294,7 +297,7 @@ __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        const double mu = sum / (double)S;
+        const double mu = sum * inv_s;
         double ss = 0.0;
         for (int32_t i = lane; i < S; i += 32) {
             const double dlt = src[i] - mu;
@@ -304,7 +307,7 @@ __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) {
             if (mean) mean[row] = mu;
-            if (var) var[row] = S > 1 ? ss / (double)(S - 1) : 0.0;
+            if (var) var[row] = ss * inv_s1;
         }
         if (quant && n_q > 0) {
             __syncwarp();
@@ -323,7 +326,7 @@ __global__ void row_stats_kernel(const double *__restrict__ rows, int64_t n_rows
                     __syncwarp();
                 }
             for (int32_t k = lane; k < n_q; k += 32) {
-                const double h = __dmul_rn(q[k], (double)(S - 1));
+                const double h = __dmul_rn(q[k], s1);
                 int32_t j = (int32_t)floor(h);
                 if (j > S - 1) j = S - 1;
                 if (j < 0) j = 0;
@@ -366,7 +369,9 @@ cudaError_t launch_row_stats(const double *rows, int64_t n_rows, int32_t S, int3
         if (e != cudaSuccess) return e;
     }
     const int64_t blocks = std::min<int64_t>((n_rows + wpb - 1) / wpb, 152 * 16);
-    row_stats_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(rows, n_rows, S, P, n_q, q_dev, mean, var, quant);
+    const double inv_s = 1.0 / (double)S, inv_s1 = S > 1 ? 1.0 / (double)(S - 1) : 0.0;
+    row_stats_kernel<<<(unsigned)blocks, 32 * wpb, smem, s>>>(rows, n_rows, S, P, inv_s, inv_s1, (double)(S - 1),
+                                                              n_q, q_dev, mean, var, quant);
     return cudaGetLastError();
 }
 

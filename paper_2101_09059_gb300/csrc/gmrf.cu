@@ -17,7 +17,7 @@
 //   update     d += alpha p, r -= alpha q, partial sums of r.z and r.r with z = M^-1 r;
 //   fin_beta   beta_s, convergence test, active count;
 //   pupdate    p = M^-1 r + beta p.
-// Every reduction has a fixed shape (fixed grid, fixed tree), so results are bitwise
+// Every reduction has a fixed shape (a grid fixed per context, fixed trees), so results are bitwise
 // reproducible; a converged sample takes alpha = beta = 0 from then on, so stopping a
 // few iterations later changes nothing. Inner iterations run as replays of a graph.
 #include <cuda_runtime.h>
@@ -36,7 +36,7 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxBlocks = 1216;  // 152 SMs x 8: fixed reduction shape
+constexpr int kMaxBlocks = 4096;  // upper bound of the row kernels' grid (see gmrf_ctx::grid)
 constexpr int kGraphIters = 8;
 constexpr double kInnerTol = 1e-4;
 constexpr int kMaxRefinements = 16;
@@ -54,6 +54,15 @@ struct gmrf_ctx {
     int32_t *rowptr = nullptr, *col = nullptr;
     double *val = nullptr, *sqrtc = nullptr;
     float *val32 = nullptr, *minv32 = nullptr;
+    // padded-row (ELL) copy of the binary32 matrix: ell_w entries per row (8 or 16; 0 when
+    // some row is longer), padding entries (own column, value 0)
+    int32_t ell_w = 0;
+    // blocks of the row kernels: the device's SM count times the fewest blocks of 256
+    // threads any of them keeps resident, so each launch is one full wave; fixed per
+    // context (and so is every reduction shape)
+    int32_t grid = 0;
+    int32_t *ell_col = nullptr;
+    float *ell_val = nullptr;
     // work vectors, sized for cap_sp samples
     int32_t cap_sp = 0;
     double *b = nullptr, *x = nullptr, *r = nullptr;       // binary64 [N][Sp]
@@ -99,13 +108,13 @@ struct Geo {
     int64_t tiles;
 };
 
-Geo geometry(int32_t N, int32_t Sp) {
+Geo geometry(int32_t N, int32_t Sp, int32_t grid) {
     Geo o;
     o.Q = Sp / 2;
     o.Qt = std::min(o.Q, kThreads);
     o.R = std::max(1, kThreads / o.Qt);
     o.tiles = ((int64_t)N + o.R - 1) / o.R;
-    o.G = (int)std::min<int64_t>(o.tiles, kMaxBlocks);
+    o.G = (int)std::min<int64_t>(o.tiles, grid);
     o.chunks = (o.Q + o.Qt - 1) / o.Qt;
     return o;
 }
@@ -274,6 +283,48 @@ __global__ void spmv_dot_kernel(const int32_t *__restrict__ rowptr, const int32_
     block_partial(widen(pq), sm, part, 0, gridDim.x, Sp, lane_q);
 }
 
+// The same product from the padded rows: the column indices and values of a row are
+// WP / 4 vector loads that do not wait for the row pointers, so a row costs two dependent
+// round trips (indices, then the WP gathers).
+template <int WP>
+__global__ void spmv_ell_kernel(const int32_t *__restrict__ ell_col, const float *__restrict__ ell_val,
+                                const float *__restrict__ p, float *__restrict__ q, int32_t N, int32_t Sp,
+                                int64_t tiles, double *part) {
+    extern __shared__ double2 sm[];
+    float2 pq = make_float2(0.f, 0.f);
+    ROW_LOOP
+        int32_t cj[WP];
+        float aj[WP];
+        const int4 *cc = reinterpret_cast<const int4 *>(ell_col + (size_t)i * WP);
+        const float4 *vv = reinterpret_cast<const float4 *>(ell_val + (size_t)i * WP);
+#pragma unroll
+        for (int u = 0; u < WP / 4; u++) {
+            const int4 c = __ldg(cc + u);
+            const float4 v = __ldg(vv + u);
+            cj[4 * u] = c.x;
+            cj[4 * u + 1] = c.y;
+            cj[4 * u + 2] = c.z;
+            cj[4 * u + 3] = c.w;
+            aj[4 * u] = v.x;
+            aj[4 * u + 1] = v.y;
+            aj[4 * u + 2] = v.z;
+            aj[4 * u + 3] = v.w;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < WP; u++) {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(p + (size_t)cj[u] * Sp + s0));
+            acc.x = fmaf(aj[u], v.x, acc.x);
+            acc.y = fmaf(aj[u], v.y, acc.y);
+        }
+        stf2(q + o, acc);
+        const float2 pv = ldf2(p + o);
+        pq.x = fmaf(pv.x, acc.x, pq.x);
+        pq.y = fmaf(pv.y, acc.y, pq.y);
+    }
+    block_partial(widen(pq), sm, part, 0, gridDim.x, Sp, lane_q);
+}
+
 // d += alpha p, r -= alpha q; partials of r.z (z = M^-1 r) and r.r.
 __global__ void update_kernel(const float *__restrict__ minv, const float *__restrict__ alpha, float *d,
                               float *ri, const float *__restrict__ p, const float *__restrict__ q, int32_t N,
@@ -316,21 +367,28 @@ __global__ void pupdate_kernel(const float *__restrict__ beta, const float *__re
     stf2(p + 2 * t, pv);
 }
 
-// Sum of part[w][s][0..G) by one warp per sample: fixed lane assignment, fixed tree.
-__device__ __forceinline__ double warp_total(const double *part, int w, int G, int32_t Sp, int s) {
-    const int lane = threadIdx.x & 31;
+// Sum of part[w][s][0..G) by the block of sample s (blockIdx.x = s): fixed strided
+// assignment to the threads, then a fixed pairwise tree.
+constexpr int kFinThreads = 128;
+__device__ __forceinline__ double block_total(const double *part, int w, int G, int32_t Sp, int s) {
+    __shared__ double red[kFinThreads];
     const double *src = part + ((size_t)w * Sp + s) * G;
     double a = 0.0;
-    for (int b = lane; b < G; b += 32) a += src[b];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    return a;
+    for (int b = threadIdx.x; b < G; b += kFinThreads) a += src[b];
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int st = kFinThreads / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    const double t = red[0];
+    __syncthreads();
+    return t;
 }
 
-#define FIN_SAMPLE                                                     \
-    const int s = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   \
-    if (s >= Sp) return;                                               \
-    const bool lead = (threadIdx.x & 31) == 0;
+#define FIN_SAMPLE                            \
+    const int s = blockIdx.x;                  \
+    const bool lead = threadIdx.x == 0;
 #define SC(row) scal[(size_t)(row) * Sp + s]
 
 // Outer test after a residual: rr = ||r||^2 (first: also ||b||^2); a sample stays active
@@ -338,7 +396,7 @@ __device__ __forceinline__ double warp_total(const double *part, int w, int G, i
 __global__ void fin_outer_kernel(const double *part, int G, int32_t Sp, double rtol2, int first, double *scal,
                                  double *inv_scale, int *n_active) {
     FIN_SAMPLE
-    const double rr = warp_total(part, 0, G, Sp, s);
+    const double rr = block_total(part, 0, G, Sp, s);
     if (lead) {
         if (first) SC(kBb) = rr;
         const double bb = SC(kBb);
@@ -353,8 +411,8 @@ __global__ void fin_outer_kernel(const double *part, int G, int32_t Sp, double r
 
 __global__ void fin_inner_init_kernel(const double *part, int G, int32_t Sp, double *scal, int *n_active) {
     FIN_SAMPLE
-    const double rz = warp_total(part, 0, G, Sp, s);
-    const double bb = warp_total(part, 1, G, Sp, s);
+    const double rz = block_total(part, 0, G, Sp, s);
+    const double bb = block_total(part, 1, G, Sp, s);
     if (lead) {
         const bool act = bb > 0.0;
         SC(kRz) = rz;
@@ -366,9 +424,9 @@ __global__ void fin_inner_init_kernel(const double *part, int G, int32_t Sp, dou
 
 __global__ void fin_alpha_kernel(const double *part, int G, int32_t Sp, double *scal, float *alpha32,
                                  int *n_active) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_active = 0;
     FIN_SAMPLE
-    const double pq = warp_total(part, 0, G, Sp, s);
+    if (s == 0 && lead) *n_active = 0;
+    const double pq = block_total(part, 0, G, Sp, s);
     if (lead) {
         const bool act = SC(kActIn) != 0.0;
         alpha32[s] = (act && pq > 0.0) ? ens::f64_to_f32_rz(SC(kRz) / pq) : 0.f;
@@ -378,8 +436,8 @@ __global__ void fin_alpha_kernel(const double *part, int G, int32_t Sp, double *
 __global__ void fin_beta_kernel(const double *part, int G, int32_t Sp, double tol2, double *scal, float *beta32,
                                 int *n_active) {
     FIN_SAMPLE
-    const double rz = warp_total(part, 0, G, Sp, s);
-    const double rr = warp_total(part, 1, G, Sp, s);
+    const double rz = block_total(part, 0, G, Sp, s);
+    const double rr = block_total(part, 1, G, Sp, s);
     if (lead) {
         float beta = 0.f;
         if (SC(kActIn) != 0.0) {
@@ -437,17 +495,23 @@ int alloc_work(gmrf_ctx *g, int32_t Sp) {
 
 // One inner (binary32) CG iteration: five launches on g's stream.
 cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double tol2) {
-    const Geo o = geometry(g->N, Sp);
+    const Geo o = geometry(g->N, Sp, g->grid);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
     const size_t sm = sizeof(double2) * o.Qt * o.R;
-    const int fin_blocks = (Sp + 7) / 8;
     float *alpha = g->scal32, *beta = g->scal32 + Sp;
-    spmv_dot_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val32, g->p, g->q, g->N, Sp, o.tiles,
-                                                    g->part);
-    fin_alpha_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, g->scal, alpha, g->n_active);
+    if (g->ell_w == 8)
+        spmv_ell_kernel<8><<<grid, block, sm, g->stream>>>(g->ell_col, g->ell_val, g->p, g->q, g->N, Sp, o.tiles,
+                                                           g->part);
+    else if (g->ell_w == 16)
+        spmv_ell_kernel<16><<<grid, block, sm, g->stream>>>(g->ell_col, g->ell_val, g->p, g->q, g->N, Sp, o.tiles,
+                                                            g->part);
+    else
+        spmv_dot_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val32, g->p, g->q, g->N, Sp, o.tiles,
+                                                        g->part);
+    fin_alpha_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, g->scal, alpha, g->n_active);
     update_kernel<<<grid, block, sm, g->stream>>>(g->minv32, alpha, g->d, g->ri, g->p, g->q, g->N, Sp, o.tiles,
                                                   g->part);
-    fin_beta_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, tol2, g->scal, beta, g->n_active);
+    fin_beta_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, tol2, g->scal, beta, g->n_active);
     const int64_t n2 = (int64_t)g->N * Sp / 2;
     pupdate_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, g->stream>>>(beta, g->minv32, g->ri, g->p, g->N, Sp);
     return cudaGetLastError();
@@ -561,11 +625,24 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
         sqrtc[i] = std::sqrt(cl[i]);
     }
     for (size_t k = 0; k < val.size(); k++) val32[k] = (float)val[k];
+    int32_t wmax = 0;
+    for (int32_t i = 0; i < N; i++) wmax = std::max(wmax, rowptr[i + 1] - rowptr[i]);
+    const int32_t ell_w = wmax <= 8 ? 8 : (wmax <= 16 ? 16 : 0);
+    std::vector<int32_t> ell_col((size_t)N * std::max(ell_w, 1));
+    std::vector<float> ell_val((size_t)N * std::max(ell_w, 1));
+    for (int32_t i = 0; ell_w > 0 && i < N; i++)
+        for (int32_t u = 0; u < ell_w; u++) {
+            const int32_t k = rowptr[i] + u;
+            const bool ok = k < rowptr[i + 1];
+            ell_col[(size_t)i * ell_w + u] = ok ? col[k] : i;
+            ell_val[(size_t)i * ell_w + u] = ok ? val32[k] : 0.f;
+        }
 
     g = new (std::nothrow) gmrf_ctx();
     if (!g) return fail(nullptr, GMRF_ERR_ALLOC, "context");
     g->N = N;
     g->nnz = (int64_t)col.size();
+    g->ell_w = ell_w;
     g->kappa = kappa;
     g->stream = (cudaStream_t)stream;
     cudaGetDevice(&g->device);
@@ -579,6 +656,8 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
         cudaMalloc((void **)&g->val, 8 * (size_t)g->nnz) != cudaSuccess ||
         cudaMalloc((void **)&g->val32, 4 * (size_t)g->nnz) != cudaSuccess ||
         cudaMalloc((void **)&g->minv32, 4 * (size_t)N) != cudaSuccess ||
+        cudaMalloc((void **)&g->ell_col, 4 * ell_col.size()) != cudaSuccess ||
+        cudaMalloc((void **)&g->ell_val, 4 * ell_val.size()) != cudaSuccess ||
         cudaMalloc((void **)&g->sqrtc, 8 * (size_t)N) != cudaSuccess ||
         cudaMalloc((void **)&g->n_active, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&g->h_active, sizeof(int)) != cudaSuccess)
@@ -588,9 +667,24 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->val, val.data(), 8 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->val32, val32.data(), 4 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->minv32, minv32.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->ell_col, ell_col.data(), 4 * ell_col.size(), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->ell_val, ell_val.data(), 4 * ell_val.size(), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->sqrtc, sqrtc.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return bail(fail(g, GMRF_ERR_CUDA, "copying the operator: %s", cudaGetErrorString(e)));
+    {
+        int sms = 0, per = 0, least = 1 << 20;
+        const size_t smb = sizeof(double2) * kThreads;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const void *fns[] = {(const void *)spmv_ell_kernel<8>, (const void *)spmv_ell_kernel<16>,
+                             (const void *)spmv_dot_kernel, (const void *)update_kernel, (const void *)inner_init_kernel,
+                             (const void *)residual_kernel, (const void *)rhs_kernel};
+        for (const void *f : fns)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, kThreads, smb) == cudaSuccess && per > 0)
+                least = std::min(least, per);
+        if (sms <= 0 || least == (1 << 20)) return bail(fail(g, GMRF_ERR_CUDA, "occupancy query failed"));
+        g->grid = std::min(kMaxBlocks, sms * least);
+    }
     g->info.n_nodes = N;
     g->info.nnz = g->nnz;
     *out = g;
@@ -606,16 +700,15 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sca
     const int32_t Sp = (S + 1) / 2 * 2;
     int rc = alloc_work(g, Sp);
     if (rc != GMRF_OK) return rc;
-    const Geo o = geometry(g->N, Sp);
+    const Geo o = geometry(g->N, Sp, g->grid);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
     const size_t sm = sizeof(double2) * o.Qt * o.R;
-    const int fin_blocks = (Sp + 7) / 8;
     const double tol = std::max(rtol, kInnerTol);
     double *inv_scale = g->scal + (size_t)kScal * Sp;
     // binary64 right-hand side and residual
     CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
     rhs_kernel<<<grid, block, sm, g->stream>>>(z, S, Sp, g->N, o.tiles, g->sqrtc, g->b, g->x, g->r, g->part);
-    fin_outer_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, rtol * rtol, 1, g->scal, inv_scale,
+    fin_outer_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, rtol * rtol, 1, g->scal, inv_scale,
                                                         g->n_active);
     CKG(cudaGetLastError());
     if ((rc = read_active(g)) != GMRF_OK) return rc;
@@ -629,7 +722,7 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sca
         CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
         inner_init_kernel<<<grid, block, sm, g->stream>>>(g->r, inv_scale, g->minv32, g->d, g->ri, g->p, g->N, Sp,
                                                           o.tiles, g->part);
-        fin_inner_init_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, g->scal, g->n_active);
+        fin_inner_init_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, g->scal, g->n_active);
         CKG(cudaGetLastError());
         if ((rc = read_active(g)) != GMRF_OK) return rc;
         while (*g->h_active > 0 && iters < max_iter) {
@@ -670,7 +763,7 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sca
         residual_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val, g->x, g->b, g->r, g->N, Sp,
                                                         o.tiles, g->part);
         CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
-        fin_outer_kernel<<<fin_blocks, 256, 0, g->stream>>>(g->part, o.G, Sp, rtol * rtol, 0, g->scal, inv_scale,
+        fin_outer_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, rtol * rtol, 0, g->scal, inv_scale,
                                                             g->n_active);
         CKG(cudaGetLastError());
         refinements++;
@@ -693,7 +786,7 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sca
     g->info.last_S = S;
     // per inner iteration: 11 passes over binary32 [N][Sp] vectors, the binary32 matrix
     // (4 + 4 B per entry), row pointers and the binary32 preconditioner
-    g->info.bytes_per_iter = 11.0 * 4.0 * (double)g->N * Sp + 8.0 * (double)g->nnz + 8.0 * g->N;
+    g->info.bytes_per_iter = 11.0 * 4.0 * (double)g->N * Sp + 8.0 * (double)g->nnz + 8.0 * g->N;  // stored entries only
     // per refinement: correction (x, d) and residual (x gathered, b, r) in binary64
     g->info.bytes_per_refinement = (8.0 * 2 + 4.0 + 8.0 * 3) * (double)g->N * Sp + 12.0 * (double)g->nnz;
     if (*g->h_active > 0)
@@ -713,7 +806,7 @@ const char *gmrf_last_error(const gmrf_ctx *g) { return g ? g->err : g_create_er
 void gmrf_destroy(gmrf_ctx *g) {
     if (!g) return;
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void *dev[] = {g->rowptr, g->col, g->val, g->val32, g->minv32, g->sqrtc, g->b, g->x, g->r, g->d, g->ri,
+    void *dev[] = {g->rowptr, g->col, g->val, g->val32, g->minv32, g->ell_col, g->ell_val, g->sqrtc, g->b, g->x, g->r, g->d, g->ri,
                    g->p, g->q, g->part, g->scal, g->scal32, g->n_active};
     for (void *p : dev)
         if (p) cudaFree(p);

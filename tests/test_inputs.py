@@ -76,3 +76,33 @@ def test_cfl_rule_matches_paper_example():
     dt = synth.cfl_dt(m, np.array([g["E_pa"]]), rho=g["rho_printed"], safety=1.0)
     assert dt == pytest.approx(g["dt_printed_s"], rel=0.05)
     assert g["safety"] * dt == pytest.approx(g["dt_after_safety_printed_s"], rel=0.15)
+
+
+def test_cylinder_workload_follows_section_3_1():
+    """The paper's cylinder: D = 4 cm, L = 30 cm, the three mesh densities' triangle counts,
+    Gaussian fields with the stated means and standard deviations, 13 mmHg plus the steady
+    Poiseuille load (pressure drop 8 mu L Q / (pi R^4), wall shear 4 mu Q / (pi R^3))."""
+    import numpy as np
+    import synth
+    for level, n_tri in ((0, 5074), (1, 15136), (2, 32994)):
+        c = synth.make_case("cylinder", level=level, S=2, n_steps=3, host_fields=False)
+        m = c["mesh"]
+        assert m.n_elems == n_tri
+        r = np.hypot(m.xyz[:, 0], m.xyz[:, 1])
+        assert np.allclose(r, 0.02) and m.xyz[:, 2].min() == 0.0 and np.isclose(m.xyz[:, 2].max(), 0.30)
+    c = synth.make_case("cylinder", level=0, S=400, corr=0.0095, n_steps=20000, seed=5)
+    E, h = c["E"], c["h"]
+    assert abs(E.mean() / 0.7e6 - 1) < 0.02 and abs(E.std() / 0.07e6 - 1) < 0.15
+    assert abs(h.mean() / 4e-3 - 1) < 0.02 and abs(h.std() / 0.4e-3 - 1) < 0.15
+    mu, Q, R, L = 4e-3, 66.59e-6, 0.02, 0.30
+    amp = c["amp"][-1]                                   # after the ramp
+    assert np.isclose(amp[0], 13 * 133.322387415)
+    assert np.isclose(amp[1], 8 * mu * L * Q / (np.pi * R ** 4))
+    assert np.isclose(amp[2], 4 * mu * Q / (np.pi * R ** 3))
+    # pattern 1 carries the linear drop: total force of the pressure patterns is radial
+    # (zero resultant), and pattern 1 weighs the inlet end more than the outlet end
+    P1 = c["modes"][1]
+    m = c["mesh"]
+    inlet = m.xyz[:, 2] < 0.05
+    outlet = m.xyz[:, 2] > 0.25
+    assert np.linalg.norm(P1[inlet], axis=1).mean() > 3 * np.linalg.norm(P1[outlet], axis=1).mean()
