@@ -209,9 +209,33 @@ StagePlan pipelined_plan(StagePlan p) {
     return p;
 }
 
+constexpr int kTuneSteps = 8;  // even: a replay leaves the ping-pong parity unchanged
+constexpr int kTuneReps = 3;
+
+// Capture n step launches (steps k = 0 .. n-1 of a chunk from the current buffer, the
+// context's current plan) into an executable graph.
+int capture_steps(ens_ctx *c, int n, cudaGraphExec_t *out) {
+    *out = nullptr;
+    if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n && e == cudaSuccess; k++) e = launch_chunk_step(c, k, false, c->cap);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return fail(c, ENS_ERR_CUDA, "step graph capture: %s [%s]", cudaGetErrorString(e), last_launch_note());
+    }
+    return ENS_OK;
+}
+
 // Launch-shape autotuner: time a few steps of every candidate shape on this context's
 // own mesh and coefficients, with the state filled with small non-zero values, and keep
 // the fastest; the state is zeroed again afterwards. Candidate 0 is the unstaged kernel.
+// The timing replays captured step graphs, as ens_step does.
 int autotune(ens_ctx *c, const StagePlan *cand, int n) {
     // time on non-zero data (zeros take shortcuts in some arithmetic); reset afterwards
     const int64_t ns = (int64_t)c->N * 3 * c->Sp;
@@ -238,19 +262,24 @@ int autotune(ens_ctx *c, const StagePlan *cand, int n) {
             continue;
         }
         c->plan = cand[k];
-        rc = run_steps(c, 2);
+        // time the shape the way ens_step runs it: replays of a captured graph of
+        // kTuneSteps step launches (one warm-up replay, then kTuneReps timed)
+        cudaGraphExec_t ge = nullptr;
+        rc = capture_steps(c, kTuneSteps, &ge);
         if (rc != ENS_OK) break;
-        cudaEventRecord(e0, c->stream);
-        rc = run_steps(c, 6);
-        if (rc != ENS_OK) break;
-        cudaEventRecord(e1, c->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = fail(c, ENS_ERR_CUDA, "autotune timing");
+        cudaError_t ce = cudaGraphLaunch(ge, c->stream);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < kTuneReps && ce == cudaSuccess; r++) ce = cudaGraphLaunch(ge, c->stream);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, c->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        cudaGraphExecDestroy(ge);
+        if (ce != cudaSuccess) {
+            rc = fail(c, ENS_ERR_CUDA, "autotune timing: %s [%s]", cudaGetErrorString(ce), last_launch_note());
             break;
         }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        c->variant_us[k] = 1000.0f * ms / 6.0f;
+        c->variant_us[k] = 1000.0f * ms / (float)(kTuneSteps * kTuneReps);
         if (best < 0 || ms < best_ms) {
             best = k;
             best_ms = ms;
