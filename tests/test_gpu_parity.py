@@ -244,6 +244,29 @@ def test_full_size_aneurysm_sampled_parity():
         e.close()
 
 
+def test_full_size_arch_sampled_parity():
+    """The synthetic arch with three branches at its full size (about 500k triangles) and
+    S = 256, travelling-wave pressure, compensated FP32 and binary64 forms: realisations are
+    independent, so the device runs 256 samples whose first two carry host-drawn fields and
+    the rest repeat them, and the oracle runs those two, compared after 100 steps."""
+    case = synth.make_case("arch", S=2, seed=1)
+    n = 100
+    case["amp"] = np.ascontiguousarray(case["amp"][: n + 1])
+    case["n_steps"] = n + 1
+    ref = _oracle_run(case, n)
+    full = dict(case, E=np.tile(case["E"], (1, 128)), h=np.tile(case["h"], (1, 128)), S=256)
+    assert full["mesh"].n_elems > 450_000
+    for precision in ("kahan32", "fp64"):
+        e = ens.Ensemble.from_case(full, precision=precision)
+        e.step(n)
+        u = e.displacement()
+        for s in (0, 1, 254, 255):
+            err = rel_l2(u[s], ref[s % 2])
+            print(f"arch {precision} sample {s}: rel-L2 {err:.3e}")
+            assert err < TOL[precision]
+        e.close()
+
+
 def test_streamed_amplitudes_equal_full_table():
     case = synth.make_case("tube_small", S=3, n_steps=60)
     full = ens.Ensemble.from_case(case, precision="fp32_force")
