@@ -115,3 +115,27 @@ def test_field_sampler_create_rejects_bad_input(L, case):
     assert L.gmrf_last_error(None).decode()
     if case != "no_out":
         assert out.value is None
+
+
+@pytest.mark.parametrize("case", ["S0", "S_big", "nq_big", "q_range", "q_nan", "rows_null", "quant_null"])
+def test_row_stats_rejects_bad_arguments_before_device_work(L, case):
+    n_rows, S, n_q = 4, 8, 2
+    q = np.array([0.05, 0.95])
+    rows = ctypes.c_void_p(0x1000)       # never dereferenced: the checks come first
+    quant = ctypes.c_void_p(0x2000)
+    if case == "S0":
+        S = 0
+    elif case == "S_big":
+        S = 16385
+    elif case == "nq_big":
+        n_q, q = 1025, np.full(1025, 0.5)
+    elif case == "q_range":
+        q = np.array([0.05, 1.5])
+    elif case == "q_nan":
+        q = np.array([float("nan"), 0.5])
+    elif case == "rows_null":
+        rows = None
+    elif case == "quant_null":
+        quant = None
+    rc = L.ens_row_stats_device(n_rows, S, rows, n_q, ctypes.c_void_p(q.ctypes.data), None, None, quant, None)
+    assert rc == -1

@@ -53,3 +53,32 @@ def test_adam_first_step_is_lr_times_sign():
     opt = mlp.Adam(params, lr=0.01, eps=1e-12)
     opt.step(params, grads)
     assert np.allclose(params[0] - before, -0.01 * np.sign(grads[0]), rtol=1e-9, atol=0)
+
+
+def test_forward_reduces_to_the_affine_map_when_gelu_is_linear():
+    """With every pre-activation far above zero, GELU(z) = z up to z * Phi(-z) < 1e-20, so
+    the network is the product of its affine maps (a closed form of the layer order and
+    the (out, in) weight convention)."""
+    rng = np.random.default_rng(5)
+    sizes = [4, 6, 5, 3]
+    W1 = rng.uniform(0.5, 1.0, (6, 4))
+    W2 = rng.uniform(0.5, 1.0, (5, 6))
+    W3 = rng.standard_normal((3, 5))
+    b1, b2, b3 = np.full(6, 20.0), np.full(5, 20.0), rng.standard_normal(3)
+    x = rng.uniform(0.0, 1.0, (7, 4))
+    y, _ = mlp.forward([W1, b1, W2, b2, W3, b3], x)
+    ref = ((x @ W1.T + b1) @ W2.T + b2) @ W3.T + b3
+    assert np.allclose(y, ref, rtol=1e-13, atol=0)
+
+
+def test_hidden_unit_permutation_and_loss_definition():
+    rng = np.random.default_rng(6)
+    params = mlp.init_params([5, 8, 8, 2], seed=4)
+    x = rng.standard_normal((9, 5))
+    y, _ = mlp.forward(params, x)
+    p1, p2 = rng.permutation(8), rng.permutation(8)
+    W1, b1, W2, b2, W3, b3 = params
+    perm = [W1[p1], b1[p1], W2[p2][:, p1], b2[p2], W3[:, p2], b3]
+    assert np.allclose(mlp.forward(perm, x)[0], y, rtol=1e-14, atol=1e-15)
+    t = y + 0.5                       # every residual is -0.5
+    assert mlp.loss(params, x, t) == pytest.approx(0.25, rel=1e-14)
