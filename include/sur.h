@@ -7,8 +7,10 @@
  * truncated Karhunen-Loeve coefficients of the realisation's E and h fields to POD
  * coefficients of a displacement field the solver produced. Training minimises the mean
  * squared error with Adam (beta1 = 0.9, beta2 = 0.999, eps = 1e-8). Matrix products run
- * on the tensor cores in BF16 with FP32 accumulation; parameters, activations, gradients
- * and optimiser state are FP32.
+ * on the fifth-generation tensor cores (tcgen05, accumulator in tensor memory) in BF16
+ * with FP32 accumulation; parameters, activations, gradients and optimiser state are FP32.
+ * The products wait for the tensor cores with bounded waits; one that gives up is reported
+ * as SUR_ERR_CUDA by the next call that synchronises (sur_loss_grad, sur_loss, sur_train).
  *
  * Conventions: every call returns SUR_OK (0) or a negative SUR_ERR_* code and
  * sur_last_error gives the message. Arrays with the suffix _dev are device pointers

@@ -1,8 +1,9 @@
 // Surrogate network on the GPU: a GELU multilayer perceptron (n_in -> H -> H -> n_out)
 // trained with mean-squared error and Adam, every step in this file's kernels.
 //
-// Matrix products run on the tensor cores in BF16 with FP32 accumulation (warp-level
-// mma m16n8k16); master weights, activations, gradients and optimiser state stay FP32.
+// Matrix products run on the fifth-generation tensor cores in BF16 with FP32 accumulation
+// (tcgen05.mma, the accumulator in tensor memory); master weights, activations, gradients
+// and optimiser state stay FP32.
 // One training epoch (gather of each shuffled mini-batch, forward, loss, backward, Adam)
 // is captured once in a CUDA graph and replayed.
 #include <algorithm>
@@ -19,12 +20,30 @@
 #include <cuda_runtime.h>
 
 #include "../../include/sur.h"
+#include "ens_bits.cuh"
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32;  // block tile
-constexpr int LDS = BK + 8;                // padded smem row (bf16 elements)
-constexpr int kThreads = 128;              // 4 warps, 2 x 2, each 32 x 32
+// ---- tensor-core product (tcgen05) ----------------------------------------------------
+// One CTA of 128 threads computes a 128 x 32 tile of C (the network's products are a few
+// tiles wide, so narrow tiles give more CTAs). Per K stage of 32 the threads stage
+// the FP32 operands as BF16 into shared memory in the canonical K-major layout without
+// swizzle: 8 x 16-byte core matrices (8 rows of 8 consecutive k), the four k-groups of a
+// row group 128 bytes apart (leading byte offset) and row groups 512 bytes apart (stride
+// byte offset). One thread then issues two tcgen05.mma (M = 128, N = 32, K = 16) into the
+// CTA's 32 tensor-memory columns and commits them to an mbarrier that every thread waits
+// on (bounded) before the stage is overwritten. At the end warp w reads rows 32w .. 32w+31
+// of the accumulator with tcgen05.ld and applies the epilogue.
+constexpr int TM = 128, TN = 32, TK = 32;
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 32;
+constexpr uint32_t kCoreK = 128;   // bytes between core matrices along k
+constexpr uint32_t kCoreMN = 512;  // bytes between 8-row groups
+constexpr uint32_t kAsBytes = TM / 8 * kCoreMN, kBsBytes = TN / 8 * kCoreMN;
+// dynamic shared memory per CTA: at most 8 CTAs fit on an SM, so their 8 x 32 columns
+// never exceed the SM's 512 columns of tensor memory and tcgen05.alloc never waits
+constexpr uint32_t kTcSmem = 28 * 1024;
+constexpr uint32_t kTcWait = 1u << 22;
 
 enum Epi : int {
     kStore = 0,      // C = acc
@@ -33,18 +52,47 @@ enum Epi : int {
     kGeluGrad = 3,   // C = acc * gelu'(Z[m][n])
 };
 
+// Set when a bounded wait for the tensor cores gave up (read back by the host calls).
+__device__ int g_tc_fault;
+
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
            z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+// Shared-memory matrix descriptor: start address, leading and stride byte offsets (all
+// >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = ens::smem_addr(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major,
+// N = TN, M = TM.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 accumulator columns of this thread's row.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// byte offset of element (row r, k) inside a staged operand tile
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+    return (uint32_t)(r >> 3) * kCoreMN + (uint32_t)(k >> 3) * kCoreK + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
 // C[M][N] (row stride ldc) = epilogue( sum_k A(m, k) B(k, n) ), FP32 sources staged to BF16.
@@ -57,82 +105,128 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
                                                         long long sbn, float *__restrict__ C, int ldc,
                                                         const float *__restrict__ bias,
                                                         float *__restrict__ Z) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][LDS];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][LDS];
+    extern __shared__ __align__(128) unsigned char tsm[];
+    unsigned char *As = tsm, *Bs = tsm + kAsBytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tsm + kAsBytes + kBsBytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tsm + kAsBytes + kBsBytes + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) acc[i][j][r] = 0.0f;
-
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // stage A tile (BM x BK) and B tile (BN x BK), walking the contiguous index fastest
-        for (int e = tid; e < BM * BK; e += kThreads) {
-            int mm, kk;
-            if (sak == 1) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
-            const int m = m0 + mm, k = k0 + kk;
-            const float v = (m < M && k < K) ? A[(long long)m * sam + (long long)k * sak] : 0.0f;
-            As[mm][kk] = __float2bfloat16_rn(v);
-        }
-        for (int e = tid; e < BN * BK; e += kThreads) {
-            int nn, kk;
-            if (sbk == 1) { nn = e / BK; kk = e % BK; } else { nn = e % BN; kk = e / BN; }
-            const int n = n0 + nn, k = k0 + kk;
-            const float v = (n < N && k < K) ? B[(long long)k * sbk + (long long)n * sbn] : 0.0f;
-            Bs[nn][kk] = __float2bfloat16_rn(v);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < BK; ks += 16) {
-            uint32_t af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int r = wm + 16 * i;
-                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r + g][ks + 2 * t]);
-                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + g + 8][ks + 2 * t]);
-                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r + g][ks + 2 * t + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + g + 8][ks + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int c = wn + 8 * j;
-                bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c + g][ks + 2 * t]);
-                bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c + g][ks + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bf[j]);
-        }
-        __syncthreads();
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ens::smem_addr(tslot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // epilogue: acc[i][j] = {C[g][2t], C[g][2t+1], C[g+8][2t], C[g+8][2t+1]} of its 16 x 8 tile
+    if (tid == 0) {
+        ens::mbar_init(bar, 1);
+        ens::fence_barrier_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int k0 = 0; k0 < K && ok; k0 += TK) {
+        // loads in groups of 8 (issued together), then their conversions and shared stores
+        constexpr int kA = TM * TK / kThreads, kB = TN * TK / kThreads, kG = 8;
+#pragma unroll 1
+        for (int j0 = 0; j0 < kA; j0 += kG) {
+            float v[kG];
 #pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int m = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + 8 * j + 2 * t + (r & 1);
-                if (m >= M || n >= N) continue;
-                float v = acc[i][j][r];
-                const long long o = (long long)m * ldc + n;
-                if constexpr (EPI == kBiasStore) v += bias[n];
-                if constexpr (EPI == kBiasGelu) {
-                    v += bias[n];
-                    Z[o] = v;
-                    v = gelu(v);
-                }
-                if constexpr (EPI == kGeluGrad) v *= gelu_grad(Z[o]);
-                C[o] = v;
+            for (int j = 0; j < kG; j++) {
+                const int e = tid + (j0 + j) * kThreads;
+                const int mm = sak == 1 ? e / TK : e % TM, kk = sak == 1 ? e % TK : e / TM;
+                const int m = m0 + mm, k = k0 + kk;
+                v[j] = (m < M && k < K) ? __ldg(A + (long long)m * sam + (long long)k * sak) : 0.0f;
             }
+#pragma unroll
+            for (int j = 0; j < kG; j++) {
+                const int e = tid + (j0 + j) * kThreads;
+                const int mm = sak == 1 ? e / TK : e % TM, kk = sak == 1 ? e % TK : e / TM;
+                *reinterpret_cast<__nv_bfloat16 *>(As + core_off(mm, kk)) = __float2bfloat16_rn(v[j]);
+            }
+        }
+        {
+            float v[kB];
+#pragma unroll
+            for (int j = 0; j < kB; j++) {
+                const int e = tid + j * kThreads;
+                const int nn = sbk == 1 ? e / TK : e % TN, kk = sbk == 1 ? e % TK : e / TN;
+                const int n = n0 + nn, k = k0 + kk;
+                v[j] = (n < N && k < K) ? __ldg(B + (long long)k * sbk + (long long)n * sbn) : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < kB; j++) {
+                const int e = tid + j * kThreads;
+                const int nn = sbk == 1 ? e / TK : e % TN, kk = sbk == 1 ? e % TK : e / TN;
+                *reinterpret_cast<__nv_bfloat16 *>(Bs + core_off(nn, kk)) = __float2bfloat16_rn(v[j]);
+            }
+        }
+        // the stores above are generic-proxy writes the tensor core reads through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < TK / 16; ks++) {
+                const uint64_t ad = smem_desc(As + ks * 2 * kCoreK, kCoreK, kCoreMN);
+                const uint64_t bd = smem_desc(Bs + ks * 2 * kCoreK, kCoreK, kCoreMN);
+                const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             ens::smem_addr(bar))
+                         : "memory");
+        }
+        ok = ens::mbar_wait(bar, phase, kTcWait);
+        phase ^= 1u;
+        tc_fence_after();
+        ok = __syncthreads_and(ok);
+    }
+    if (!ok) {
+        // report, give the products in flight one more bounded wait, then free the columns
+        if (tid == 0) atomicExch(&g_tc_fault, 1);
+        ens::mbar_wait(bar, phase ^ 1u, kTcWait);
+    } else {
+        const int m = m0 + 32 * warp + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int c = 0; c < TN; c += 16) {
+            float v[16];
+            if (K > 0) {
+                tc_ld16(trow + (uint32_t)c, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; j++) v[j] = 0.0f;
+            }
+            if (m < M) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int n = n0 + c + j;
+                    if (n >= N) continue;
+                    float x = v[j];
+                    const long long o = (long long)m * ldc + n;
+                    if constexpr (EPI == kBiasStore) x += bias[n];
+                    if constexpr (EPI == kBiasGelu) {
+                        x += bias[n];
+                        Z[o] = x;
+                        x = gelu(x);
+                    }
+                    if constexpr (EPI == kGeluGrad) x *= gelu_grad(Z[o]);
+                    C[o] = x;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 // loss = sum (y - t)^2 / count (one block, fixed order); dy = 2 (y - t) / count.
@@ -257,13 +351,37 @@ long long float_bits(float f) {
     return i;
 }
 
+// The products' dynamic shared memory is above the 48 KB default only in principle (28
+// KB), but setting it explicitly once, outside any graph capture, keeps every launch valid.
+cudaError_t gemm_setup() {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<kStore>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_kernel<kBiasStore>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_kernel<kBiasGelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_kernel<kGeluGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    return e;
+}
+
+// A bounded tensor-core wait that gave up since the last check (the flag is cleared).
+bool tc_faulted() {
+    int f = 0;
+    if (cudaMemcpyFromSymbol(&f, g_tc_fault, sizeof(int)) != cudaSuccess) return true;
+    if (f) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_tc_fault, &zero, sizeof(int));
+    }
+    return f != 0;
+}
+
 template <int EPI>
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float *A, long long sam, long long sak,
                  const float *B, long long sbk, long long sbn, float *C, int ldc,
                  const float *bias = nullptr, float *Z = nullptr) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid(cdiv(N, BN), cdiv(M, BM));
-    gemm_kernel<EPI><<<grid, kThreads, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, Z);
+    dim3 grid(cdiv(N, TN), cdiv(M, TM));
+    gemm_kernel<EPI><<<grid, kThreads, kTcSmem, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, Z);
     return cudaGetLastError();
 }
 
@@ -429,6 +547,7 @@ int sur_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch,
         SCK(cudaMemset(c->g, 0, sizeof(float) * c->np));
         SCK(cudaMemset(c->tstep, 0, sizeof(int)));
         SCK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        SCK(gemm_setup());
         return SUR_OK;
     }();
     if (rc != SUR_OK) {
@@ -485,6 +604,7 @@ int sur_loss_grad(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B,
     if (grad_host)
         SCK(cudaMemcpyAsync(grad_host, c->g, sizeof(float) * c->np, cudaMemcpyDeviceToHost, c->stream));
     SCK(cudaStreamSynchronize(c->stream));
+    if (tc_faulted()) return sfail(c, SUR_ERR_CUDA, "a tensor-core product gave up waiting");
     return SUR_OK;
 }
 
@@ -555,12 +675,14 @@ int sur_train(sur_ctx *c, const float *X_dev, const float *T_dev, int64_t n, int
             SCK(cudaMemcpyAsync(hist.data(), c->loss_hist, sizeof(float) * steps, cudaMemcpyDeviceToHost,
                                 c->stream));
             SCK(cudaStreamSynchronize(c->stream));
+            if (tc_faulted()) return sfail(c, SUR_ERR_CUDA, "a tensor-core product gave up waiting");
             double s = 0.0;
             for (float x : hist) s += x;
             loss_host[ep] = (float)(s / steps);
         }
     }
     SCK(cudaStreamSynchronize(c->stream));
+    if (tc_faulted()) return sfail(c, SUR_ERR_CUDA, "a tensor-core product gave up waiting");
     return SUR_OK;
 }
 
@@ -576,6 +698,7 @@ int sur_loss(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, floa
         float l = 0.0f;
         SCK(cudaMemcpyAsync(&l, c->loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         SCK(cudaStreamSynchronize(c->stream));
+        if (tc_faulted()) return sfail(c, SUR_ERR_CUDA, "a tensor-core product gave up waiting");
         acc += (double)l * nb;
     }
     *loss_host = (float)(acc / B);
@@ -607,6 +730,7 @@ int sur_field_stats(const float *coef_dev, int32_t M, int32_t r, const float *me
 int sur_matmul(const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn,
                float *C, int32_t M, int32_t N, int32_t K, int32_t ldc, void *stream) {
     if (!A || !B || !C || M < 0 || N < 0 || K < 0 || ldc < N) return SUR_ERR_INVALID_ARG;
+    if (gemm_setup() != cudaSuccess) return SUR_ERR_CUDA;
     return gemm<kStore>((cudaStream_t)stream, M, N, K, A, sam, sak, B, sbk, sbn, C, ldc) == cudaSuccess
                ? SUR_OK
                : SUR_ERR_CUDA;

@@ -166,3 +166,26 @@ def test_surrogate_pipeline_beats_plain_ensemble_on_time_to_statistics():
     assert e_mean < 1e-2 and e_std < 0.15 and e_fluct < 0.35
     assert t_sur < 0.1 * t_solver
     net.close()
+
+
+def _bf16(a):
+    """Round float32 values to BF16 (nearest, ties to even) and back, in numpy."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (128, 64, 32), (129, 65, 33), (300, 200, 1111), (256, 256, 16)])
+def test_tensor_core_product_equals_bf16_inputs_with_fp32_accumulation(M, N, K):
+    """The product of the BF16-rounded operands, accumulated in binary64. Products of BF16
+    values are exact in FP32; the device's FP32 accumulation over K terms may differ from
+    the exact sum by (K + 2) * 2^-22 of the sum of |terms| (a bound that also covers an
+    accumulator that truncates instead of rounding)."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((K, N)).astype(np.float32)
+    C = sur.matmul(_dev(A), _dev(B)).cpu().numpy().astype(np.float64)
+    Ab, Bb = _bf16(A), _bf16(B)
+    ref = Ab @ Bb
+    bound = (K + 2) * 2.0 ** -22 * (np.abs(Ab) @ np.abs(Bb)) + 1e-30
+    assert np.all(np.abs(C - ref) <= bound)
