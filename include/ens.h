@@ -149,8 +149,10 @@ typedef struct {
                                (binary32 forms), 7 staged 128x9 with two samples
                                per thread and the traction loads issued before
                                the force loop, 8 and 9 persistent double-buffered
-                               forms of 5 and 6                                   */
-    float variant_us[10];   /* autotuner's time per step of each shape (-1: n/a,
+                               forms of 5 and 6, 10 and 11 the shapes of 6 and 4
+                               staged from fixed-stride block records (binary32
+                               forms)                                             */
+    float variant_us[12];   /* autotuner's time per step of each shape (-1: n/a,
                                0: not timed)                                      */
 } ens_info_t;
 

@@ -106,7 +106,7 @@ class ens_info_t(ctypes.Structure):
                 ("dt", ctypes.c_double), ("omega_lower", ctypes.c_double),
                 ("omega_upper", ctypes.c_double), ("bytes_per_step", ctypes.c_double),
                 ("device_bytes", ctypes.c_double), ("kernel_variant", ctypes.c_int32),
-                ("variant_us", ctypes.c_float * 10)]
+                ("variant_us", ctypes.c_float * 12)]
 
 
 class ens_batch_info_t(ctypes.Structure):

@@ -200,6 +200,18 @@ int make_stage_plan(ens_ctx *c, const std::vector<int32_t> &rowptr, int32_t bloc
     return ENS_OK;
 }
 
+// The fixed-stride block-record form of a staged plan (binary32 forms; the record
+// pointers are filled in once the records exist).
+StagePlan record_plan(StagePlan p) {
+    if (!p.staged) return p;
+    p.rec = 1;
+    p.rec_h = (p.nb + 1 + 3) / 4;
+    p.smem += 16u * (uint32_t)p.rec_h;
+    p.smem = (p.smem + 127u) / 128u * 128u;
+    if (p.smem > 160 * 1024) p.staged = 0;
+    return p;
+}
+
 // The pipelined (persistent, double-buffered) form of a staged plan.
 StagePlan pipelined_plan(StagePlan p) {
     if (!p.staged) return p;
@@ -518,6 +530,10 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                     // persistent CTAs with a double-buffered staging ring
                     cand[8] = pipelined_plan(cand[5]);
                     cand[9] = pipelined_plan(cand[6]);
+                    // shapes 6 and 4 staged from fixed-stride block records
+                    cand[10] = record_plan(cand[6]);
+                    cand[11] = record_plan(cand[4]);
+                    if (cand[11].nb != cand[10].nb) cand[11].staged = 0;
                 }
             }
             if (rcp != ENS_OK) return rcp;
@@ -534,6 +550,32 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         c->minv = dev_alloc(c, es * (size_t)NSp);
         if (!c->kc || !c->minv) return fail(c, ENS_ERR_ALLOC, "coefficient buffers");
         CK(launch_pack_kc(kc64, c->nnz, c->kc, to_f, c->stream));
+        if (cand[10].staged) {
+            const StagePlan &rp = cand[10];
+            const int64_t nblk = (N + rp.nb - 1) / rp.nb;
+            const int64_t words = (int64_t)rp.rec_h + rp.cnt_max;
+            std::vector<int4> rec((size_t)(nblk * words), make_int4(0, 0, 0, 0));
+            for (int64_t b = 0; b < nblk; b++) {
+                const int64_t n0 = b * rp.nb, n1 = std::min<int64_t>(N, n0 + rp.nb);
+                const int32_t pb = rowptr[n0];
+                int32_t *hdr = reinterpret_cast<int32_t *>(&rec[(size_t)(b * words)]);
+                for (int32_t k = 0; k <= rp.nb; k++) hdr[k] = rowptr[std::min<int64_t>(n0 + k, n1)] - pb;
+                for (int32_t j = 0; j < rowptr[n1] - pb; j++) rec[(size_t)(b * words + rp.rec_h + j)] = ent[pb + j];
+            }
+            c->rec_ent = (int4 *)dev_alloc(c, sizeof(int4) * rec.size());
+            c->rec_kc = dev_alloc(c, sizeof(float) * (size_t)nblk * rp.cnt_max * 20);
+            if (!c->rec_ent || !c->rec_kc) return fail(c, ENS_ERR_ALLOC, "block records");
+            CK(cudaMemcpyAsync(c->rec_ent, rec.data(), sizeof(int4) * rec.size(), cudaMemcpyHostToDevice,
+                               c->stream));
+            CK(launch_pack_records((const float *)c->kc, c->rowptr, N, rp.nb, rp.cnt_max, (float *)c->rec_kc,
+                                   c->stream));
+            CK(cudaStreamSynchronize(c->stream));  // the host records leave scope
+            for (int k : {10, 11}) {
+                cand[k].rec_ent = c->rec_ent;
+                cand[k].rec_kc = c->rec_kc;
+            }
+            if (c->plan.rec) c->plan = cand[c->variant];  // a forced record shape
+        }
         CK(launch_convert(m64, NSp, c->minv, to_f, 1, c->stream));
         if (to_f) {
             c->eh = dev_alloc(c, es * (size_t)E * c->Sp);
@@ -603,6 +645,12 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         if (!(c->flags_in & (ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | 0xf00)) && c->plan.staged) {
             rc0 = autotune(c, cand, kVariants);
             if (rc0 != ENS_OK) return rc0;
+        }
+        if (!c->plan.rec && c->rec_ent) {  // the records serve no chosen shape
+            dev_free(c, c->rec_ent);
+            dev_free(c, c->rec_kc);
+            c->rec_ent = nullptr;
+            c->rec_kc = nullptr;
         }
         return ens_reset(c);
     }();

@@ -9,7 +9,7 @@
 #include "ens_internal.cuh"
 
 namespace ens {
-constexpr int kVariants = 10;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kVariants = 12;  // launch shapes the autotuner can time (see ens_info_t)
 constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
 }
 
@@ -46,6 +46,8 @@ struct ens_ctx {
     int *h_flags = nullptr;  // pinned
     ens::StagePlan plan{};     // launch shape of the step kernel
     ens::StagePlan plan_fo{};  // launch shape of force-only evaluations
+    int4 *rec_ent = nullptr;     // fixed-stride block records (record shapes only)
+    void *rec_kc = nullptr;
     int32_t variant = 0;
     float variant_us[ens::kVariants] = {};
     int32_t flags_in = 0;

@@ -85,6 +85,15 @@ struct StagePlan {
     int32_t pipelined;  // persistent CTAs with a double-buffered staging ring
     uint32_t stage;     // bytes of one staging buffer (pipelined plans)
     int32_t grid;       // CTAs of a pipelined launch (0: computed at first launch)
+    // Fixed-stride block records (rec = 1): block b's incidence entries sit at
+    // rec_ent + b (rec_h + cnt_max), after rec_h 16-byte words of block-local row offsets
+    // (nb + 1 int32), and its coupling blocks at rec_kc + b cnt_max Kc<R>::stride, both
+    // zero-padded to cnt_max entries. The block can then issue its bulk copies before any
+    // global load, since every address and size follows from its index.
+    int32_t rec;
+    int32_t rec_h;
+    const int4 *rec_ent;
+    const void *rec_kc;
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or
@@ -159,6 +168,10 @@ cudaError_t launch_setup_stability(const int32_t *tri, const double *eh64, const
                                    double rho, double *w2lo, double *w2hi, cudaStream_t s);
 cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
                            cudaStream_t s);
+// Binary32 coupling blocks (stride 20) into fixed-stride block records of nb nodes and
+// cnt_max entries each (StagePlan::rec_kc), zero-padded.
+cudaError_t launch_pack_records(const float *kc, const int32_t *rowptr, int32_t N, int32_t nb,
+                                int32_t cnt_max, float *kc_rec, cudaStream_t s);
 // Output statistics (ens_outputs.cu).
 cudaError_t launch_element_mean(const int32_t *tri, const double *En, int32_t E, int32_t Sp, double *ebar,
                                 cudaStream_t s);

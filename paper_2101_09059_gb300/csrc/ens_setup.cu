@@ -259,6 +259,22 @@ __global__ void pack_kc_kernel(const double *__restrict__ kc64, int64_t nnz, voi
     }
 }
 
+__global__ void pack_records_kernel(const float *__restrict__ kc, const int32_t *__restrict__ rowptr,
+                                    int32_t N, int32_t nb, int32_t cnt_max, float *__restrict__ kc_rec,
+                                    int64_t total) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int64_t per = (int64_t)cnt_max * 20;
+    const int64_t b = t / per;
+    const int32_t r = (int32_t)(t - b * per);
+    const int32_t j = r / 20, q = r - j * 20;
+    const int64_t n0 = b * nb;
+    const int64_t n1 = n0 + nb < N ? n0 + nb : N;
+    const int32_t pb = rowptr[n0];
+    const int32_t cnt = rowptr[n1] - pb;
+    kc_rec[t] = j < cnt ? kc[((int64_t)pb + j) * 20 + q] : 0.0f;
+}
+
 __global__ void convert_kernel(const double *__restrict__ in, int64_t n, void *out, int to_float,
                                int invert) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -332,6 +348,14 @@ cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to
                            cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     pack_kc_kernel<<<blocks_for(nnz * 20, 256), 256, 0, s>>>(kc64, nnz, kc_out, to_float);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_records(const float *kc, const int32_t *rowptr, int32_t N, int32_t nb,
+                                int32_t cnt_max, float *kc_rec, cudaStream_t s) {
+    const int64_t total = (int64_t)((N + nb - 1) / nb) * cnt_max * 20;
+    if (total == 0) return cudaSuccess;
+    pack_records_kernel<<<blocks_for(total, 256), 256, 0, s>>>(kc, rowptr, N, nb, cnt_max, kc_rec, total);
     return cudaGetLastError();
 }
 

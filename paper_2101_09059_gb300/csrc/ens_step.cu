@@ -157,6 +157,22 @@ __device__ __forceinline__ void ld_state(const R *p, R (&x)[V]) {
         ld_nc(p, x);
 }
 
+// The step index a block keeps in shared memory, read where it is used (a volatile load,
+// so that it does not occupy registers through the force loop).
+__device__ __forceinline__ int64_t lds_step(const void *p) {
+    int64_t n;
+    asm volatile("ld.shared.s64 %0, [%1];" : "=l"(n) : "r"(smem_addr(p)));
+    return n;
+}
+
+// L2 prefetch of [p, p + bytes) widened to 16-byte boundaries (device allocations are
+// padded to 256 bytes, so the widened range stays inside the array's allocation).
+__device__ __forceinline__ void prefetch_range_l2(const void *p, uint32_t bytes) {
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(15);
+    const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~uintptr_t(15);
+    bulk_prefetch_l2(reinterpret_cast<const void *>(lo), (uint32_t)(hi - lo));
+}
+
 // Per-thread bases of the gathered arrays: the thread's own column within node 0 of u and
 // within (E h) row 0, so that a neighbour costs one 32 x 32 -> 64-bit multiply-add on its
 // node (element) index, and its other two dof rows one row stride each.
@@ -271,9 +287,18 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             // the conversion of the binary32 velocity increment on the integer pipe. A held
             // dof is the same for every sample of the node, so the branch is uniform across
             // the node's threads.
+            // The state rows are read whether or not the dof is held, so that these loads
+            // do not wait for the fixed-dof mask.
             double vv[V], h2[2];
             uint32_t tl[V];
             float ug[V];
+            ld_cs(a.utail + row, tl);
+#pragma unroll
+            for (int q = 0; q < V; q += 2) {
+                ld_cs(a.v64 + row + q, h2);
+                vv[q] = h2[0];
+                vv[q + 1] = h2[1];
+            }
             if (held) {
 #pragma unroll
                 for (int v = 0; v < V; v++) {
@@ -282,13 +307,6 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
                     ug[v] = 0.0f;
                 }
             } else {
-                ld_cs(a.utail + row, tl);
-#pragma unroll
-                for (int q = 0; q < V; q += 2) {
-                    ld_cs(a.v64 + row + q, h2);
-                    vv[q] = h2[0];
-                    vv[q + 1] = h2[1];
-                }
                 const float c2 = a.c2f;
 #pragma unroll
                 for (int v = 0; v < V; v++) {
@@ -305,12 +323,12 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
             st_wb(a.ug_next + row, ug);
         } else {  // kKahan32
             float lo[V], vv[V], hi[V];
+            ld_cs(a.ulo + row, lo);  // read whether or not held, as above
+            ld_cs(a.v32 + row, vv);
             if (held) {  // uniform across the node's threads
 #pragma unroll
                 for (int v = 0; v < V; v++) lo[v] = vv[v] = hi[v] = 0.0f;
             } else {
-                ld_cs(a.ulo + row, lo);
-                ld_cs(a.v32 + row, vv);
                 const float c1 = a.c1f, c2 = a.c2f, dt = a.dtf;
 #pragma unroll
                 for (int v = 0; v < V; v++) {
@@ -406,16 +424,22 @@ __device__ __forceinline__ void load_incidence(const GatherBase<R> &g, const int
     ld_nc(g.ehrow(en.x), e);
 }
 
+// REC: the block's entries and coupling blocks come from fixed-stride block records
+// (StagePlan::rec_*), so thread 0 issues every bulk copy at once, without first loading
+// the block's row offsets; each thread then reads its node's offsets from the staged
+// record header.
 template <int FORM, typename R, bool FORCE_ONLY, int BLOCK, int MINB, int V = Vw<R>::V,
-          bool HOIST = false>
+          bool HOIST = false, bool REC = false>
 __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs<R> a,
                                                                   const StagePlan pl) {
     const int32_t nb_block = pl.nb;
     const int32_t cnt_max = pl.cnt_max;
+    const int32_t hw = REC ? pl.rec_h : 0;  // header words of a record
     constexpr int KS = Kc<R>::stride;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int4 *ent_s = reinterpret_cast<int4 *>(smem + 16);
+    int4 *rec_s = reinterpret_cast<int4 *>(smem + 16);
+    int4 *ent_s = rec_s + hw;
     R *kc_s = reinterpret_cast<R *>(ent_s + cnt_max);
     R *ug_s = kc_s + (size_t)cnt_max * KS;
 
@@ -424,31 +448,41 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     const int32_t N = a.fv.N;
     const int32_t n0 = blockIdx.x * nb_block;
     const int32_t nb = min(nb_block, N - n0);
-    const int32_t pb = __ldg(a.fv.rowptr + n0);
-    const int32_t cnt = __ldg(a.fv.rowptr + n0 + nb) - pb;
-    if (cnt < 1 || cnt > cnt_max) {
-        // the plan does not describe this block: copy nothing, report, leave
-        if (threadIdx.x == 0) atomicOr(a.flags, 4);
-        return;
+    int32_t pb = 0, cnt = cnt_max;
+    if constexpr (!REC) {
+        pb = __ldg(a.fv.rowptr + n0);
+        cnt = __ldg(a.fv.rowptr + n0 + nb) - pb;
+        if (cnt < 1 || cnt > cnt_max) {
+            // the plan does not describe this block: copy nothing, report, leave
+            if (threadIdx.x == 0) atomicOr(a.flags, 4);
+            return;
+        }
     }
     const int32_t li = threadIdx.x / Q;
     const int32_t s0 = (threadIdx.x - li * Q) * V;
     const bool valid = li < nb;
     const int32_t i = n0 + li;
     int32_t p0 = 0, p1 = 0;
-    if (valid) {
-        p0 = __ldg(a.fv.rowptr + i) - pb;
-        p1 = __ldg(a.fv.rowptr + i + 1) - pb;
+    if constexpr (!REC) {
+        if (valid) {
+            p0 = __ldg(a.fv.rowptr + i) - pb;
+            p1 = __ldg(a.fv.rowptr + i + 1) - pb;
+        }
     }
     const uint32_t row_bytes = (uint32_t)(nb * 3 * Sp * sizeof(R));
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_barrier_init();
-        const uint32_t b_ent = (uint32_t)cnt * 16u;
+        const uint32_t b_ent = (uint32_t)(hw + cnt) * 16u;
         const uint32_t b_kc = (uint32_t)cnt * KS * (uint32_t)sizeof(R);
         mbar_expect_tx(bar, b_ent + b_kc + row_bytes);
-        bulk_g2s(ent_s, a.fv.ent + pb, b_ent, bar);
-        bulk_g2s(kc_s, a.fv.kc + (size_t)pb * KS, b_kc, bar);
+        if constexpr (REC) {
+            bulk_g2s(rec_s, pl.rec_ent + (size_t)blockIdx.x * (hw + cnt_max), b_ent, bar);
+            bulk_g2s(kc_s, static_cast<const R *>(pl.rec_kc) + (size_t)blockIdx.x * cnt_max * KS, b_kc, bar);
+        } else {
+            bulk_g2s(ent_s, a.fv.ent + pb, b_ent, bar);
+            bulk_g2s(kc_s, a.fv.kc + (size_t)pb * KS, b_kc, bar);
+        }
         bulk_g2s(ug_s, a.ug_cur + (size_t)n0 * 3 * Sp, row_bytes, bar);
         if constexpr (!FORCE_ONLY) {
             const size_t r0 = (size_t)n0 * 3 * Sp;
@@ -462,13 +496,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
             } else {
                 bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
             }
+            // the block's traction-pattern rows (a few patterns only: one request each)
+            if (a.J <= 4)
+                for (int32_t j = 0; j < a.J; j++)
+                    prefetch_range_l2(a.modes + ((int64_t)j * N + n0) * 3, (uint32_t)(nb * 3 * sizeof(R)));
+            // the step index, once per block, while the copies are in flight (the
+            // mbarrier uses the first 8 of the 16 bytes before the staged data)
+            *reinterpret_cast<int64_t *>(smem + 8) = *a.step_ctr + a.k_off;
         }
     }
     __syncthreads();
     // HOIST: issue the traction loads now so they overlap the staging and the gathers
     R fe[3] = {R(0), R(0), R(0)};
     if constexpr (!FORCE_ONLY && HOIST)
-        if (valid) step_traction<R>(a, i, fe);
+        if (valid) node_traction<R>(a, i, lds_step(smem + 8), fe);
     if (!mbar_wait(bar, 0, kWaitLimit)) {
         // Report, then give the copies in flight one more bounded wait before leaving.
         if (threadIdx.x == 0) atomicOr(a.flags, 2);
@@ -476,6 +517,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
         return;
     }
     if (!valid) return;
+    if constexpr (REC) {
+        const int32_t *hdr = reinterpret_cast<const int32_t *>(rec_s);
+        p0 = hdr[li];
+        p1 = hdr[li + 1];
+        if (p0 < 0 || p1 < p0 || p1 > cnt_max) {  // not a record of this plan
+            atomicOr(a.flags, 4);
+            return;
+        }
+    }
 
     R ui[3][V];
 #pragma unroll
@@ -499,7 +549,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     if constexpr (FORCE_ONLY) {
         store_force<R, V>(a, i, s0, f);
     } else {
-        if constexpr (!HOIST) step_traction<R>(a, i, fe);
+        if constexpr (!HOIST) node_traction<R>(a, i, lds_step(smem + 8), fe);
         node_update<FORM, R, V>(a, i, s0, ui, f, fe);
     }
 }
@@ -856,9 +906,10 @@ void note_launch(const char *what, int block, int minb, uint32_t smem, cudaError
              block, minb, smem, cudaGetErrorString(e));
 }
 
-template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V, bool HOIST = false>
+template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V, bool HOIST = false,
+          bool REC = false>
 cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
-    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V, HOIST>;
+    auto *k = step_staged_kernel<FORM, R, FO, BLOCK, MINB, V, HOIST, REC>;
     StepArgs<R> a = a0;
     a.fv.Q = a.fv.Sp / V;
     if (plan->smem > 48 * 1024) {
@@ -916,6 +967,10 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
                 if (plan->pipelined) {
                     if (plan->block == 128) return launch_pipelined<FORM, R, 128, 8, 2>(a, s, plan);
                     return launch_pipelined<FORM, R, 256, 4, 2>(a, s, plan);
+                }
+                if (plan->rec) {
+                    if (plan->vw == 2) return launch_staged<FORM, R, FO, 128, 10, 2, false, true>(a, s, plan);
+                    return launch_staged<FORM, R, FO, 64, 12, 4, false, true>(a, s, plan);
                 }
                 if (plan->vw == 2) {
                     if (plan->hoist) return launch_staged<FORM, R, FO, 128, 9, 2, true>(a, s, plan);

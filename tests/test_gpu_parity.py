@@ -306,7 +306,7 @@ def test_every_launch_shape_is_bitwise_identical(precision, S):
     # the tuned context timed every candidate shape that applies
     tuned = runs[0][1]["variant_us"]
     assert tuned[0] > 0 and tuned[1] > 0
-    for k in range(10):                # every launch shape, forced
+    for k in range(12):                # every launch shape, forced
         e = ens.Ensemble.from_case(case, precision=precision, flags=ens.ensemble.FLAG_FORCE_VARIANT(k))
         e.step(80)
         assert np.array_equal(e.displacement(), base), k
