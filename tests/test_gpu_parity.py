@@ -313,6 +313,36 @@ def test_every_launch_shape_is_bitwise_identical(precision, S):
         e.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32_force", "kahan32"])
+@pytest.mark.parametrize("J", [1, 12])
+def test_block_records_with_uneven_blocks(precision, J):
+    """Shapes 10 and 11 stage from fixed-stride block records padded to the largest block.
+    With the node ids shuffled, the valence-3 end nodes fall into arbitrary blocks, so the
+    blocks hold different incidence counts (81 to 90 for 16 nodes here). J = 12 traction
+    patterns skip the pattern prefetch, J = 1 takes it. Both shapes must match the unstaged
+    kernel bit for bit."""
+    from synth.configs import _case
+    from synth.mesh import Mesh, tube_mesh
+    m = tube_mesh(12, 8, length=0.03)
+    perm = np.random.Generator(np.random.Philox(key=5)).permutation(m.n_nodes)  # new id of node
+    inv = np.argsort(perm)
+    shuffled = Mesh(m.xyz[inv], perm[m.tri].astype(np.int32), m.fixed[inv], name="tube_shuffled")
+    case = _case(shuffled, 16, 0, 80, "step")
+    if J > 1:  # J scaled copies of the pressure pattern, amplitudes split among them
+        case["modes"] = np.stack([case["modes"][0] * (1.0 + 0.05 * j) for j in range(J)])
+        case["amp"] = np.repeat(case["amp"][:, :1], J, axis=1) / J
+    e = ens.Ensemble.from_case(case, precision=precision, flags=ens.ensemble.FLAG_UNSTAGED)
+    e.step(60)
+    base = e.displacement()
+    e.close()
+    for k in (10, 11):
+        e = ens.Ensemble.from_case(case, precision=precision, flags=ens.ensemble.FLAG_FORCE_VARIANT(k))
+        assert e.info()["kernel_variant"] == k
+        e.step(60)
+        assert np.array_equal(e.displacement(), base), k
+        e.close()
+
+
 def test_ragged_width_uses_unstaged_kernel():
     case = synth.make_case("tube_small", S=33, n_steps=4)
     e = ens.Ensemble.from_case(case, precision="kahan32")
