@@ -106,3 +106,34 @@ def test_sample_solves_the_spde_system():
     K, Cl = og.operator(m.xyz, m.tri, kappa)
     r = K @ x - np.sqrt(Cl)[:, None] * z
     assert np.abs(r).max() < 1e-12 * np.abs(np.sqrt(Cl)[:, None] * z).max()
+
+
+def test_correlation_length_is_the_papers_distance_of_correlation_one_tenth():
+    """Section 2.1 defines rho = sqrt(8 nu) / kappa as the distance at which the Matérn
+    correlation is about 0.1, for every nu (tests/golden/paper_matern_correlation_length.json).
+    kappa_of must reproduce that: the exact Matérn correlation (scipy's K_nu, not the
+    oracle) at d = rho, and the oracle's own discrete nu = 1 covariance on a fine plate."""
+    import json
+    import os
+    from scipy.special import kv
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_matern_correlation_length.json")))
+    rho = 0.02
+    for nu in g["nu_values"]:
+        x = og.kappa_of(rho, nu) * rho
+        corr = 2.0 ** (1.0 - nu) / gamma(nu) * x ** nu * kv(nu, x)
+        assert 0.5 * g["correlation_at_rho_printed"] <= corr <= 1.5 * g["correlation_at_rho_printed"], (nu, corr)
+    # the discrete field: covariance column of the centre node of a fine plate
+    n, L = 121, 0.24
+    m = synth.plate_mesh(nx=n, ny=n, lx=L, ly=L)
+    K, Cl = og.operator(m.xyz, m.tri, og.kappa_of(rho))
+    lu = spla.splu(K.tocsc())
+    c = (n // 2) * n + n // 2
+    e = np.zeros(m.n_nodes)
+    e[c] = 1.0
+    col = lu.solve(Cl * lu.solve(e))
+    d = np.linalg.norm(m.xyz - m.xyz[c], axis=1)
+    at_rho = np.abs(d - rho) < 0.02 * rho
+    assert at_rho.sum() >= 4
+    corr = col[at_rho].mean() / col[c]
+    assert 0.5 * g["correlation_at_rho_printed"] <= corr <= 1.5 * g["correlation_at_rho_printed"], corr
+
