@@ -14,6 +14,10 @@
 * Discrete energy H_n = 1/2 d^T (M/dt^2 - K/4) d + 1/2 w^T K w - f^T w, with d = u_{n+1} - u_n
   and w = (u_n + u_{n+1}) / 2, is conserved by the undamped scheme under constant load.
 * Static limit: the damped run converges to the direct solve K_s u = f per realisation.
+* Ensemble invariants: realisations are independent systems, so permuting them permutes
+  the trajectories, a one-member run equals that member of the ensemble, and uniform
+  fields give identical members whose tube response is axisymmetric (no circumferential
+  displacement, Section 3.1's homogeneous case).
 """
 import numpy as np
 import pytest
@@ -184,3 +188,27 @@ def test_static_limit_of_damped_run(case_tiny):
     for k in range(mod.S):
         us = _static(mod, dict(case_tiny, amp=mod.amp), sample=k)
         assert np.linalg.norm(u[k] - us) <= 1e-7 * np.linalg.norm(us)
+
+
+def test_ensemble_invariants():
+    """A sample index mixed into another sample's coefficients (a transposed [N][S] field,
+    a shared mass, a wrong stride) breaks one of these, all of which hold bit for bit."""
+    case = synth.make_case("tube_small", S=4, n_steps=80, seed=2)
+    u = oracle.Model(case).run(60)[0]                       # [S][N][3]
+    perm = [2, 0, 3, 1]
+    shuffled = dict(case, E=case["E"][:, perm], h=case["h"][:, perm])
+    assert np.array_equal(oracle.Model(shuffled).run(60)[0], u[perm])
+    assert np.array_equal(oracle.Model(case, samples=[3]).run(60)[0][0], u[3])
+    # uniform fields: identical members, axisymmetric response of the clamped tube
+    from synth.configs import _case
+    m = synth.tube_mesh(24, 20, length=0.06)
+    uni = _case(m, 3, 0, 400, "step", uniform=True)
+    uu = oracle.Model(uni).run(300)[0]
+    assert np.array_equal(uu[0], uu[1]) and np.array_equal(uu[0], uu[2])
+    x = m.xyz
+    r = np.hypot(x[:, 0], x[:, 1])
+    u_r = (uu[0, :, 0] * x[:, 0] + uu[0, :, 1] * x[:, 1]) / r
+    u_t = (-uu[0, :, 0] * x[:, 1] + uu[0, :, 1] * x[:, 0]) / r
+    assert np.abs(u_r).max() > 0
+    assert np.abs(u_t).max() <= 1e-12 * np.abs(u_r).max()
+
