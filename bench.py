@@ -287,13 +287,13 @@ def bench_fields(args, local, stream, hbm_peak):
     z = [torch.from_numpy(rng.standard_normal((m.n_nodes, S))).to(f"cuda:{local}") for _ in range(2)]
     fs = pkg.FieldSampler(m.xyz, m.tri, rho, stream=stream)
     out = torch.empty_like(z[0])
-    fs.sample(z[0], scale=fs.scale_for(sigma), mean=0.7e6, lognormal=True, rtol=rtol, out=out)  # warm-up
+    fs.sample(z[0], sigma=sigma, mean=0.7e6, lognormal=True, rtol=rtol, out=out)  # warm-up
     torch.cuda.synchronize()
     times, iters, refs = [], [], []
     for k, mean in ((0, 0.7e6), (1, 1e-3)):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        fs.sample(z[k], scale=fs.scale_for(sigma), mean=mean, lognormal=True, rtol=rtol, out=out)
+        fs.sample(z[k], sigma=sigma, mean=mean, lognormal=True, rtol=rtol, out=out)
         ev1.record(stream)
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1) / 1e3)
@@ -424,8 +424,8 @@ def bench_paper_tables(args, local, stream):
         zh = torch.from_numpy(rng.standard_normal((m.n_nodes, S))).to(dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        E = fs.sample(zE, scale=fs.scale_for(0.07e6), mean=0.7e6, rtol=1e-8)
-        h = fs.sample(zh, scale=fs.scale_for(0.4e-3), mean=4.0e-3, rtol=1e-8)
+        E = fs.sample(zE, sigma=0.07e6, mean=0.7e6, rtol=1e-8)
+        h = fs.sample(zh, sigma=0.4e-3, mean=4.0e-3, rtol=1e-8)
         torch.cuda.synchronize()
         t_fields = time.perf_counter() - t0
         fs.close()

@@ -79,6 +79,15 @@ typedef enum { ENS_FP64 = 0, ENS_FP32_FORCE = 1, ENS_KAHAN32 = 2 } ens_precision
  * context's device, e.g. written by gmrf_sample) instead of host pointers; they are
  * checked on the device (every value finite and > 0) and copied.                     */
 #define ENS_FLAG_DEVICE_FIELDS 16
+/* The two field arguments of ens_create are per-element coefficients instead of nodal
+ * fields: E_node is read as eh host [n_elems][S], the Gauss-weighted product
+ * (E h)_e,s = sum_gp w_gp E(gp) h(gp) of Section 2.2.1, and h_node as rho_h host
+ * [n_elems][S], rho times the element's mean thickness, so that the lumped mass is
+ * m_i,s = sum over elements of A_e rho_h_e,s / 3 (Section 2.3); params.rho is then used
+ * only by the stress output, whose element modulus becomes E_e,s = eh_e,s rho / rho_h_e,s
+ * (exact when E and h are constant on each element). Every value finite and > 0. Not
+ * combinable with ENS_FLAG_DEVICE_FIELDS.                                             */
+#define ENS_FLAG_ELEMENT_COEFFS 32
 
 /* ---- displacement layouts for the getters ---------------------------------------- */
 #define ENS_LAYOUT_SNC 0 /* out[s][node][dof]  */
@@ -163,7 +172,8 @@ typedef struct {
  * S       : ensemble width, >= 1.
  * E_node, h_node : host [n_nodes][S] nodal modulus and thickness of every
  *           realisation (sample index innermost), all > 0 (device arrays with
- *           ENS_FLAG_DEVICE_FIELDS).
+ *           ENS_FLAG_DEVICE_FIELDS; per-element eh and rho_h [n_elems][S] with
+ *           ENS_FLAG_ELEMENT_COEFFS).
  * stream  : cudaStream_t to run on (NULL = legacy default stream).
  * alloc   : device allocator or NULL.
  * out     : receives the context; on failure *out is NULL and the code is returned
@@ -213,8 +223,13 @@ int ens_stats_device(ens_ctx *ctx, double *mean_dev, double *var_dev);
 
 /* Internal force K_s u_s of every realisation for a given displacement field
  * (Section 2.4 assembly-free product; the term dt^2 K u_n of Eq. dynamicsCD without
- * dt^2), computed by the same device path and precision as ens_step. u, f: host
- * [n_nodes][3][S] binary64. The context state is not changed.                       */
+ * dt^2), computed by the same device path and precision as ens_step. u is first brought
+ * to the value the form's step gathers: binary64 as is (ENS_FP64), truncated toward
+ * zero to binary32 (ENS_FP32_FORCE, the state's head), rounded to nearest binary32
+ * (ENS_KAHAN32, the state's hi part). For a u that a state of the context holds, f is
+ * bit for bit the internal force the next step applies. u, f: host [n_nodes][3][S]
+ * binary64; u finite, and below 2^128 in magnitude for the binary32 forms
+ * (ENS_ERR_INVALID_ARG otherwise). The context state is not changed.               */
 int ens_internal_force(ens_ctx *ctx, const double *u, double *f);
 
 /* The same internal force as ens_internal_force, for callers that may not allocate
@@ -229,7 +244,9 @@ int ens_internal_force(ens_ctx *ctx, const double *u, double *f);
  * that first call before any stream capture. Asynchronous on the context stream. All
  * calls share the one array, so calls that overlap on the GPU (other streams, other
  * contexts on the same device) race; every staged value is rewritten before it is read,
- * so a call never sees the previous call's contents.                                 */
+ * so a call never sees the previous call's contents. Unlike ens_internal_force, which
+ * reads u on the host and rejects non-finite values, this call does not inspect u_dev:
+ * an Inf or NaN in u_dev gives non-finite forces in f_dev and no error code.          */
 int ens_internal_force_noalloc(ens_ctx *ctx, const double *u_dev, double *f_dev);
 
 /* Per-realisation coefficients as binary64 (Section 2.2.1 Gauss rule, Section 2.3

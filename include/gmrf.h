@@ -31,16 +31,20 @@ typedef struct gmrf_ctx gmrf_ctx;
 /* Assemble K = kappa^2 C~ + G of the triangulated surface on the host, in binary64, and
  * copy it to the device as CSR together with the Jacobi preconditioner and C~^(1/2).
  * xyz host [n_nodes][3], tri host [n_elems][3] (node ids in [0, n_nodes), every node in
- * some element, no element of zero area). kappa > 0: sqrt(8) / correlation length for
- * nu = 1 (Section 2.1). stream: cudaStream_t (NULL = legacy default stream).        */
+ * some element, no element of zero area). corr_length > 0: the correlation length rho
+ * of Section 2.1 (the distance at which the correlation is near 0.1); the library takes
+ * kappa = sqrt(8 nu) / rho with nu = 1 and reports it in gmrf_info_t. stream:
+ * cudaStream_t (NULL = legacy default stream).                                      */
 int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32_t *tri,
-                double kappa, void *stream, gmrf_ctx **out);
+                double corr_length, void *stream, gmrf_ctx **out);
 
 /* Draw S fields. z: device [n_nodes][S] binary64 standard normals (sample index
  * innermost), read only. out: device [n_nodes][S] binary64, written with
- *     out = mean * exp(scale * x)   (lognormal = 1)   or   out = mean + scale * x   (0),
- * x = K^-1 C~^(1/2) z. For marginal standard deviation sigma of x (nu = 1, d = 2) pass
- * scale = sigma sqrt(4 pi) kappa. The solve is iterative refinement from x = 0: the
+ *     out = mean * exp(c * x)   (lognormal = 1)   or   out = mean + c * x   (0),
+ * x = K^-1 C~^(1/2) z, where c = sigma sqrt(4 pi) kappa gives the Gaussian field c x the
+ * marginal standard deviation sigma of the continuous Matern field (variance
+ * 1 / (4 pi kappa^2) for nu = 1 on a 2-D surface, Section 2.1); sigma <= 0 means c = 1
+ * (x itself). The solve is iterative refinement from x = 0: the
  * residual b - K x (b = C~^(1/2) z) is formed in binary64, a Jacobi-preconditioned
  * conjugate-gradient solve in binary32 reduces it by max(rtol, 1e-4), and x takes the
  * correction in binary64, until every sample has ||K x - b|| <= rtol ||b|| in binary64,
@@ -48,7 +52,7 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
  * written). Each sample stops updating once it converges, so the result is
  * deterministic.
  * rtol in (0, 1), max_iter >= 1, S >= 1.                                            */
-int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double scale, double mean,
+int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sigma, double mean,
                 int32_t lognormal, double rtol, int32_t max_iter);
 
 typedef struct {
@@ -60,6 +64,7 @@ typedef struct {
     int32_t last_S;
     int32_t refinements;    /* binary64 residual / correction steps it took         */
     double bytes_per_refinement; /* algorithmic HBM bytes of one of those steps    */
+    double kappa;           /* sqrt(8) / corr_length                                */
 } gmrf_info_t;
 
 int gmrf_info(const gmrf_ctx *g, gmrf_info_t *info);

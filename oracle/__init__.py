@@ -143,22 +143,32 @@ def lumped_mass(n_nodes: int, tri, area, hbar, rho: float):
 class Model:
     """Element matrices, Gauss products and lumped masses of one workload (all FP64)."""
 
-    def __init__(self, case, samples=None):
+    def __init__(self, case, samples=None, coeffs=None):
+        """coeffs = (eh [E][S], rho_hbar [E][S]): per-element coefficients given directly
+        (the Gauss products and rho times the element-mean thickness) instead of the
+        nodal fields case["E"], case["h"]."""
         mesh = case["mesh"]
         self.case = case
         self.N = mesh.n_nodes
         self.E = mesh.n_elems
-        E_node = case["E"] if samples is None else case["E"][:, samples]
-        h_node = case["h"] if samples is None else case["h"][:, samples]
-        self.S = E_node.shape[1]
         self.tri = _c(mesh.tri, np.int32)
         self.fixed = _c(mesh.fixed, np.uint8).reshape(-1)
         self.Kg, self.area = element_matrices(mesh.xyz, mesh.tri, case["nu"], case["kshear"])
         self.Kg = _c(self.Kg.reshape(self.E, 81), np.float64)
-        eh, hb = gauss_eh(mesh.tri, E_node, h_node)
+        if coeffs is None:
+            E_node = case["E"] if samples is None else case["E"][:, samples]
+            h_node = case["h"] if samples is None else case["h"][:, samples]
+            eh, hb = gauss_eh(mesh.tri, E_node, h_node)
+            rho = case["rho"]
+        else:
+            eh, hb = (np.asarray(a, dtype=np.float64) for a in coeffs)
+            if samples is not None:
+                eh, hb = eh[:, samples], hb[:, samples]
+            rho = 1.0                               # hb already carries rho
+        self.S = eh.shape[1]
         self.eh_se = _c(eh.T, np.float64)          # [S][E]
         self.hbar_se = _c(hb.T, np.float64)
-        m = lumped_mass(self.N, mesh.tri, self.area, hb, case["rho"])
+        m = lumped_mass(self.N, mesh.tri, self.area, hb, rho)
         self.m_sn = _c(m.T, np.float64)            # [S][N]
         self.alpha = float(case["alpha"])
         self.dt = float(case["dt"])

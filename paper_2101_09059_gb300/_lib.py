@@ -120,7 +120,7 @@ class gmrf_info_t(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("nnz", ctypes.c_int64), ("iterations", ctypes.c_int32),
                 ("max_relres", ctypes.c_double), ("bytes_per_iter", ctypes.c_double),
                 ("last_S", ctypes.c_int32), ("refinements", ctypes.c_int32),
-                ("bytes_per_refinement", ctypes.c_double)]
+                ("bytes_per_refinement", ctypes.c_double), ("kappa", ctypes.c_double)]
 
 
 _lib = None

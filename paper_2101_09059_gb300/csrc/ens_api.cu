@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/ens.h: argument checking, the node ->
 // element incidence lists, device memory, and the launch sequence of every call.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -375,13 +376,17 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         !std::isfinite(p->kshear) || !std::isfinite(p->alpha) || !std::isfinite(p->dt) ||
         p->precision < 0 || p->precision > 2 ||
         (p->flags & ~(ENS_FLAG_NO_AUTOTUNE | ENS_FLAG_UNSTAGED | ENS_FLAG_NO_GRAPH |
-                      ENS_FLAG_DEVICE_FIELDS | 0xf00)) != 0 ||
+                      ENS_FLAG_DEVICE_FIELDS | ENS_FLAG_ELEMENT_COEFFS | 0xf00)) != 0 ||
+        ((p->flags & ENS_FLAG_DEVICE_FIELDS) && (p->flags & ENS_FLAG_ELEMENT_COEFFS)) ||
         ((p->flags >> 8) & 0xf) > kVariants)
         return ENS_ERR_INVALID_ARG;
     if (alloc && (!alloc->alloc || !alloc->release)) return ENS_ERR_INVALID_ARG;
     if (!finite_all(mesh->xyz, 3 * (size_t)N)) return ENS_ERR_INVALID_ARG;
     const bool dev_fields = (p->flags & ENS_FLAG_DEVICE_FIELDS) != 0;
-    if (!dev_fields && (!finite_pos(E_node, (size_t)N * S) || !finite_pos(h_node, (size_t)N * S)))
+    // per-element coefficients: E_node, h_node carry (E h) and (rho hbar), [E][S]
+    const bool elem_coeffs = (p->flags & ENS_FLAG_ELEMENT_COEFFS) != 0;
+    const int64_t f_rows = elem_coeffs ? E : N;
+    if (!dev_fields && (!finite_pos(E_node, (size_t)f_rows * S) || !finite_pos(h_node, (size_t)f_rows * S)))
         return ENS_ERR_INVALID_ARG;
 
     ens_ctx *c = new (std::nothrow) ens_ctx();
@@ -461,12 +466,14 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         CK(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->stream));
         CK(cudaMemsetAsync(c->step_ctr, 0, sizeof(int64_t), c->stream));
 
-        // padded nodal fields: padding samples repeat sample 0 (finite, never reported)
+        // padded fields (nodal, or per element with ENS_FLAG_ELEMENT_COEFFS): padding
+        // samples repeat sample 0 (finite, never reported)
+        const int64_t FSp = f_rows * c->Sp;
         std::vector<double> Ep, hp;
         if (!dev_fields) {
-            Ep.resize((size_t)NSp);
-            hp.resize((size_t)NSp);
-            for (int64_t i = 0; i < N; i++)
+            Ep.resize((size_t)FSp);
+            hp.resize((size_t)FSp);
+            for (int64_t i = 0; i < f_rows; i++)
                 for (int32_t s = 0; s < c->Sp; s++) {
                     int32_t src = s < S ? s : 0;
                     Ep[i * c->Sp + s] = E_node[i * S + src];
@@ -475,8 +482,8 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         }
         double *En_d, *hn_d, *kc64, *area, *laml, *lamh, *xsq, *eh64, *m64, *w2lo, *w2hi;
         int *bad;
-        ALLOC(En_d, double, NSp);
-        ALLOC(hn_d, double, NSp);
+        ALLOC(En_d, double, FSp);
+        ALLOC(hn_d, double, FSp);
         ALLOC(kc64, double, 18 * c->nnz);
         ALLOC(area, double, E);
         ALLOC(laml, double, E);
@@ -496,8 +503,8 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
             CK(cudaStreamSynchronize(c->stream));
             if (nbad) return fail(c, ENS_ERR_INVALID_ARG, "%d device field values not finite and > 0", nbad);
         } else {
-            CK(cudaMemcpyAsync(En_d, Ep.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
-            CK(cudaMemcpyAsync(hn_d, hp.data(), sizeof(double) * NSp, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(En_d, Ep.data(), sizeof(double) * FSp, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(hn_d, hp.data(), sizeof(double) * FSp, cudaMemcpyHostToDevice, c->stream));
         }
         const int big = 0x7fffffff;
         CK(cudaMemcpyAsync(bad, &big, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -505,10 +512,15 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         // ---- set-up kernels ----------------------------------------------------------
         CK(launch_setup_elements(c->xyz_d, c->tri_d, c->ec2ent_d, E, c->nu, c->ks, kc64, area,
                                  laml, lamh, xsq, nullptr, bad, c->stream));
-        CK(launch_setup_eh(c->tri_d, En_d, hn_d, E, c->Sp, eh64, c->stream));
-        CK(launch_setup_mass(c->rowptr, c->ent, area, hn_d, N, c->Sp, c->rho, m64, c->stream));
+        if (elem_coeffs) {  // (E h) given per element; mass from the given rho hbar
+            CK(cudaMemcpyAsync(eh64, En_d, sizeof(double) * FSp, cudaMemcpyDeviceToDevice, c->stream));
+            CK(launch_setup_mass_elem(c->rowptr, c->ent, area, hn_d, N, c->Sp, m64, c->stream));
+        } else {
+            CK(launch_setup_eh(c->tri_d, En_d, hn_d, E, c->Sp, eh64, c->stream));
+            CK(launch_setup_mass(c->rowptr, c->ent, area, hn_d, N, c->Sp, c->rho, m64, c->stream));
+        }
         CK(launch_setup_stability(c->tri_d, eh64, m64, area, hn_d, laml, lamh, xsq, E, S, c->Sp,
-                                  c->rho, w2lo, w2hi, c->stream));
+                                  c->rho, elem_coeffs ? hn_d : nullptr, w2lo, w2hi, c->stream));
         const size_t es = elem_size(c->form);
         const int to_f = c->form != kFP64;
         StagePlan cand[kVariants] = {};  // every slot unstaged until a plan is built
@@ -586,7 +598,10 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
         }
         // element-mean modulus for the stress output
         ALLOC(c->ebar, double, (int64_t)E * c->Sp);
-        CK(launch_element_mean(c->tri_d, En_d, E, c->Sp, c->ebar, c->stream));
+        if (elem_coeffs)
+            CK(launch_modulus_from_coeffs(eh64, hn_d, (int64_t)E * c->Sp, c->rho, c->ebar, c->stream));
+        else
+            CK(launch_element_mean(c->tri_d, En_d, E, c->Sp, c->ebar, c->stream));
         int hbad = 0;
         std::vector<double> h_lo(E), h_hi(E);
         CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -900,6 +915,10 @@ int ens_internal_force(ens_ctx *c, const double *u, double *f) {
     if (!u || !f) return fail(c, ENS_ERR_INVALID_ARG, "null array");
     const size_t n = (size_t)c->N * 3 * c->S, np = (size_t)c->N * 3 * c->Sp;
     if (!finite_all(u, n)) return fail(c, ENS_ERR_INVALID_ARG, "non-finite displacement");
+    if (c->form != kFP64)
+        for (size_t k = 0; k < n; k++)
+            if (std::fabs(u[k]) >= 0x1p128)
+                return fail(c, ENS_ERR_INVALID_ARG, "displacement outside the binary32 range");
     const size_t es = elem_size(c->form);
     double *in_d = (double *)dev_alloc(c, 8 * n);
     void *ug = dev_alloc(c, es * np);
@@ -1124,13 +1143,17 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};
+// Per-device address cache. Two host threads making their first call on one device at
+// the same time may both look the address up; they store the same value, and the
+// atomics make that well defined.
+std::atomic<void *> g_scratch_addr[kMaxDevices];
 
 // Device address of g_static_scratch on device `dev`, looked up once per device with
 // that device current (in host code the symbol name is only a host-side stand-in).
 int static_scratch(ens_ctx *c, int dev, void **out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(c, ENS_ERR_INVALID_ARG, "device %d", dev);
-    if (g_scratch_addr[dev] == nullptr) {
+    void *cached = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (cached == nullptr) {
         int prev = -1;
         CK(cudaGetDevice(&prev));
         if (prev != dev) CK(cudaSetDevice(dev));
@@ -1140,9 +1163,10 @@ int static_scratch(ens_ctx *c, int dev, void **out) {
         if (e != cudaSuccess || p == nullptr)
             return fail(c, ENS_ERR_CUDA, "cudaGetSymbolAddress(g_static_scratch): %s",
                         cudaGetErrorString(e));
-        g_scratch_addr[dev] = p;
+        g_scratch_addr[dev].store(p, std::memory_order_release);
+        cached = p;
     }
-    *out = g_scratch_addr[dev];
+    *out = cached;
     return ENS_OK;
 }
 

@@ -165,7 +165,14 @@ cudaError_t launch_setup_stability(const int32_t *tri, const double *eh64, const
                                    const double *area, const double *h_node,
                                    const double *lam_lo, const double *lam_hi,
                                    const double *xsq, int32_t E, int32_t S, int32_t Sp,
-                                   double rho, double *w2lo, double *w2hi, cudaStream_t s);
+                                   double rho, const double *rhoh, double *w2lo, double *w2hi,
+                                   cudaStream_t s);
+// Per-element coefficients (ENS_FLAG_ELEMENT_COEFFS): lumped mass from (rho hbar) [E][Sp],
+// and the element modulus (E h) rho / (rho hbar) for the stress output.
+cudaError_t launch_setup_mass_elem(const int32_t *rowptr, const int4 *ent, const double *area,
+                                   const double *rhoh, int32_t N, int32_t Sp, double *m64, cudaStream_t s);
+cudaError_t launch_modulus_from_coeffs(const double *eh64, const double *rhoh, int64_t n, double rho,
+                                       double *ebar, cudaStream_t s);
 cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
                            cudaStream_t s);
 // Binary32 coupling blocks (stride 20) into fixed-stride block records of nb nodes and

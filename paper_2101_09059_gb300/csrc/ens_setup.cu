@@ -212,6 +212,33 @@ __global__ void setup_mass_kernel(const int32_t *__restrict__ rowptr, const int4
     m[t] = acc;
 }
 
+// The same lumped mass from per-element coefficients: each element gives each of its
+// corners A_e (rho hbar)_e,s / 3, with (rho hbar)_e,s given by the caller.
+__global__ void setup_mass_elem_kernel(const int32_t *__restrict__ rowptr, const int4 *__restrict__ ent,
+                                       const double *__restrict__ area, const double *__restrict__ rhoh,
+                                       int32_t N, int32_t Sp, double *__restrict__ m) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * Sp) return;
+    int32_t i = (int32_t)(t / Sp);
+    int32_t s = (int32_t)(t - (int64_t)i * Sp);
+    double acc = 0.0;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; p++) {
+        const int32_t e = ent[p].x;
+        acc += area[e] * rhoh[(int64_t)e * Sp + s] / 3.0;
+    }
+    m[t] = acc;
+}
+
+// Element modulus of per-element coefficients for the stress output: E_e,s =
+// (E h)_e,s / hbar_e,s with hbar_e,s = (rho hbar)_e,s / rho (E and h constant on the
+// element).
+__global__ void modulus_from_coeffs_kernel(const double *__restrict__ eh, const double *__restrict__ rhoh,
+                                           int64_t n, double rho, double *__restrict__ ebar) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    ebar[t] = eh[t] * rho / rhoh[t];
+}
+
 // Per element, over the real samples: omega^2 lower bound (element top eigenvector
 // padded with zeros, global lumped masses) and upper bound (element eigenvalue with
 // the element's own lumped-mass share, Irons-Treharne).
@@ -223,8 +250,8 @@ __global__ void setup_stability_kernel(const int32_t *__restrict__ tri,
                                        const double *__restrict__ lam_lo,
                                        const double *__restrict__ lam_hi,
                                        const double *__restrict__ xsq, int32_t E, int32_t S,
-                                       int32_t Sp, double rho, double *__restrict__ w2lo,
-                                       double *__restrict__ w2hi) {
+                                       int32_t Sp, double rho, const double *__restrict__ rhoh,
+                                       double *__restrict__ w2lo, double *__restrict__ w2hi) {
     int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     double lo = 0.0, hi = 0.0;
@@ -235,10 +262,11 @@ __global__ void setup_stability_kernel(const int32_t *__restrict__ tri,
             for (int c = 0; c < 3; c++) {
                 int64_t node = tri[3 * e + c];
                 mx += m[node * Sp + s] * xsq[3 * e + c];
-                hbar += hn[node * Sp + s] / 3.0;
+                if (!rhoh) hbar += hn[node * Sp + s] / 3.0;
             }
             if (mx > 0.0) lo = fmax(lo, ehs * lam_lo[e] / mx);
-            double me = rho * area[e] * hbar / 3.0;
+            // (rhoh: per-element coefficients, the element's own rho hbar)
+            double me = rhoh ? area[e] * rhoh[(int64_t)e * Sp + s] / 3.0 : rho * area[e] * hbar / 3.0;
             if (me > 0.0) hi = fmax(hi, ehs * lam_hi[e] / me);
         }
     }
@@ -336,11 +364,27 @@ cudaError_t launch_setup_stability(const int32_t *tri, const double *eh64, const
                                    const double *area, const double *h_node,
                                    const double *lam_lo, const double *lam_hi,
                                    const double *xsq, int32_t E, int32_t S, int32_t Sp,
-                                   double rho, double *w2lo, double *w2hi, cudaStream_t s) {
+                                   double rho, const double *rhoh, double *w2lo, double *w2hi,
+                                   cudaStream_t s) {
     if (E == 0) return cudaSuccess;
     setup_stability_kernel<<<blocks_for(E, 128), 128, 0, s>>>(tri, eh64, m64, area, h_node,
                                                                lam_lo, lam_hi, xsq, E, S, Sp,
-                                                               rho, w2lo, w2hi);
+                                                               rho, rhoh, w2lo, w2hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_mass_elem(const int32_t *rowptr, const int4 *ent, const double *area,
+                                   const double *rhoh, int32_t N, int32_t Sp, double *m64, cudaStream_t s) {
+    int64_t n = (int64_t)N * Sp;
+    if (n == 0) return cudaSuccess;
+    setup_mass_elem_kernel<<<blocks_for(n, 256), 256, 0, s>>>(rowptr, ent, area, rhoh, N, Sp, m64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modulus_from_coeffs(const double *eh64, const double *rhoh, int64_t n, double rho,
+                                       double *ebar, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    modulus_from_coeffs_kernel<<<blocks_for(n, 256), 256, 0, s>>>(eh64, rhoh, n, rho, ebar);
     return cudaGetLastError();
 }
 

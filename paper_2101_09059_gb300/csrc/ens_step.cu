@@ -882,7 +882,9 @@ __global__ void export_kernel(const void *__restrict__ u_main, const void *__res
 }
 
 // Load a binary64 [N][3][S] field into a gathered-precision buffer (force-only
-// evaluations); padding samples are zero.
+// evaluations) as the form's state would hold it for the gather: binary64 as is; the
+// FP32-force head, u truncated toward zero (magnitudes below 2^-126 as signed zero);
+// the compensated form's hi part, u rounded to nearest. Padding samples are zero.
 template <int FORM>
 __global__ void import_kernel(const double *__restrict__ in, int32_t N, int32_t S, int32_t Sp,
                               void *ug) {
@@ -893,6 +895,8 @@ __global__ void import_kernel(const double *__restrict__ in, int32_t N, int32_t 
     const double x = s < S ? in[row * S + s] : 0.0;
     if constexpr (FORM == kFP64)
         ((double *)ug)[t] = x;
+    else if constexpr (FORM == kFP32Force)
+        ((float *)ug)[t] = f64_to_f32_rz(x);
     else
         ((float *)ug)[t] = (float)x;
 }
@@ -1151,8 +1155,10 @@ cudaError_t launch_import(int form, const double *in_ncs, int32_t N, int32_t S, 
     const unsigned grid = blocks_for(n, 256);
     if (form == kFP64)
         import_kernel<kFP64><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug);
-    else
+    else if (form == kFP32Force)
         import_kernel<kFP32Force><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug);
+    else
+        import_kernel<kKahan32><<<grid, 256, 0, s>>>(in_ncs, N, S, Sp, ug);
     return cudaGetLastError();
 }
 

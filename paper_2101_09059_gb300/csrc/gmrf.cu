@@ -528,13 +528,16 @@ int read_active(gmrf_ctx *g) {
 extern "C" {
 
 int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32_t *tri,
-                double kappa, void *stream, gmrf_ctx **out) {
+                double corr_length, void *stream, gmrf_ctx **out) {
     gmrf_ctx *g = nullptr;
     if (!out) return fail(g, GMRF_ERR_INVALID_ARG, "null output pointer");
     *out = nullptr;
     if (n_nodes < 1 || n_elems < 1 || !xyz || !tri)
         return fail(g, GMRF_ERR_INVALID_ARG, "mesh sizes or pointers");
-    if (!(kappa > 0.0) || !std::isfinite(kappa)) return fail(g, GMRF_ERR_INVALID_ARG, "kappa must be > 0");
+    if (!(corr_length > 0.0) || !std::isfinite(corr_length))
+        return fail(g, GMRF_ERR_INVALID_ARG, "correlation length must be finite and > 0");
+    // Section 2.1: rho = sqrt(8 nu) / kappa, with nu = 1
+    const double kappa = std::sqrt(8.0) / corr_length;
     const int32_t N = n_nodes, E = n_elems;
     // ---- assembly (host, binary64): G from barycentric gradients, lumped C~ -------------
     std::vector<double> cl(N, 0.0);
@@ -687,16 +690,21 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
     }
     g->info.n_nodes = N;
     g->info.nnz = g->nnz;
+    g->info.kappa = kappa;
     *out = g;
     return GMRF_OK;
 }
 
-int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double scale, double mean,
+int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sigma, double mean,
                 int32_t lognormal, double rtol, int32_t max_iter) {
     if (!g) return GMRF_ERR_INVALID_ARG;
-    if (S < 1 || !z || !out || !(rtol > 0.0 && rtol < 1.0) || max_iter < 1 || !std::isfinite(scale) ||
+    if (S < 1 || !z || !out || !(rtol > 0.0 && rtol < 1.0) || max_iter < 1 || !std::isfinite(sigma) ||
         !std::isfinite(mean) || (lognormal != 0 && lognormal != 1))
-        return fail(g, GMRF_ERR_INVALID_ARG, "S, pointers, rtol in (0, 1), max_iter >= 1, finite scale/mean");
+        return fail(g, GMRF_ERR_INVALID_ARG, "S, pointers, rtol in (0, 1), max_iter >= 1, finite sigma/mean");
+    // marginal variance of x for nu = 1 on a 2-D surface: 1 / (4 pi kappa^2) (Section 2.1,
+    // Matern variance Gamma(nu) / (Gamma(nu + d/2) (4 pi)^(d/2) kappa^(2 nu))), so the
+    // factor sigma sqrt(4 pi) kappa gives marginal standard deviation sigma
+    const double scale = sigma > 0.0 ? sigma * std::sqrt(4.0 * 3.14159265358979323846) * g->info.kappa : 1.0;
     const int32_t Sp = (S + 1) / 2 * 2;
     int rc = alloc_work(g, Sp);
     if (rc != GMRF_OK) return rc;

@@ -14,6 +14,7 @@ from . import _lib
 
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
 FLAG_NO_AUTOTUNE, FLAG_UNSTAGED, FLAG_NO_GRAPH, FLAG_DEVICE_FIELDS = 1, 2, 4, 16
+FLAG_ELEMENT_COEFFS = 32
 QTY_DISPLACEMENT, QTY_DISP_MAGNITUDE, QTY_STRESS = 0, 1, 2
 
 
@@ -85,7 +86,7 @@ class Ensemble:
 
     def __init__(self, xyz, tri, fixed, E_node, h_node, *, rho, nu, kshear, alpha, dt,
                  precision="fp64", stream=None, torch_allocator: bool = True, device: int = 0,
-                 flags: int = 0):
+                 flags: int = 0, element_coeffs: bool = False):
         torch = _torch()
         self._L = _lib.load()
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
@@ -102,6 +103,8 @@ class Ensemble:
             E_node = np.ascontiguousarray(E_node, dtype=np.float64)
             h_node = np.ascontiguousarray(h_node, dtype=np.float64)
             fields = (_ptr(E_node), _ptr(h_node))
+        if element_coeffs:  # E_node, h_node are (E h) and rho * hbar per element [E][S]
+            flags |= FLAG_ELEMENT_COEFFS
         self.N, self.E = self.xyz.shape[0], self.tri.shape[0]
         self.S = int(E_node.shape[1])
         self.precision = PRECISIONS.get(precision, precision)

@@ -4,8 +4,6 @@ the assembly of K = kappa^2 C~ + G runs in the library's host code, the solves o
 from __future__ import annotations
 
 import ctypes
-import math
-
 import numpy as np
 
 from . import _lib
@@ -21,31 +19,28 @@ class FieldSampler:
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self.tri = np.ascontiguousarray(tri, dtype=np.int32)
         self.n_nodes = self.xyz.shape[0]
-        self.kappa = math.sqrt(8.0) / corr_length
+        self.corr_length = float(corr_length)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         out = ctypes.c_void_p()
         rc = self._L.gmrf_create(self.n_nodes, self.tri.shape[0], ctypes.c_void_p(self.xyz.ctypes.data),
-                                 ctypes.c_void_p(self.tri.ctypes.data), self.kappa,
+                                 ctypes.c_void_p(self.tri.ctypes.data), self.corr_length,
                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(out))
         if rc != 0:
             raise EnsError(rc, self._L.gmrf_last_error(None).decode())
         self._g = out
+        self.kappa = self.info()["kappa"]
 
-    def scale_for(self, sigma: float) -> float:
-        """Scale giving marginal standard deviation sigma (variance 1 / (4 pi kappa^2) for
-        nu = 1 on a 2-D surface)."""
-        return sigma * math.sqrt(4.0 * math.pi) * self.kappa
-
-    def sample(self, z, scale: float = 1.0, mean: float = 0.0, lognormal: bool = False,
+    def sample(self, z, sigma: float = 0.0, mean: float = 0.0, lognormal: bool = False,
                rtol: float = 1e-10, max_iter: int = 20000, out=None):
-        """Fields from standard normals z (CUDA float64 [n_nodes][S]); returns out."""
+        """Fields from standard normals z (CUDA float64 [n_nodes][S]); returns out.
+        sigma > 0: marginal standard deviation of the Gaussian field; sigma <= 0: x itself."""
         import torch
         assert z.is_cuda and z.dtype == torch.float64 and z.is_contiguous() and z.shape[0] == self.n_nodes
         S = z.shape[1]
         if out is None:
             out = torch.empty_like(z)
         rc = self._L.gmrf_sample(self._g, S, ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                 float(scale), float(mean), 1 if lognormal else 0, float(rtol), int(max_iter))
+                                 float(sigma), float(mean), 1 if lognormal else 0, float(rtol), int(max_iter))
         if rc != 0:
             raise EnsError(rc, self._L.gmrf_last_error(self._g).decode())
         return out

@@ -95,11 +95,11 @@ def test_python_binding_has_no_cpu_path():
 def test_field_sampler_create_rejects_bad_input(L, case):
     xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], dtype=np.float64)
     tri = np.array([[0, 1, 2], [1, 3, 2]], dtype=np.int32)
-    kappa = 100.0
+    corr = 0.02
     if case == "kappa0":
-        kappa = 0.0
+        corr = 0.0
     elif case == "kappa_nan":
-        kappa = float("nan")
+        corr = float("nan")
     elif case == "node_out_of_range":
         tri = np.array([[0, 1, 2], [1, 4, 2]], dtype=np.int32)
     elif case == "orphan_node":
@@ -109,7 +109,7 @@ def test_field_sampler_create_rejects_bad_input(L, case):
         tri = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
     out = ctypes.c_void_p(1234)
     rc = L.gmrf_create(xyz.shape[0], tri.shape[0], ctypes.c_void_p(xyz.ctypes.data),
-                       ctypes.c_void_p(tri.ctypes.data), kappa, None,
+                       ctypes.c_void_p(tri.ctypes.data), corr, None,
                        None if case == "no_out" else ctypes.byref(out))
     assert rc == -1
     assert L.gmrf_last_error(None).decode()

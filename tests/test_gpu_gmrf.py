@@ -55,18 +55,20 @@ def test_lognormal_transform_and_determinism():
     z[:, 4] = 0.0   # a zero draw: the field is exactly the mean
     fs = pkg.FieldSampler(m.xyz, m.tri, RHO)
     zt = torch.from_numpy(z).cuda()
-    scale = fs.scale_for(sigma)
-    a = fs.sample(zt, scale=scale, mean=mean, lognormal=True).cpu().numpy()
-    b = fs.sample(zt, scale=scale, mean=mean, lognormal=True).cpu().numpy()
+    kappa = og.kappa_of(RHO)
+    # the library derives kappa from the correlation length as the pinned oracle does
+    assert fs.kappa == pytest.approx(kappa, rel=1e-15)
+    scale = og.marginal_scale(kappa, sigma)
+    a = fs.sample(zt, sigma=sigma, mean=mean, lognormal=True).cpu().numpy()
+    b = fs.sample(zt, sigma=sigma, mean=mean, lognormal=True).cpu().numpy()
     assert np.array_equal(a, b)
     assert np.all(a[:, 4] == mean)
-    kappa = og.kappa_of(RHO)
     x = og.sample(m.xyz, m.tri, kappa, z) * og.marginal_scale(kappa, sigma)
     ref = mean * np.exp(x)
     # |d exp(v)| <= exp(v) |dv| with |dv| <= scale * (solve bound), plus rounding of exp
     dv = scale * bound(m, z, 1e-10)
     assert np.all(np.abs(a - ref) <= ref * (dv[None, :] + 4e-16) * 1.01 + 1e-300)
-    lin = fs.sample(zt, scale=scale, mean=1.0, lognormal=False).cpu().numpy()
+    lin = fs.sample(zt, sigma=sigma, mean=1.0, lognormal=False).cpu().numpy()
     assert np.abs(lin - (1.0 + x)).max() <= dv.max() * 1.01 + 1e-15
     fs.close()
 
@@ -90,8 +92,8 @@ def test_device_fields_feed_the_ensemble_bitwise():
     fs = pkg.FieldSampler(m.xyz, m.tri, RHO)
     zE = torch.from_numpy(normals(m.n_nodes, 6, 1)).cuda()
     zh = torch.from_numpy(normals(m.n_nodes, 6, 2)).cuda()
-    E = fs.sample(zE, scale=fs.scale_for(0.1), mean=0.7e6, lognormal=True)
-    h = fs.sample(zh, scale=fs.scale_for(0.1), mean=1e-3, lognormal=True)
+    E = fs.sample(zE, sigma=0.1, mean=0.7e6, lognormal=True)
+    h = fs.sample(zh, sigma=0.1, mean=1e-3, lognormal=True)
     kw = dict(rho=case["rho"], nu=case["nu"], kshear=case["kshear"], alpha=case["alpha"], dt=case["dt"],
               precision="fp64")
     dev = pkg.Ensemble(m.xyz, m.tri, m.fixed, E, h, **kw)

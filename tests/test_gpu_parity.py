@@ -88,6 +88,84 @@ def test_internal_force_matches_oracle(name, S, precision):
     e.close()
 
 
+def _state_arrays(blob, precision, n):
+    """Split an ens_get_state blob (64-byte header) into (u main words, second words, v)."""
+    body = memoryview(blob)[64:]
+    if precision == "fp64":
+        u = np.frombuffer(body[:8 * n], dtype=np.float64)
+        return u, None, np.frombuffer(body[8 * n:16 * n], dtype=np.float64)
+    u = np.frombuffer(body[:4 * n], dtype=np.float32)
+    aux = np.frombuffer(body[4 * n:8 * n], dtype=np.uint32 if precision == "fp32_force" else np.float32)
+    vdt = np.float64 if precision == "fp32_force" else np.float32
+    return u, aux, np.frombuffer(body[8 * n:8 * n + n * np.dtype(vdt).itemsize], dtype=vdt)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+def test_internal_force_is_bitwise_the_force_the_step_applies(precision):
+    """ens_internal_force of a displacement a state holds equals, bit for bit, the force the
+    next step applies. The state is set to that displacement (binary32 values for the
+    binary32 forms, so the FP32-force tail and the compensated low part are zero) with zero
+    velocity, the step is undamped and unloaded, so the step's velocity is exactly
+    dt * ((0 - f) * (1 / m)) in the form's arithmetic (the update's fused multiply-add with
+    a zero velocity adds nothing): recomputed here from f and 1 / m in that precision."""
+    case = synth.make_case("tube_small", S=8, n_steps=4, alpha=0.0)
+    case = dict(case, amp=np.zeros_like(case["amp"]))
+    e = ens.Ensemble.from_case(case, precision=precision)
+    info = e.info()
+    N, S, Sp = info["n_nodes"], info["n_samples"], info["n_samples_padded"]
+    assert Sp == S
+    n = N * 3 * Sp
+    rng = np.random.default_rng(31)
+    free = np.asarray(case["mesh"].fixed, dtype=bool).reshape(N, 3) == 0
+    u = 1e-4 * rng.standard_normal((N, 3, S)) * free[:, :, None]
+    if precision != "fp64":
+        u = u.astype(np.float32).astype(np.float64)
+    blob = bytearray(e.get_state())
+    np.frombuffer(blob, dtype=np.int32, count=1, offset=28)[:] = 1      # started
+    body = np.frombuffer(blob, dtype=np.uint8, offset=64)
+    body[:] = 0
+    if precision == "fp64":
+        body[:8 * n] = np.frombuffer(u.astype(np.float64).tobytes(), dtype=np.uint8)
+    else:
+        body[:4 * n] = np.frombuffer(u.astype(np.float32).tobytes(), dtype=np.uint8)
+    e.set_state(bytes(blob))
+    f = e.internal_force(u)
+    _, minv = e.coefficients()
+    e.step(1)
+    _, _, v = _state_arrays(e.get_state(), precision, n)
+    v = v.reshape(N, 3, Sp)
+    dt = info["dt"]
+    if precision == "fp64":
+        expect = dt * ((0.0 - f) * minv[:, None, :])
+    else:
+        f32, m32 = f.astype(np.float32), minv.astype(np.float32)
+        assert np.array_equal(f32.astype(np.float64), f) and np.array_equal(m32.astype(np.float64), minv)
+        expect = np.float32(dt) * ((np.float32(0.0) - f32) * m32[:, None, :])
+    expect = np.where(free[:, :, None], expect, 0.0)
+    assert np.array_equal(v.astype(np.float64), np.asarray(expect, dtype=np.float64))
+    e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_force", "kahan32"])
+def test_internal_force_reads_u_as_the_state_holds_it(precision):
+    """FP32-force gathers u truncated toward zero, the compensated form u rounded to
+    nearest: a binary64 u between two binary32 values gives the force of that value."""
+    case = synth.make_case("tube_small", S=4, n_steps=4)
+    e = ens.Ensemble.from_case(case, precision=precision)
+    rng = np.random.default_rng(5)
+    u = 1e-4 * rng.standard_normal((e.N, 3, e.S))
+    rz = np.nextafter(u.astype(np.float32), np.float32(0.0))
+    near = u.astype(np.float32)
+    head = np.where(np.abs(near.astype(np.float64)) > np.abs(u), rz, near)   # truncation
+    held = head if precision == "fp32_force" else near
+    f = e.internal_force(u)
+    assert np.array_equal(f, e.internal_force(held.astype(np.float64)))
+    with pytest.raises(ens.EnsError) as ei:
+        e.internal_force(np.full_like(u, 1e39))
+    assert ei.value.code == -1
+    e.close()
+
+
 @pytest.mark.parametrize("flags", [0, ens.ensemble.FLAG_UNSTAGED])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
 @pytest.mark.parametrize("name,S", SMALL)
@@ -101,6 +179,40 @@ def test_trajectory_small_meshes(name, S, precision, flags):
     u = e.displacement("snc")
     assert rel_l2(u, ref) < TOL[precision]
     e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+def test_per_element_coefficients_match_oracle(case_tiny, precision):
+    """ens_create with ENS_FLAG_ELEMENT_COEFFS takes the per-element Gauss products (E h)
+    and rho * hbar directly, [E][S] (here drawn per element, not from nodal fields). The
+    oracle is fed the same two arrays; coefficients and the full 2000-step trajectory must
+    match."""
+    rng = np.random.default_rng(17)
+    E, S = case_tiny["mesh"].n_elems, case_tiny["S"]
+    eh = 0.7e6 * 1e-3 * np.exp(0.1 * rng.standard_normal((E, S)))
+    rho_h = case_tiny["rho"] * 1e-3 * np.exp(0.1 * rng.standard_normal((E, S)))
+    case = dict(case_tiny, dt=0.8 * case_tiny["dt"])
+    m = case["mesh"]
+    e = ens.Ensemble(m.xyz, m.tri, m.fixed, eh, rho_h, rho=case["rho"], nu=case["nu"],
+                     kshear=case["kshear"], alpha=case["alpha"], dt=case["dt"], precision=precision,
+                     element_coeffs=True)
+    e.set_traction(case["modes"], case["amp"])
+    mod = oracle.Model(case, coeffs=(eh, rho_h))
+    eh_d, minv_d = e.coefficients()
+    ctol = 1e-14 if precision == "fp64" else 1e-7
+    assert np.abs(eh_d - eh).max() <= ctol * eh.max()
+    assert np.abs(minv_d - 1.0 / mod.m_sn.T).max() <= ctol * (1.0 / mod.m_sn).max()
+    n = case["n_steps"]
+    ref, _ = mod.run(n)
+    e.step(n)
+    err = rel_l2(e.displacement(), ref)
+    print(f"per-element coefficients {precision}: rel-L2 {err:.3e}")
+    assert err < TOL[precision]
+    e.close()
+    with pytest.raises(ens.EnsError) as ei:   # a non-positive coefficient is refused
+        ens.Ensemble(m.xyz, m.tri, m.fixed, -eh, rho_h, rho=case["rho"], nu=case["nu"],
+                     kshear=case["kshear"], alpha=case["alpha"], dt=case["dt"], element_coeffs=True)
+    assert ei.value.code == -1
 
 
 @pytest.mark.parametrize("flags", [0, ens.ensemble.FLAG_UNSTAGED])
@@ -122,6 +234,23 @@ def test_tube_40x40_full_run(case_tiny, precision, flags):
     if precision == "fp64":
         assert np.abs(mean - m_ref).max() <= 1e-9 * np.abs(m_ref).max()
     # statistics of the device state must equal the two-pass statistics of that state
+    m2, v2 = oracle.stats(u)
+    assert np.abs(mean - m2).max() <= 1e-12 * np.abs(m2).max()
+    assert np.abs(var - v2).max() <= 1e-12 * np.abs(v2).max()
+    e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+@pytest.mark.parametrize("S", [129, 256, 500])
+def test_stats_of_wide_ensembles_match_two_pass(precision, S):
+    """Ensembles wider than the 128 samples the statistics kernel keeps in registers take
+    its re-reading branch: mean and sample variance of the device state must equal the
+    oracle's two-pass statistics of that state."""
+    case = synth.make_case("tube_small", S=S, n_steps=60)
+    e = ens.Ensemble.from_case(case, precision=precision)
+    e.step(60)
+    u = e.displacement()
+    mean, var = e.stats()
     m2, v2 = oracle.stats(u)
     assert np.abs(mean - m2).max() <= 1e-12 * np.abs(m2).max()
     assert np.abs(var - v2).max() <= 1e-12 * np.abs(v2).max()
@@ -226,22 +355,26 @@ def test_stability_bounds_bracket_true_frequency():
     e.close()
 
 
-def test_full_size_aneurysm_sampled_parity():
-    """The 200k-node, S = 64 aneurysm in the benchmark's launch configuration: the device
-    runs all 64 samples, the oracle two of them (samples are independent, so the subset
-    is exact), compared after 150 steps."""
-    case = synth.make_case("aneurysm", S=64, n_steps=150)
-    picks = [3, 60]
-    ref = _oracle_run(case, 150, samples=picks)
+def test_full_size_aneurysm_all_samples_1000_steps():
+    """The 200k-node, S = 64 aneurysm in the benchmark's launch configuration, every one
+    of the 64 realisations against the oracle after 1000 steps. That is past the damping
+    horizon 1 / (alpha dt), about 590 steps, over which rounding differences between the
+    two paths build up before damping bounds them, so the tolerances below are exercised
+    in the regime they were derived for. Every realisation is also checked on its own,
+    within ten times the ensemble tolerance."""
+    n = 1000
+    case = synth.make_case("aneurysm", S=64, n_steps=n)
+    ref = _oracle_run(case, n)
     for precision in ("fp32_force", "kahan32", "fp64"):
         e = ens.Ensemble.from_case(case, precision=precision)
-        e.step(150)
+        e.step(n)
         u = e.displacement()
-        for k, s in enumerate(picks):
-            err = rel_l2(u[s], ref[k])
-            print(f"aneurysm {precision} sample {s}: rel-L2 {err:.3e}")
-            assert err < TOL[precision]
         e.close()
+        err = rel_l2(u, ref)
+        worst = max(rel_l2(u[s], ref[s]) for s in range(u.shape[0]))
+        print(f"aneurysm {precision}, 64 samples x {n} steps: rel-L2 {err:.3e}, worst sample {worst:.3e}")
+        assert err < TOL[precision]
+        assert worst < 10 * TOL[precision]
 
 
 def test_full_size_arch_sampled_parity():

@@ -76,6 +76,32 @@ def test_adam_first_step():
     net.close()
 
 
+def test_adam_steps_match_oracle_adam_on_device_gradients():
+    """Five Adam steps on distinct mini-batches. Before each step the device's gradient of
+    the current parameters is read back (sur_loss_grad runs the same kernels on the same
+    data as sur_adam_step, so it is the gradient the step uses); the FP64 oracle's Adam is
+    fed those gradients from the same initial FP32 parameters. After every step each
+    parameter tensor must match: the moments are carried, the bias corrections use this
+    step's t, and beta1 / beta2 are not swapped. Tolerance: 1e-4 of the accumulated update
+    (FP32 moments, square root and division) plus a few FP32 ulps of the parameter per step
+    (the device stores the parameters in FP32)."""
+    net = sur.Surrogate(64, 256, 32, max_batch=512, seed=13)
+    P0 = net.params()
+    P_orc = [p.copy() for p in P0]
+    opt = mlp.Adam(P_orc, lr=2e-3)
+    for t in range(1, 6):
+        x, tg = _data(192, seed=20 + t)
+        X, T = _dev(x), _dev(tg)
+        _, g = net.loss_grad(X, T)
+        net.adam_step(X, T, 2e-3)
+        opt.step(P_orc, [np.asarray(gg, dtype=np.float64) for gg in g])
+        P_dev = net.params()
+        for k, (pd, po, p0) in enumerate(zip(P_dev, P_orc, P0)):
+            tol = 1e-4 * np.abs(po - p0) + 2.0 * t * np.finfo(np.float32).eps * np.abs(po) + 1e-12
+            assert np.all(np.abs(pd - po) <= tol), (t, k, float(np.abs(pd - po).max()))
+    net.close()
+
+
 def test_training_reduces_loss_like_the_oracle():
     x, t = _data(2048, seed=9)
     net = sur.Surrogate(64, 256, 32, max_batch=2048, seed=11)

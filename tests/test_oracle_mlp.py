@@ -5,6 +5,8 @@
   finite difference.
 * Adam's first step moves every parameter by lr * g / (|g| + eps / ...) which, with the
   bias corrections, is lr * sign(g) up to eps: a closed form independent of the code path.
+* Adam's later steps against the unrolled form of its recurrences: the bias-corrected
+  moments are normalised exponentially weighted means of the gradient history.
 """
 import numpy as np
 import pytest
@@ -82,3 +84,43 @@ def test_hidden_unit_permutation_and_loss_definition():
     assert np.allclose(mlp.forward(perm, x)[0], y, rtol=1e-14, atol=1e-15)
     t = y + 0.5                       # every residual is -0.5
     assert mlp.loss(params, x, t) == pytest.approx(0.25, rel=1e-14)
+
+
+def test_adam_later_steps_match_the_weighted_mean_closed_form():
+    """Adam beyond its first step. Unrolling m_t = b1 m_{t-1} + (1 - b1) g_t from m_0 = 0
+    gives m_t = (1 - b1) sum_k b1^(t-k) g_k, and 1 - b1^t = (1 - b1) sum_{j<t} b1^j, so the
+    bias-corrected moment is the normalised exponentially weighted mean
+        mhat_t = sum_k b1^(t-k) g_k / sum_k b1^(t-k)
+    (likewise vhat_t with b2 and g_k^2). The parameter after T steps is therefore
+    p_0 - lr sum_t mhat_t / (sqrt(vhat_t) + eps), written here from those weighted means
+    over the whole gradient history, not from the recurrence. Distinct gradients per step
+    and b1 != b2 make a swapped beta, a wrong bias-correction exponent or a moment that is
+    not carried between steps fail."""
+    rng = np.random.default_rng(11)
+    shape = (4, 5)
+    T = 5
+    gs = [rng.standard_normal(shape) * (1.0 + 0.5 * t) for t in range(T)]
+    p0 = rng.standard_normal(shape)
+    lr, b1, b2, eps = 0.01, 0.9, 0.999, 1e-8
+    params = [p0.copy()]
+    opt = mlp.Adam(params, lr=lr, b1=b1, b2=b2, eps=eps)
+    expect = p0.copy()
+    for t in range(1, T + 1):
+        opt.step(params, [gs[t - 1]])
+        w1 = np.array([b1 ** (t - k) for k in range(1, t + 1)])
+        w2 = np.array([b2 ** (t - k) for k in range(1, t + 1)])
+        hist = np.stack(gs[:t])
+        mhat = np.tensordot(w1, hist, axes=1) / w1.sum()
+        vhat = np.tensordot(w2, hist * hist, axes=1) / w2.sum()
+        expect = expect - lr * mhat / (np.sqrt(vhat) + eps)
+        assert np.allclose(params[0], expect, rtol=1e-12, atol=1e-14), t
+    # the closed form itself is not symmetric in (b1, b2): swapping them moves step 2
+    q = [p0.copy()]
+    swapped = mlp.Adam(q, lr=lr, b1=b2, b2=b1, eps=eps)
+    for t in range(2):
+        swapped.step(q, [gs[t]])
+    p2 = [p0.copy()]
+    right = mlp.Adam(p2, lr=lr, b1=b1, b2=b2, eps=eps)
+    for t in range(2):
+        right.step(p2, [gs[t]])
+    assert np.abs(q[0] - p2[0]).max() > 1e-4
