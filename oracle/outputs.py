@@ -57,6 +57,26 @@ def magnitude_rows(u_snc: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.linalg.norm(u_snc, axis=2).T)
 
 
+def peak_magnitude(model, n_steps: int, stride: int = 1, up=None, uc=None, step0: int = 0, peak=None):
+    """Running peak of the displacement magnitude (Section 3's peak and band quantities
+    over a heart cycle): for every node and realisation, the largest |u_k| over the
+    recorded steps k, the multiples of `stride` in (step0, step0 + n_steps]. Starts from
+    rest unless (up, uc) = (u_{step0 - 1}, u_{step0}) [S][N][3] and a previous peak [N][S]
+    are given. Returns (peak [N][S], u_prev, u_cur) after the last step; steps with
+    model.steps, one recording interval at a time."""
+    if up is None:
+        up, uc = model.start()
+    peak = np.zeros((model.N, model.S)) if peak is None else np.array(peak, dtype=np.float64)
+    step, end = step0, step0 + n_steps
+    while step < end:
+        k = min(stride - step % stride, end - step)
+        model.steps(up, uc, step, k)
+        step += k
+        if step % stride == 0:
+            peak = np.maximum(peak, magnitude_rows(uc))
+    return peak, up, uc
+
+
 def _frames(xyz, tri):
     X = xyz[tri]
     d12 = X[:, 1] - X[:, 0]
