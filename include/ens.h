@@ -337,6 +337,9 @@ int ens_merge_stats(int32_t n_parts, const int64_t *counts, const double *const 
 #define ENS_QTY_DISPLACEMENT 0
 #define ENS_QTY_DISP_MAGNITUDE 1
 #define ENS_QTY_STRESS 2
+/* Running peak over time (needs ens_set_peak), rows node: n_nodes rows, the largest
+ * |u_k| over the recorded steps k.                                                    */
+#define ENS_QTY_PEAK_MAGNITUDE 3
 
 /* Centreline polyline for the stress frame: pts host [n_pts][3], n_pts >= 2. Builds the
  * per-element stress operators on the device (6 x 9 binary64 values per element).
@@ -364,6 +367,19 @@ int ens_quantity_stats(ens_ctx *ctx, int32_t qty, int32_t n_q, const double *q, 
 int ens_row_stats_device(int64_t n_rows, int32_t S, const double *rows, int32_t n_q,
                          const double *q, double *mean, double *var, double *quant,
                          void *stream);
+
+/* Running peak of the displacement magnitude per node and realisation (the peak and
+ * band quantities of Section 3 over a heart cycle): with stride >= 1, every step that
+ * ends on an index k that is a multiple of stride updates peak = max(peak, |u_k|), |u|
+ * formed in binary64 from the state of any form; read it as ENS_QTY_PEAK_MAGNITUDE.
+ * The call zeroes the peak (so it covers steps after the call), as does ens_reset;
+ * stride = 0 switches tracking off and frees it. The peak is updated by a separate
+ * kernel after each step launch (also inside the captured time-loop graphs): per
+ * recorded step it reads the state once (24 B per node and sample) and reads and writes
+ * the peak (16 B). It is not part of ens_get_state's checkpoint, and contexts that
+ * track a peak cannot join a batch (ens_batch_create / ens_batch_step return
+ * ENS_ERR_STATE).                                                                     */
+int ens_set_peak(ens_ctx *ctx, int32_t stride);
 
 /* Probe time histories: after every ens_step segment that ends on a step index that is
  * a multiple of stride, record the displacement of n_nodes probe nodes (all dofs, all

@@ -186,6 +186,7 @@ def load(build_if_missing: bool = True):
         "ens_quantity_stats": ([vp, i32, i32, dp, dp, dp, dp], ctypes.c_int),
         "ens_row_stats_device": ([i64, i32, dp, i32, dp, dp, dp, dp, vp], ctypes.c_int),
         "ens_set_probes": ([vp, i32, dp, i32, dp, i32, i64], ctypes.c_int),
+        "ens_set_peak": ([vp, i32], ctypes.c_int),
         "ens_get_probes": ([vp, dp, dp, dp, ctypes.POINTER(i64)], ctypes.c_int),
         "gmrf_create": ([i32, i32, dp, dp, ctypes.c_double, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "gmrf_sample": ([vp, i32, dp, dp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, i32],

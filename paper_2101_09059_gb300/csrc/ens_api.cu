@@ -130,6 +130,7 @@ cudaError_t launch_chunk_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s)
         c2 = c->dt / (1.0 + beta);
     }
     const int par = c->cur ^ (k & 1);
+    cudaError_t e;
     if (c->form == kFP64) {
         StepArgs<double> a = make_args<double>(c);
         a.ug_cur = (const double *)c->ug[par];
@@ -137,17 +138,22 @@ cudaError_t launch_chunk_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s)
         a.k_off = k;
         a.c1 = c1;
         a.c2 = c2;
-        return launch_step<double>(c->form, a, false, s, &c->plan);
+        e = launch_step<double>(c->form, a, false, s, &c->plan);
+    } else {
+        StepArgs<float> a = make_args<float>(c);
+        a.ug_cur = (const float *)c->ug[par];
+        a.ug_next = (float *)c->ug[par ^ 1];
+        a.k_off = k;
+        a.c1 = c1;
+        a.c2 = c2;
+        a.c1f = (float)c1;
+        a.c2f = (float)c2;
+        e = launch_step<float>(c->form, a, false, s, &c->plan);
     }
-    StepArgs<float> a = make_args<float>(c);
-    a.ug_cur = (const float *)c->ug[par];
-    a.ug_next = (float *)c->ug[par ^ 1];
-    a.k_off = k;
-    a.c1 = c1;
-    a.c2 = c2;
-    a.c1f = (float)c1;
-    a.c2f = (float)c2;
-    return launch_step<float>(c->form, a, false, s, &c->plan);
+    if (e == cudaSuccess && c->peak)  // running peak of the state just written
+        e = launch_peak(c->form, c->ug[par ^ 1], c->form == kFP32Force ? (const void *)c->utail : c->ulo, c->N,
+                        c->Sp, c->step_ctr, k, c->peak_stride, c->peak, s);
+    return e;
 }
 
 int run_steps(ens_ctx *c, int64_t n) {
@@ -691,6 +697,7 @@ int ens_reset(ens_ctx *c) {
     if (c->v32) CK(cudaMemsetAsync(c->v32, 0, 4 * n, c->stream));
     CK(cudaMemsetAsync(c->step_ctr, 0, sizeof(int64_t), c->stream));
     CK(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->stream));
+    if (c->peak) CK(cudaMemsetAsync(c->peak, 0, 8 * (size_t)c->N * c->Sp, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->cur = 0;
     c->step = 0;
@@ -780,7 +787,8 @@ int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
     const int K = kGraphSteps;
     if (n < 2 * K || !c->started || (c->flags_in & ENS_FLAG_NO_GRAPH)) return ENS_OK;
     std::vector<uintptr_t> key = {(uintptr_t)(c->cur & 1), (uintptr_t)c->amp, (uintptr_t)c->modes,
-                                  (uintptr_t)c->J, (uintptr_t)c->variant, (uintptr_t)c->plan.staged};
+                                  (uintptr_t)c->J, (uintptr_t)c->variant, (uintptr_t)c->plan.staged,
+                                  (uintptr_t)c->peak, (uintptr_t)c->peak_stride};
     if (!c->graph || c->graph_key != key) {
         if (c->graph) cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;

@@ -67,6 +67,9 @@ struct ens_ctx {
     int32_t probe_stride = 0, probe_nn = 0, probe_ne = 0;
     int64_t probe_rec = 0, probe_cap = 0;
     std::vector<int64_t> probe_steps;
+    // running peak of |u| per node and sample [N][Sp] (ens_set_peak)
+    double *peak = nullptr;
+    int32_t peak_stride = 0;
 };
 
 

@@ -45,6 +45,24 @@ __device__ __forceinline__ double u_at(const void *u_main, const void *aux, int6
         return ((const double *)u_main)[idx];
 }
 
+// Running peak of |u| per node and sample (ens_set_peak): after a step launch, the state
+// just written has index n = *ctr + k_off + 1; when n is a multiple of the stride the
+// peak takes max(peak, |u_n|) with |u| formed in binary64 from the form's state.
+template <int FORM>
+__global__ void peak_kernel(const void *__restrict__ u_main, const void *__restrict__ aux, int32_t N,
+                            int32_t Sp, const int64_t *__restrict__ ctr, int32_t k_off, int32_t stride,
+                            double *__restrict__ peak) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * Sp) return;
+    if ((*ctr + k_off + 1) % stride != 0) return;
+    const int64_t i = t / Sp;
+    const int64_t r0 = i * 3 * Sp + (t - i * Sp);
+    const double x = u_at<FORM>(u_main, aux, r0);
+    const double y = u_at<FORM>(u_main, aux, r0 + Sp);
+    const double z = u_at<FORM>(u_main, aux, r0 + 2 * Sp);
+    peak[t] = fmax(peak[t], sqrt(x * x + y * y + z * z));
+}
+
 // E_e,s = (E_a + E_b + E_c) / 3 over the element's nodes.
 __global__ void ebar_kernel(const int32_t *__restrict__ tri, const double *__restrict__ En, int32_t E,
                             int32_t Sp, double *__restrict__ ebar) {
@@ -356,6 +374,20 @@ cudaError_t launch_element_mean(const int32_t *tri, const double *En, int32_t E,
     return cudaGetLastError();
 }
 
+cudaError_t launch_peak(int form, const void *u_main, const void *aux, int32_t N, int32_t Sp,
+                        const int64_t *step_ctr, int32_t k_off, int32_t stride, double *peak, cudaStream_t s) {
+    const int64_t n = (int64_t)N * Sp;
+    if (n == 0) return cudaSuccess;
+    const unsigned g = blocks_for(n, 256);
+    if (form == kFP64)
+        peak_kernel<kFP64><<<g, 256, 0, s>>>(u_main, aux, N, Sp, step_ctr, k_off, stride, peak);
+    else if (form == kFP32Force)
+        peak_kernel<kFP32Force><<<g, 256, 0, s>>>(u_main, aux, N, Sp, step_ctr, k_off, stride, peak);
+    else
+        peak_kernel<kKahan32><<<g, 256, 0, s>>>(u_main, aux, N, Sp, step_ctr, k_off, stride, peak);
+    return cudaGetLastError();
+}
+
 // Rows statistics on the device (context free). Shared memory per warp: P doubles.
 cudaError_t launch_row_stats(const double *rows, int64_t n_rows, int32_t S, int32_t n_q, const double *q_dev,
                              double *mean, double *var, double *quant, cudaStream_t s) {
@@ -393,6 +425,7 @@ int64_t quantity_rows(const ens_ctx *c, int32_t qty) {
     if (qty == ENS_QTY_DISPLACEMENT) return (int64_t)c->N * 3;
     if (qty == ENS_QTY_DISP_MAGNITUDE) return c->N;
     if (qty == ENS_QTY_STRESS) return (int64_t)c->E * 6;
+    if (qty == ENS_QTY_PEAK_MAGNITUDE) return c->N;
     return -1;
 }
 
@@ -415,6 +448,9 @@ cudaError_t launch_quantity_t(ens_ctx *c, int32_t qty, double *out) {
 cudaError_t launch_quantity(ens_ctx *c, int32_t qty, double *out) {
     if (qty == ENS_QTY_DISPLACEMENT)
         return launch_export(c->form, c->ug[c->cur], aux_of(c), c->N, c->S, c->Sp, out, ENS_LAYOUT_NCS, c->stream);
+    if (qty == ENS_QTY_PEAK_MAGNITUDE)  // [N][Sp] -> rows [N][S]
+        return cudaMemcpy2DAsync(out, 8 * (size_t)c->S, c->peak, 8 * (size_t)c->Sp, 8 * (size_t)c->S, (size_t)c->N,
+                                 cudaMemcpyDeviceToDevice, c->stream);
     if (c->form == kFP64) return launch_quantity_t<kFP64>(c, qty, out);
     if (c->form == kFP32Force) return launch_quantity_t<kFP32Force>(c, qty, out);
     return launch_quantity_t<kKahan32>(c, qty, out);
@@ -493,6 +529,8 @@ int ens_quantity_device(ens_ctx *c, int32_t qty, double *out) {
     if (rows < 0 || !out) return ofail(c, ENS_ERR_INVALID_ARG, "quantity code or output pointer");
     if (qty == ENS_QTY_STRESS && !c->has_centerline)
         return ofail(c, ENS_ERR_STATE, "stress needs a centreline (ens_set_centerline)");
+    if (qty == ENS_QTY_PEAK_MAGNITUDE && !c->peak)
+        return ofail(c, ENS_ERR_STATE, "no running peak (ens_set_peak)");
     OCK(launch_quantity(c, qty, out));
     return ENS_OK;
 }
@@ -532,6 +570,8 @@ int ens_quantity_stats(ens_ctx *c, int32_t qty, int32_t n_q, const double *q, do
     if (c->S > 16384) return ofail(c, ENS_ERR_INVALID_ARG, "quantiles support S <= 16384");
     if (qty == ENS_QTY_STRESS && !c->has_centerline)
         return ofail(c, ENS_ERR_STATE, "stress needs a centreline (ens_set_centerline)");
+    if (qty == ENS_QTY_PEAK_MAGNITUDE && !c->peak)
+        return ofail(c, ENS_ERR_STATE, "no running peak (ens_set_peak)");
     const size_t need = (size_t)rows * c->S;
     if (c->qty_cap < need) {
         if (c->qty_buf) ctx_free(c, c->qty_buf);
@@ -554,6 +594,22 @@ int ens_quantity_stats(ens_ctx *c, int32_t qty, int32_t n_q, const double *q, do
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     ctx_free(c, st);
     if (e != cudaSuccess) return ctx_fail(c, ENS_ERR_CUDA, "quantity statistics: %s", cudaGetErrorString(e));
+    return ENS_OK;
+}
+
+int ens_set_peak(ens_ctx *c, int32_t stride) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (stride < 0) return ofail(c, ENS_ERR_INVALID_ARG, "stride < 0");
+    OCK(cudaStreamSynchronize(c->stream));
+    if (c->peak) ctx_free(c, c->peak);
+    c->peak = nullptr;
+    c->peak_stride = 0;
+    if (stride == 0) return ENS_OK;
+    c->peak = (double *)ctx_alloc(c, 8 * (size_t)c->N * c->Sp);
+    if (!c->peak) return ofail(c, ENS_ERR_ALLOC, "peak buffer");
+    OCK(cudaMemsetAsync(c->peak, 0, 8 * (size_t)c->N * c->Sp, c->stream));
+    OCK(cudaStreamSynchronize(c->stream));
+    c->peak_stride = stride;
     return ENS_OK;
 }
 

@@ -15,7 +15,7 @@ from . import _lib
 FP64, FP32_FORCE, KAHAN32 = 0, 1, 2
 FLAG_NO_AUTOTUNE, FLAG_UNSTAGED, FLAG_NO_GRAPH, FLAG_DEVICE_FIELDS = 1, 2, 4, 16
 FLAG_ELEMENT_COEFFS = 32
-QTY_DISPLACEMENT, QTY_DISP_MAGNITUDE, QTY_STRESS = 0, 1, 2
+QTY_DISPLACEMENT, QTY_DISP_MAGNITUDE, QTY_STRESS, QTY_PEAK_MAGNITUDE = 0, 1, 2, 3
 
 
 def FLAG_FORCE_VARIANT(k: int) -> int:
@@ -239,7 +239,8 @@ class Ensemble:
         self._call("ens_set_centerline", pts.shape[0], _ptr(pts))
 
     def quantity_rows(self, qty: int) -> int:
-        return {QTY_DISPLACEMENT: 3 * self.N, QTY_DISP_MAGNITUDE: self.N, QTY_STRESS: 6 * self.E}[qty]
+        return {QTY_DISPLACEMENT: 3 * self.N, QTY_DISP_MAGNITUDE: self.N, QTY_STRESS: 6 * self.E,
+                QTY_PEAK_MAGNITUDE: self.N}[qty]
 
     def quantity_device(self, qty: int, out=None):
         """Rows of a quantity at the current step as a CUDA float64 tensor [rows][S]."""
@@ -260,6 +261,11 @@ class Ensemble:
         self._call("ens_quantity_stats", int(qty), len(qa), _ptr(qa) if len(qa) else None, _ptr(mean), _ptr(var),
                    _ptr(quant) if quant is not None else None)
         return mean, var, quant
+
+    def set_peak(self, stride: int = 1):
+        """Track the running peak of |u| per node and realisation on every step index that
+        is a multiple of stride (0: off); read it with QTY_PEAK_MAGNITUDE."""
+        self._call("ens_set_peak", int(stride))
 
     def set_probes(self, nodes=(), elems=(), stride: int = 0, capacity: int = 0):
         """Record displacement at probe nodes and stress at probe elements every stride steps."""

@@ -156,3 +156,53 @@ def test_full_size_aneurysm_outputs_sampled():
     mean, var, quant = e.quantity_stats(QTY_DISP_MAGNITUDE, [0.05, 0.5, 0.95])
     assert np.all(quant[:, 0] <= quant[:, 1]) and np.all(quant[:, 1] <= quant[:, 2])
     e.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+@pytest.mark.parametrize("stride", [1, 7])
+def test_running_peak_matches_oracle(precision, stride):
+    """The running peak of |u| per node and realisation (ens_set_peak) over 2000 steps of
+    the 40 x 40 tube against oracle.outputs.peak_magnitude on the same recorded steps,
+    within the trajectory tolerance of the form, relative to the largest peak; its row
+    statistics against the oracle's; graph replays and direct launches give the same
+    peak bit for bit; ens_reset clears it."""
+    from paper_2101_09059_gb300.ensemble import FLAG_NO_GRAPH, QTY_PEAK_MAGNITUDE
+    case = synth.make_case("tube_40x40", S=8, seed=5)
+    n = case["n_steps"]
+    ref, _, u_end = oo.peak_magnitude(oracle.Model(case), n, stride)
+    peaks = []
+    for flags in (0, FLAG_NO_GRAPH):
+        e = ens.Ensemble.from_case(case, precision=precision, flags=flags)
+        with pytest.raises(ens.EnsError) as ei:
+            e.quantity_device(QTY_PEAK_MAGNITUDE)
+        assert ei.value.code == -8
+        e.set_peak(stride)
+        for part in (1, 700, 299, n - 1000):
+            e.step(part)
+        p = e.quantity_device(QTY_PEAK_MAGNITUDE).cpu().numpy()
+        peaks.append(p)
+        err = np.abs(p - ref).max() / np.abs(ref).max()
+        print(f"peak {precision} stride {stride}: max rel {err:.2e}")
+        assert err < TOL[precision]
+        u = e.displacement()
+        assert np.linalg.norm(u - u_end) <= TOL[precision] * np.linalg.norm(u_end)
+        m, v, q = e.quantity_stats(QTY_PEAK_MAGNITUDE, Q)
+        mo, vo, qo = oo.row_stats(ref, Q)
+        assert np.abs(q - qo).max() <= TOL[precision] * np.abs(ref).max()
+        assert np.abs(m - mo).max() <= TOL[precision] * np.abs(ref).max()
+        e.reset()
+        assert not e.quantity_device(QTY_PEAK_MAGNITUDE).cpu().numpy().any()
+        e.close()
+    assert np.array_equal(peaks[0], peaks[1])
+
+
+def test_running_peak_members_cannot_join_a_batch():
+    case = synth.make_case("tube_small", S=4, n_steps=20)
+    a = ens.Ensemble.from_case(case, precision="kahan32")
+    b = ens.Ensemble.from_case(case, precision="kahan32")
+    a.set_peak(1)
+    with pytest.raises(ens.EnsError) as ei:
+        ens.Batch([a, b])
+    assert ei.value.code == -8
+    a.close()
+    b.close()
