@@ -7,8 +7,10 @@ of time steps: ens_step(chunk) (traction, internal force, fused update for every
 step) followed by the ensemble statistics of the new state.
 
 Prints one JSON line (rank 0). value = sample-steps/s of the headline form over all
-ranks; every rank runs its own S-sample ensemble (weak scaling, no data-path
-collective). --impl reference times the FP64 CPU oracle on the host cores instead.
+ranks; the ranks hold disjoint S-sample shards of one ensemble (weak scaling, no data-path
+collective; after the timed region the per-dof statistics of the shards are merged once,
+the method's one exchange). --impl reference times the FP64 CPU oracle on the host cores
+instead.
 """
 from __future__ import annotations
 
@@ -59,6 +61,8 @@ def parse():
                     help="use this step-kernel launch shape instead of autotuning (profiling)")
     ap.add_argument("--drift", action="store_true", help="long-run drift study instead of the benchmark")
     ap.add_argument("--drift-arch-elems", type=int, default=100_000)
+    ap.add_argument("--drift-studies", default="energy,aneurysm,arch",
+                    help="comma list of: energy, aneurysm, arch, arch_full")
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-val", type=int, default=512)
     ap.add_argument("--sur-epochs", type=int, default=400)
@@ -94,6 +98,17 @@ def max_over_ranks(x, world):
     dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
     t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def min_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
     return float(t.item())
 
 
@@ -614,6 +629,57 @@ def bench_surrogate(args, local, stream):
     return out
 
 
+def energy_drift(pkg, synth, name, stream, local, n_total, checkpoints):
+    """Discrete energy of undamped runs under a constant load: the central-difference
+    scheme conserves H_n = 1/2 d^T (M / dt^2 - K / 4) d + 1/2 w^T K w - f^T w exactly, with
+    d = u_{n+1} - u_n and w = (u_n + u_{n+1}) / 2 (Section 2.3, Eq. dynamicsCD with C = 0).
+    Each form's trajectory (4 realisations) is evaluated with the binary64 stiffness and
+    masses of a binary64 context (ens_internal_force, ens_get_coefficients); reported is
+    |H_n - H_0| over the largest of |kinetic|, |potential| and |f^T w|, per realisation, at
+    `checkpoints` points."""
+    base = synth.make_case(name, S=4, n_steps=2, seed=0, alpha=0.0)
+    # a constant load: the step pressure of the tube; the aneurysm's mean pressure and shear
+    row = {"tube_40x40": [1.0e4], "aneurysm": [1.07e4, 1.0]}[name]
+    amp = np.repeat(np.array([row], dtype=np.float64), n_total + 2, axis=0)
+    case = dict(base, amp=np.ascontiguousarray(amp), n_steps=n_total + 2)
+    ref = pkg.Ensemble.from_case(case, precision="fp64", stream=stream, device=local)
+    _, minv = ref.coefficients()
+    mass = (1.0 / minv)[:, None, :]                            # [N][1][S]
+    f = np.einsum("j,jnd->nd", case["amp"][0], case["modes"])[:, :, None]
+    dt = case["dt"]
+
+    def energy(u0, u1):
+        d, w = u1 - u0, 0.5 * (u0 + u1)
+        Kd, Kw = ref.internal_force(d), ref.internal_force(w)
+        kin = 0.5 * np.einsum("nds,nds->s", d, mass * d) / dt ** 2 - 0.125 * np.einsum("nds,nds->s", d, Kd)
+        pot = 0.5 * np.einsum("nds,nds->s", w, Kw)
+        work = np.einsum("nds,nds->s", f.repeat(w.shape[2], axis=2), w)
+        return kin + pot - work, np.maximum(np.maximum(np.abs(kin), np.abs(pot)), np.abs(work))
+
+    out = {"workload": f"{name}: {case['mesh'].n_nodes} nodes, 4 realisations, undamped, constant load, "
+                       f"{n_total} steps, dt {dt:.3e} s", "rel_drift": {}}
+    chunk = n_total // checkpoints
+    for form in ("fp64", "fp32_force", "kahan32"):
+        e = pkg.Ensemble.from_case(case, precision=form, stream=stream, device=local)
+        curve, H0, scale = [], None, None
+        for k in range(checkpoints + 1):
+            if k:
+                e.step(chunk - 1)
+            u0 = e.displacement("ncs")
+            e.step(1)
+            u1 = e.displacement("ncs")
+            H, sc = energy(u0, u1)
+            if H0 is None:
+                H0, scale = H, sc
+            scale = np.maximum(scale, sc)
+            curve.append(float(np.max(np.abs(H - H0) / scale)))
+        out["rel_drift"][form] = curve
+        e.close()
+    ref.close()
+    out["max_rel_drift"] = {f: max(c) for f, c in out["rel_drift"].items()}
+    return out
+
+
 def run_drift(args, local):
     """Drift of the binary32 forms against the binary64 GPU form over long runs, on the same
     4 realisations (realisations are independent, so a 4-sample ensemble steps each of them
@@ -625,9 +691,18 @@ def run_drift(args, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     out = {"drift": []}
-    studies = [("aneurysm", dict(name="aneurysm", S=64), [0, 21, 42, 63], 1),
-               ("arch", dict(name="arch", S=8, target_elems=args.drift_arch_elems), [0, 3, 5, 7], 3)]
-    for label, spec, picks, periods in studies:
+    want = set(args.drift_studies.split(","))
+    if "energy" in want:
+        out["energy"] = [energy_drift(pkg, synth, name, stream, local, n_total, 16)
+                         for name, n_total in (("tube_40x40", 200_000), ("aneurysm", 48_000))]
+    studies = []
+    if "aneurysm" in want:
+        studies.append(("aneurysm", dict(name="aneurysm", S=64), [0, 21, 42, 63], 1, None))
+    if "arch" in want:
+        studies.append(("arch", dict(name="arch", S=8, target_elems=args.drift_arch_elems), [0, 3, 5, 7], 3, None))
+    if "arch_full" in want:  # the configuration's size: 256 realisations, binary64 on 16 of them
+        studies.append(("arch_full", dict(name="arch", S=256), list(range(0, 256, 16)), 1, ("kahan32",)))
+    for label, spec, picks, periods, only in studies:
         name = spec.pop("name")
         base = synth.make_case(name, n_steps=2, seed=0, **spec)
         dt = base["dt"]
@@ -636,9 +711,13 @@ def run_drift(args, local):
         sub = dict(case, E=case["E"][:, picks], h=case["h"][:, picks], S=len(picks))
         checkpoints = 16
         chunk = n_total // checkpoints
-        ctxs = {f: pkg.Ensemble.from_case(sub, precision=f, stream=stream, device=local)
-                for f in ("fp64", "fp32_force", "kahan32")}
-        curve = {"fp32_force": [], "kahan32": []}
+        forms = only or ("fp32_force", "kahan32")
+        # the binary32 forms step every realisation of the case when `only` is given (the
+        # configuration's full width), the binary64 reference the picked subset
+        ctxs = {"fp64": pkg.Ensemble.from_case(sub, precision="fp64", stream=stream, device=local)}
+        for f in forms:
+            ctxs[f] = pkg.Ensemble.from_case(case if only else sub, precision=f, stream=stream, device=local)
+        curve = {f: [] for f in forms}
         t0 = time.perf_counter()
         for k in range(checkpoints):
             for e in ctxs.values():
@@ -646,12 +725,15 @@ def run_drift(args, local):
             ref = ctxs["fp64"].displacement()
             for f in curve:
                 u = ctxs[f].displacement()
+                if only:
+                    u = u[picks]
                 curve[f].append(float(np.linalg.norm(u - ref) / np.linalg.norm(ref)))
         for e in ctxs.values():
             e.close()
         m = case["mesh"]
         out["drift"].append({
-            "workload": f"{label}: {m.n_nodes} nodes, {m.n_elems} triangles, {len(picks)} realisations, "
+            "workload": f"{label}: {m.n_nodes} nodes, {m.n_elems} triangles, "
+                        f"{case['S'] if only else len(picks)} realisations ({len(picks)} against binary64), "
                         f"{periods} period(s) of 0.8 s, dt {dt:.3e} s, {chunk * checkpoints} steps",
             "steps_per_checkpoint": chunk,
             "rel_l2_vs_fp64_gpu": curve,
@@ -681,7 +763,11 @@ def main():
     forms = [f for f in args.forms.split(",") if f]
     K, W, C = args.steps, args.warmup, args.chunk
     n_steps = C * (W + K)
-    case = synth.make_case(args.workload, S=args.samples, n_steps=n_steps, seed=rank)
+    # one seeded ensemble of S x world realisations; rank r steps realisations
+    # [r S, (r + 1) S) with the time step of the ensemble's stiffest realisation
+    case = synth.make_case(args.workload, S=args.samples, n_steps=n_steps, seed=0, sample0=rank * args.samples)
+    if world > 1:
+        case = synth.configs.with_dt(args.workload, case, min_over_ranks(case["dt"], world))
     m = case["mesh"]
     N, S = m.n_nodes, args.samples
     stream = torch.cuda.current_stream(dev)
@@ -729,6 +815,8 @@ def main():
             res["achieved_tflops"] = flops / per_launch_s / 1e12
             res["fp64_frac"] = res["achieved_tflops"] / FP64_PEAK_TFLOPS
         finals[form] = e.displacement()
+        if form == (HEADLINE if HEADLINE in forms else forms[0]):
+            shard_stats = e.stats()      # this rank's per-dof mean and variance
         results[form] = res
         e.close()
         del mean, var
@@ -740,6 +828,19 @@ def main():
 
     head = HEADLINE if HEADLINE in results else forms[0]
     h = results[head]
+
+    # the method's one exchange: merge the ranks' per-dof statistics of the headline form
+    # into those of the whole ensemble (an all-gather over NCCL, then ens_merge_stats)
+    t0 = time.perf_counter()
+    if world > 1:
+        mean_all, var_all = pkg.ensemble.sharded_stats(S, shard_stats[0], shard_stats[1])
+    else:
+        mean_all, var_all = shard_stats
+    ensemble = {"realisations": S * world, "ranks": world, "form": head,
+                "merge": "all-gather of (count, mean, variance) per dof, ens_merge_stats" if world > 1
+                         else "single shard",
+                "merge_s": time.perf_counter() - t0,
+                "max_abs_mean_m": float(np.abs(mean_all).max()), "max_std_m": float(np.sqrt(var_all.max()))}
 
     # end to end through the public API with host buffers: every step streams this
     # chunk's load amplitudes from pinned host memory and reads the statistics back
@@ -799,8 +900,9 @@ def main():
                         f"pulsatile pressure + axial shear",
             "form": head, "time_steps_per_step": C, "dt_s": case["dt"],
             "l2": "inputs larger than L2 (state and coefficients > 129 MB per form)",
-            "parallelism": f"sample-sharded x{world}",
+            "parallelism": f"one ensemble of {S * world} realisations, sample-sharded x{world}",
         },
+        "ensemble": ensemble,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "peak_kind": peak_kind, "kernel": f"step_kernel<{head}>",

@@ -160,8 +160,11 @@ typedef struct {
                                the force loop, 8 and 9 persistent double-buffered
                                forms of 5 and 6, 10 and 11 the shapes of 6 and 4
                                staged from fixed-stride block records (binary32
-                               forms)                                             */
-    float variant_us[12];   /* autotuner's time per step of each shape (-1: n/a,
+                               forms), 12 and 13 the shapes of 6 and 5 with every
+                               neighbour row staged in shared memory from halo
+                               records, 14 halo-staged 128x6 with four samples
+                               per thread (binary32 forms)                        */
+    float variant_us[16];   /* autotuner's time per step of shapes 0..14 (-1: n/a,
                                0: not timed)                                      */
 } ens_info_t;
 
@@ -204,8 +207,32 @@ int ens_set_amplitudes(ens_ctx *ctx, int64_t first_row, int64_t n_rows, const do
  * displacement became Inf/NaN during these steps.                                    */
 int ens_step(ens_ctx *ctx, int64_t n);
 
-/* Back to rest: u = v = 0, step index 0.                                             */
+/* Back to rest: u = v = 0, step index 0 (with a geometry update, the per-realisation
+ * stiffness is re-assembled on the reference surface).                               */
 int ens_reset(ens_ctx *ctx);
+
+/* Geometry update with selective stiffness re-assembly (Section 2.3: the system
+ * M u'' + C u' + K(u) u = f, the lumen geometry updated by the displacement at every
+ * step, the stiffness re-assembled only after a prescribed number of iterations, the
+ * lumped mass and the traction history kept fixed). K(u) is the stiffness of the current
+ * surface applied to displacement increments: with k >= 1, at every step index m that is
+ * a multiple of k (after this call) each realisation's coupling blocks are re-assembled
+ * on its deformed surface X + u_s,m (scaled by the same (E h)_e,s), and the steps from m
+ * use f_int(u_n) = f_int(u_m) + K(X + u_m) (u_n - u_m). Before the first re-assembly the
+ * run is the linear method (bit for bit). k = 0 returns to the linear method and frees
+ * the per-realisation data: two block buffers of nnz * 18 * Sp values in the form's force
+ * precision (binary64 for ENS_FP64, binary32 otherwise) and the force correction
+ * f_int(u_m) - K_m u_m, N * 3 * Sp values in binary64 plus its force-precision copy.
+ * ens_reset and ens_set_state return to the linear stiffness with a zero correction (the
+ * checkpoint holds neither); ens_internal_force keeps the reference blocks. A step with
+ * per-realisation blocks streams them (72 B per incidence and sample in binary32)
+ * instead of the shared ones, several times the bytes of a linear step; a re-assembly
+ * costs one binary64 pass over the elements and samples and two force evaluations.
+ * Selective re-assembly (k > 1) uses the stiffness of a segment's start for the whole
+ * segment, a path error of order k. An element that degenerates on its deformed surface
+ * ends ens_step with ENS_ERR_NONFINITE. Contexts with a geometry update cannot join a
+ * batch.                                                                              */
+int ens_set_geometry_update(ens_ctx *ctx, int32_t k);
 
 /* Current displacements u_n as binary64. out: host array of S * n_nodes * 3 values in
  * the given ENS_LAYOUT_*.                                                             */

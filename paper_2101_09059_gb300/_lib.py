@@ -106,7 +106,7 @@ class ens_info_t(ctypes.Structure):
                 ("dt", ctypes.c_double), ("omega_lower", ctypes.c_double),
                 ("omega_upper", ctypes.c_double), ("bytes_per_step", ctypes.c_double),
                 ("device_bytes", ctypes.c_double), ("kernel_variant", ctypes.c_int32),
-                ("variant_us", ctypes.c_float * 12)]
+                ("variant_us", ctypes.c_float * 16)]
 
 
 class ens_batch_info_t(ctypes.Structure):
@@ -187,6 +187,7 @@ def load(build_if_missing: bool = True):
         "ens_row_stats_device": ([i64, i32, dp, i32, dp, dp, dp, dp, vp], ctypes.c_int),
         "ens_set_probes": ([vp, i32, dp, i32, dp, i32, i64], ctypes.c_int),
         "ens_set_peak": ([vp, i32], ctypes.c_int),
+        "ens_set_geometry_update": ([vp, i32], ctypes.c_int),
         "ens_get_probes": ([vp, dp, dp, dp, ctypes.POINTER(i64)], ctypes.c_int),
         "gmrf_create": ([i32, i32, dp, dp, ctypes.c_double, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "gmrf_sample": ([vp, i32, dp, dp, ctypes.c_double, ctypes.c_double, i32, ctypes.c_double, i32],

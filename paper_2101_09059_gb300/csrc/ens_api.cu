@@ -219,6 +219,78 @@ StagePlan record_plan(StagePlan p) {
     return p;
 }
 
+// The halo form of a staged plan (binary32 forms): for every block of nb nodes, the
+// distinct nodes its incidences touch (its own nodes first) and the distinct elements,
+// with every incidence re-expressed as slots into those lists. Fills the host records
+// (layout in StagePlan) and returns the plan, unstaged if the rows do not fit in shared
+// memory.
+StagePlan halo_plan(const ens_ctx *c, const std::vector<int32_t> &rowptr, const std::vector<int4> &ent,
+                    StagePlan base, std::vector<int4> *rec) {
+    StagePlan p = base;
+    p.staged = 0;
+    rec->clear();
+    if (!base.staged || c->form == kFP64) return p;
+    const int32_t N = c->N, nb = base.nb, Sp = c->Sp;
+    const int64_t nblk = (N + nb - 1) / nb;
+    std::vector<int32_t> nodes, elems;
+    auto slot = [](std::vector<int32_t> &v, int32_t id) -> int32_t {
+        for (size_t k = 0; k < v.size(); k++)
+            if (v[k] == id) return (int32_t)k;
+        v.push_back(id);
+        return (int32_t)v.size() - 1;
+    };
+    auto collect = [&](int64_t b) {
+        const int64_t n0 = b * nb, n1 = std::min<int64_t>(N, n0 + nb);
+        nodes.clear();
+        elems.clear();
+        for (int64_t i = n0; i < n1; i++) nodes.push_back((int32_t)i);
+        for (int32_t q = rowptr[n0]; q < rowptr[n1]; q++) {
+            slot(elems, ent[q].x);
+            slot(nodes, ent[q].y);
+            slot(nodes, ent[q].z);
+        }
+    };
+    int32_t hmax = 0, hemax = 0;
+    for (int64_t b = 0; b < nblk; b++) {
+        collect(b);
+        hmax = std::max<int32_t>(hmax, (int32_t)nodes.size());
+        hemax = std::max<int32_t>(hemax, (int32_t)elems.size());
+    }
+    p.rec = 1;
+    p.halo = 1;
+    p.h_max = hmax;
+    p.he_max = hemax;
+    p.rec_h = (nb + 3 + 3) / 4;
+    const int32_t hn4 = (hmax + 3) & ~3, he4 = (hemax + 3) & ~3;
+    p.halo_w = (hn4 + he4) / 4;
+    const int64_t words = (int64_t)p.rec_h + p.halo_w + p.cnt_max;
+    const size_t bytes = 16 + (size_t)words * 16 + (size_t)p.cnt_max * 80 + (size_t)hmax * 3 * Sp * 4 +
+                         (size_t)hemax * Sp * 4;
+    if (bytes > 200 * 1024) return p;
+    p.smem = (uint32_t)((bytes + 127) / 128 * 128);
+    rec->assign((size_t)(nblk * words), make_int4(0, 0, 0, 0));
+    for (int64_t b = 0; b < nblk; b++) {
+        collect(b);
+        const int64_t n0 = b * nb, n1 = std::min<int64_t>(N, n0 + nb);
+        int4 *r = rec->data() + b * words;
+        int32_t *hdr = reinterpret_cast<int32_t *>(r);
+        const int32_t pb = rowptr[n0];
+        for (int32_t k = 0; k <= nb; k++) hdr[k] = rowptr[std::min<int64_t>(n0 + k, n1)] - pb;
+        hdr[nb + 1] = (int32_t)nodes.size();
+        hdr[nb + 2] = (int32_t)elems.size();
+        int32_t *ids = reinterpret_cast<int32_t *>(r + p.rec_h);
+        for (size_t k = 0; k < nodes.size(); k++) ids[k] = nodes[k];
+        for (size_t k = 0; k < elems.size(); k++) ids[hn4 + k] = elems[k];
+        int4 *en = r + p.rec_h + p.halo_w;
+        for (int32_t q = pb; q < rowptr[n1]; q++) {
+            const int4 g = ent[q];
+            en[q - pb] = make_int4(slot(elems, g.x), slot(nodes, g.y), slot(nodes, g.z), g.w);
+        }
+    }
+    p.staged = 1;
+    return p;
+}
+
 // The pipelined (persistent, double-buffered) form of a staged plan.
 StagePlan pipelined_plan(StagePlan p) {
     if (!p.staged) return p;
@@ -347,6 +419,40 @@ cudaError_t ctx_launch_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s) {
     return launch_chunk_step(c, k, start, s);
 }
 void ctx_free(ens_ctx *c, void *p) { dev_free(c, p); }
+
+// Re-assembly on the current state u_m: the new per-realisation blocks go to the other
+// buffer, the correction takes f_int(u_m) under the old stiffness minus K_new u_m, and the
+// new blocks become current.
+int geometry_reassemble(ens_ctx *c) {
+    const void *aux = c->form == kFP32Force ? (const void *)c->utail : (const void *)c->ulo;
+    const int next = c->geo_active ? c->kcs_cur ^ 1 : c->kcs_cur;
+    CK(launch_reassemble(c->form, c->xyz_d, c->tri_d, c->ec2ent_d, c->E, c->Sp, c->nu, c->ks, c->ug[c->cur], aux,
+                         c->kcs[next], c->flags, c->stream));
+    if (c->form == kFP64) {
+        StepArgs<double> a = make_args<double>(c);
+        a.ug_cur = (const double *)c->ug[c->cur];
+        CK(launch_geo_correct<double>(a, c->geo_active ? (const double *)c->kcs[c->kcs_cur] : nullptr,
+                                      (const double *)c->kcs[next], c->geo_c64, (double *)c->geo_cR, c->stream));
+    } else {
+        StepArgs<float> a = make_args<float>(c);
+        a.ug_cur = (const float *)c->ug[c->cur];
+        CK(launch_geo_correct<float>(a, c->geo_active ? (const float *)c->kcs[c->kcs_cur] : nullptr,
+                                     (const float *)c->kcs[next], c->geo_c64, (float *)c->geo_cR, c->stream));
+    }
+    c->kcs_cur = next;
+    c->geo_active = true;
+    return ENS_OK;
+}
+
+// Back to the linear stiffness and a zero correction (rest, or a restored checkpoint).
+int geometry_restart(ens_ctx *c) {
+    c->geo_active = false;
+    c->kcs_cur = 0;
+    const size_t n = (size_t)c->N * 3 * c->Sp;
+    CK(cudaMemsetAsync(c->geo_c64, 0, 8 * n, c->stream));
+    if (c->geo_cR != c->geo_c64) CK(cudaMemsetAsync(c->geo_cR, 0, elem_size(c->form) * n, c->stream));
+    return ENS_OK;
+}
 }  // namespace ens
 
 extern "C" {
@@ -552,6 +658,11 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                     cand[10] = record_plan(cand[6]);
                     cand[11] = record_plan(cand[4]);
                     if (cand[11].nb != cand[10].nb) cand[11].staged = 0;
+                    // every neighbour row staged from halo records: shapes of 6 and 5,
+                    // and 128 x 8 with four samples per thread
+                    cand[12] = cand[6];
+                    cand[13] = cand[5];
+                    if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 128, 6, &cand[14], 4);
                 }
             }
             if (rcp != ENS_OK) return rcp;
@@ -593,6 +704,43 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                 cand[k].rec_kc = c->rec_kc;
             }
             if (c->plan.rec) c->plan = cand[c->variant];  // a forced record shape
+        }
+        // halo records: one set per distinct block size among shapes 12..14
+        {
+            int hs = 0;
+            int32_t nb_of[2] = {0, 0};
+            for (int k = 12; k <= 14; k++) {
+                if (!cand[k].staged || cand[k].halo) continue;
+                std::vector<int4> hrec;
+                StagePlan hp = halo_plan(c, rowptr, ent, cand[k], &hrec);
+                int set = -1;
+                for (int q = 0; q < hs; q++)
+                    if (nb_of[q] == hp.nb) set = q;
+                if (hp.staged && set < 0 && hs < 2) {
+                    set = hs++;
+                    nb_of[set] = hp.nb;
+                    const int64_t nblk = (N + hp.nb - 1) / hp.nb;
+                    c->halo_ent[set] = (int4 *)dev_alloc(c, sizeof(int4) * hrec.size());
+                    c->halo_kc[set] = dev_alloc(c, sizeof(float) * (size_t)nblk * hp.cnt_max * 20);
+                    if (!c->halo_ent[set] || !c->halo_kc[set]) return fail(c, ENS_ERR_ALLOC, "halo records");
+                    CK(cudaMemcpyAsync(c->halo_ent[set], hrec.data(), sizeof(int4) * hrec.size(),
+                                       cudaMemcpyHostToDevice, c->stream));
+                    CK(launch_pack_records((const float *)c->kc, c->rowptr, N, hp.nb, hp.cnt_max,
+                                           (float *)c->halo_kc[set], c->stream));
+                    CK(cudaStreamSynchronize(c->stream));  // the host records leave scope
+                }
+                if (hp.staged && set >= 0) {
+                    hp.rec_ent = c->halo_ent[set];
+                    hp.rec_kc = c->halo_kc[set];
+                    cand[k] = hp;
+                } else {
+                    cand[k].staged = 0;
+                }
+            }
+            if (forced_v >= 12) {
+                c->plan = cand[forced_v];
+                c->variant = c->plan.staged ? forced_v : 0;
+            }
         }
         CK(launch_convert(m64, NSp, c->minv, to_f, 1, c->stream));
         if (to_f) {
@@ -667,12 +815,19 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
             rc0 = autotune(c, cand, kVariants);
             if (rc0 != ENS_OK) return rc0;
         }
-        if (!c->plan.rec && c->rec_ent) {  // the records serve no chosen shape
+        if (!(c->plan.rec && !c->plan.halo) && c->rec_ent) {  // the records serve no chosen shape
             dev_free(c, c->rec_ent);
             dev_free(c, c->rec_kc);
             c->rec_ent = nullptr;
             c->rec_kc = nullptr;
         }
+        for (int q = 0; q < 2; q++)
+            if (c->halo_ent[q] && !(c->plan.halo && c->plan.rec_ent == c->halo_ent[q])) {
+                dev_free(c, c->halo_ent[q]);
+                dev_free(c, c->halo_kc[q]);
+                c->halo_ent[q] = nullptr;
+                c->halo_kc[q] = nullptr;
+            }
         return ens_reset(c);
     }();
     if (rc != ENS_OK) {
@@ -704,6 +859,11 @@ int ens_reset(ens_ctx *c) {
     c->started = false;
     c->probe_rec = 0;
     c->probe_steps.clear();
+    if (c->geo_k > 0) {  // the linear stiffness until the first re-assembly
+        int rc = geometry_restart(c);
+        if (rc != ENS_OK) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+    }
     return ENS_OK;
 }
 
@@ -788,7 +948,8 @@ int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
     if (n < 2 * K || !c->started || (c->flags_in & ENS_FLAG_NO_GRAPH)) return ENS_OK;
     std::vector<uintptr_t> key = {(uintptr_t)(c->cur & 1), (uintptr_t)c->amp, (uintptr_t)c->modes,
                                   (uintptr_t)c->J, (uintptr_t)c->variant, (uintptr_t)c->plan.staged,
-                                  (uintptr_t)c->peak, (uintptr_t)c->peak_stride};
+                                  (uintptr_t)c->peak, (uintptr_t)c->peak_stride,
+                                  (uintptr_t)(c->geo_active ? c->kcs[c->kcs_cur] : nullptr)};
     if (!c->graph || c->graph_key != key) {
         if (c->graph) cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
@@ -851,20 +1012,29 @@ int ens_step(ens_ctx *c, int64_t n) {
     if (n == 0) return ENS_OK;
     if (n > INT32_MAX) return fail(c, ENS_ERR_INVALID_ARG, "n too large for one call");
     CK(cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream));
-    // with probes, advance in segments that end on the recording steps
+    // with probes or a geometry update, advance in segments that end on the recording
+    // and re-assembly steps
     int64_t left = n;
     while (left > 0) {
         int64_t seg = left;
         if (c->probe_stride > 0) seg = std::min(left, c->probe_stride - c->step % c->probe_stride);
+        if (c->geo_k > 0) seg = std::min(seg, c->geo_k - c->step % c->geo_k);
         int rc = advance(c, seg);
         if (rc != ENS_OK) return rc;
         c->step += seg;
         left -= seg;
         rc = probe_record(c);
         if (rc != ENS_OK) return rc;
+        if (c->geo_k > 0 && c->step % c->geo_k == 0) {
+            rc = geometry_reassemble(c);
+            if (rc != ENS_OK) return rc;
+        }
     }
     CK(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (c->h_flags[0] & 8)
+        return fail(c, ENS_ERR_NONFINITE, "an element degenerated on the deformed surface before step %lld",
+                    (long long)c->step);
     if (c->h_flags[0] & 4)
         return fail(c, ENS_ERR_CUDA, "a staged block found its launch plan inconsistent");
     if (c->h_flags[0] & 2)
@@ -872,6 +1042,42 @@ int ens_step(ens_ctx *c, int64_t n) {
     if (c->h_flags[0] & 1)
         return fail(c, ENS_ERR_NONFINITE, "displacement became Inf/NaN before step %lld",
                     (long long)c->step);
+    return ENS_OK;
+}
+
+int ens_set_geometry_update(ens_ctx *c, int32_t k) {
+    if (!c) return ENS_ERR_INVALID_ARG;
+    if (k < 0) return fail(c, ENS_ERR_INVALID_ARG, "k = %d", k);
+    CK(cudaStreamSynchronize(c->stream));
+    c->geo_k = 0;
+    c->geo_active = false;
+    c->kcs_cur = 0;
+    if (k == 0) {
+        for (int q = 0; q < 2; q++) {
+            dev_free(c, c->kcs[q]);
+            c->kcs[q] = nullptr;
+        }
+        if (c->geo_cR != c->geo_c64) dev_free(c, c->geo_cR);
+        dev_free(c, c->geo_c64);
+        c->geo_c64 = nullptr;
+        c->geo_cR = nullptr;
+        return ENS_OK;
+    }
+    const size_t n = (size_t)c->N * 3 * c->Sp;
+    for (int q = 0; q < 2; q++)
+        if (!c->kcs[q]) {
+            c->kcs[q] = dev_alloc(c, elem_size(c->form) * (size_t)c->nnz * 18 * c->Sp);
+            if (!c->kcs[q]) return fail(c, ENS_ERR_ALLOC, "per-realisation coupling blocks");
+        }
+    if (!c->geo_c64) {
+        c->geo_c64 = (double *)dev_alloc(c, 8 * n);
+        c->geo_cR = c->form == kFP64 ? (void *)c->geo_c64 : dev_alloc(c, 4 * n);
+        if (!c->geo_c64 || !c->geo_cR) return fail(c, ENS_ERR_ALLOC, "geometry-update force correction");
+    }
+    int rc = geometry_restart(c);
+    if (rc != ENS_OK) return rc;
+    c->geo_k = k;
+    CK(cudaStreamSynchronize(c->stream));
     return ENS_OK;
 }
 
@@ -1107,6 +1313,11 @@ int ens_set_state(ens_ctx *c, const void *buf, size_t bytes) {
     CK(cudaStreamSynchronize(c->stream));
     c->step = h.step;
     c->started = h.started != 0;
+    if (c->geo_k > 0) {  // the checkpoint holds no re-assembled stiffness
+        int rc = geometry_restart(c);
+        if (rc != ENS_OK) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+    }
     return ENS_OK;
 }
 

@@ -408,7 +408,7 @@ int ens_batch_create(ens_ctx *const *members, int32_t n, int32_t mode, ens_batch
             if (members[j] == members[k]) return ENS_ERR_INVALID_ARG;
         if (members[k]->form != members[0]->form || members[k]->device != members[0]->device)
             return ENS_ERR_INVALID_ARG;
-        if (members[k]->peak) return ENS_ERR_STATE;  // running peaks are per-context only
+        if (members[k]->peak || members[k]->geo_k) return ENS_ERR_STATE;  // per-context features only
     }
     ens_batch *b = new (std::nothrow) ens_batch();
     if (!b) return ENS_ERR_ALLOC;
@@ -474,7 +474,8 @@ int ens_batch_step(ens_batch *b, int64_t n) {
     if (n < 0) return bfail(b, ENS_ERR_INVALID_ARG, "n < 0");
     for (ens_ctx *c : b->m) {
         if (c->J == 0) return bfail(b, ENS_ERR_STATE, "a member has no traction table");
-        if (c->peak) return bfail(b, ENS_ERR_STATE, "a member tracks a running peak (not in batched launches)");
+        if (c->peak || c->geo_k)
+            return bfail(b, ENS_ERR_STATE, "a member tracks a running peak or updates its geometry (not in batches)");
         if (c->step + n > c->n_amp) return bfail(b, ENS_ERR_RANGE, "a member's traction table is too short");
     }
     if (n == 0) return ENS_OK;

@@ -9,7 +9,7 @@
 #include "ens_internal.cuh"
 
 namespace ens {
-constexpr int kVariants = 12;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kVariants = 15;  // launch shapes the autotuner can time (see ens_info_t)
 constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
 }
 
@@ -48,6 +48,8 @@ struct ens_ctx {
     ens::StagePlan plan_fo{};  // launch shape of force-only evaluations
     int4 *rec_ent = nullptr;     // fixed-stride block records (record shapes only)
     void *rec_kc = nullptr;
+    int4 *halo_ent[2] = {nullptr, nullptr};  // halo records of the halo shapes (two block sizes)
+    void *halo_kc[2] = {nullptr, nullptr};
     int32_t variant = 0;
     float variant_us[ens::kVariants] = {};
     int32_t flags_in = 0;
@@ -70,6 +72,17 @@ struct ens_ctx {
     // running peak of |u| per node and sample [N][Sp] (ens_set_peak)
     double *peak = nullptr;
     int32_t peak_stride = 0;
+    // geometry update (ens_set_geometry_update): per-realisation coupling blocks
+    // [nnz][18][Sp] of the deformed surface (two buffers: old and new during a
+    // re-assembly), re-assembled every geo_k steps, and the force correction
+    // c = f_int(u_m) - K_m u_m [N][3][Sp] in binary64 and in the force precision.
+    // Until the first re-assembly (geo_active false) the linear kernels run.
+    void *kcs[2] = {nullptr, nullptr};
+    int32_t kcs_cur = 0;
+    bool geo_active = false;
+    double *geo_c64 = nullptr;
+    void *geo_cR = nullptr;
+    int32_t geo_k = 0;
 };
 
 
@@ -83,6 +96,9 @@ void ctx_free(ens_ctx *c, void *p);
 cudaError_t ctx_launch_step(ens_ctx *c, int32_t k, bool start, cudaStream_t s);
 // Record the probes if the current step is due (ens_outputs.cu).
 int probe_record(ens_ctx *c);
+// Re-assemble the per-realisation coupling blocks on the current state (ens_api.cu).
+int geometry_reassemble(ens_ctx *c);
+int geometry_restart(ens_ctx *c);
 inline size_t elem_size(int form) { return form == kFP64 ? 8 : 4; }
 
 template <typename R>
@@ -108,6 +124,8 @@ StepArgs<R> make_args(ens_ctx *c) {
     a.dt = c->dt;
     a.dtf = (float)c->dt;
     a.flags = c->flags;
+    a.kcs = c->geo_active ? (const R *)c->kcs[c->kcs_cur] : nullptr;
+    a.kcorr = c->geo_active ? (const R *)c->geo_cR : nullptr;
     return a;
 }
 

@@ -66,6 +66,8 @@ struct StepArgs {
     double c1, c2, dt;  // v_new = c1 v + c2 a ; u_new = u + dt v_new
     float c1f, c2f, dtf;  // the same constants rounded to binary32 (binary32 forms)
     double *force_out;  // force-only mode: [N][3][Sp] binary64
+    const R *kcs;       // geometry update: per-realisation coupling blocks [nnz][18][Sp]
+    const R *kcorr;     // geometry update: force correction f_int(u_m) - K_m u_m [N][3][Sp]
     int *flags;         // [0] bit 0: non-finite seen, bit 1: a bounded wait gave up
 };
 
@@ -94,6 +96,15 @@ struct StagePlan {
     int32_t rec_h;
     const int4 *rec_ent;
     const void *rec_kc;
+    // Halo records (halo = 1, binary32 forms, with rec = 1): block b's record holds rec_h
+    // header words (the nb + 1 block-local row offsets, then the counts of distinct halo
+    // nodes and elements), halo_w words of halo ids (h_max node ids with the block's own
+    // nodes first, then he_max element ids, each list padded to a multiple of 4), and
+    // cnt_max entries {element slot, node slot a, node slot b, corner} whose slots index
+    // the block's staged halo rows. The block copies those rows into shared memory once
+    // (cp.async by every thread), so its force loop reads shared memory only.
+    int32_t halo;
+    int32_t h_max, he_max, halo_w;
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or
@@ -150,6 +161,13 @@ cudaError_t launch_export(int form, const void *u_main, const void *aux, int32_t
                           int32_t Sp, double *out, int layout, cudaStream_t s);
 cudaError_t launch_import(int form, const double *in_ncs, int32_t N, int32_t S, int32_t Sp,
                           void *ug, cudaStream_t s);
+// Geometry update: c64 += K_old u - K_new u per realisation (the internal forces of the
+// state a.ug_cur under the old blocks, per-realisation kcs_old or the shared ones when
+// null, and the new per-realisation blocks kcs_new), cR = c64 rounded to the force
+// precision.
+template <typename R>
+cudaError_t launch_geo_correct(const StepArgs<R> &a, const R *kcs_old, const R *kcs_new, double *c64, R *cR,
+                               cudaStream_t s);
 
 // Setup launchers (ens_setup.cu).
 cudaError_t launch_setup_elements(const double *xyz, const int32_t *tri, const int32_t *ec2ent,
@@ -173,6 +191,12 @@ cudaError_t launch_setup_mass_elem(const int32_t *rowptr, const int4 *ent, const
                                    const double *rhoh, int32_t N, int32_t Sp, double *m64, cudaStream_t s);
 cudaError_t launch_modulus_from_coeffs(const double *eh64, const double *rhoh, int64_t n, double rho,
                                        double *ebar, cudaStream_t s);
+// Geometry update (ens_setup.cu): per-realisation coupling blocks kcs [nnz][18][Sp] of the
+// deformed surface xyz + u (u the state of the given form); bit 3 of *flags for an
+// element that degenerated.
+cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, const int32_t *ec2ent, int32_t E,
+                              int32_t Sp, double nu, double kshear, const void *u_main, const void *aux, void *kcs,
+                              int *flags, cudaStream_t s);
 cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
                            cudaStream_t s);
 // Binary32 coupling blocks (stride 20) into fixed-stride block records of nb nodes and

@@ -19,6 +19,7 @@
 // There are no atomics in the force path: every node sums its own incidences in list
 // order, so results are bitwise reproducible.
 #include <cstdio>
+#include <utility>
 
 #include "ens_bits.cuh"
 #include "ens_internal.cuh"
@@ -254,10 +255,11 @@ __device__ __forceinline__ void step_traction(const StepArgs<R> &a, int32_t i, R
     node_traction<R>(a, i, *a.step_ctr + a.k_off, fe);
 }
 
-// The fused update of node i, samples [s0, s0 + V): a = (f_ext - f_int) / m, then the
-// velocity form of Eq. (dynamicsCD) with the fixed-dof mask, stored per form.
+// The fused update of node i, samples [s0, s0 + V), one dof after the other (the shapes
+// with two samples per thread, whose 48-register budget the loads of all three dofs at
+// once would spill).
 template <int FORM, typename R, int V>
-__device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int32_t s0,
+__device__ __forceinline__ void node_update_per_dof(const StepArgs<R> &a, int32_t i, int32_t s0,
                                             const R (&ui)[3][V], const R (&f)[3][V],
                                             const R (&fe)[3]) {
     const int64_t Sp = a.fv.Sp;
@@ -352,6 +354,139 @@ __device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int
     if (bad) atomicOr(a.flags, 1);
 }
 
+// The fused update of node i, samples [s0, s0 + V): a = (f_ext - f_int) / m, then the
+// velocity form of Eq. (dynamicsCD) with the fixed-dof mask, stored per form. Here every
+// state word of the three dofs is loaded before the first store: the stores and the later
+// dofs' loads go to different arrays, which the compiler cannot prove, so loading per dof
+// serialises three round trips to memory.
+template <int FORM, typename R, int V>
+__device__ __forceinline__ void node_update_hoisted(const StepArgs<R> &a, int32_t i, int32_t s0,
+                                            const R (&ui)[3][V], const R (&f)[3][V],
+                                            const R (&fe)[3]) {
+    const int64_t Sp = a.fv.Sp;
+    R mi[V];
+    ld_nc(a.minv + (int64_t)i * Sp + s0, mi);
+    const unsigned fx = __ldg(a.fix + i);
+    const int64_t row0 = (int64_t)i * 3 * Sp + s0;
+    bool bad = false;
+    if constexpr (FORM == kFP64) {
+        double vv[3][V];
+#pragma unroll
+        for (int d = 0; d < 3; d++) ld_cs(a.v64 + row0 + d * Sp, vv[d]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const bool held = (fx >> d) & 1u;
+            const int64_t row = row0 + d * Sp;
+            double un[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const double acc = (fe[d] - f[d][v]) * mi[v];
+                const double vn = held ? 0.0 : fma(a.c1, vv[d][v], a.c2 * acc);
+                un[v] = held ? 0.0 : fma(a.dt, vn, ui[d][v]);
+                vv[d][v] = vn;
+                bad |= !isfinite(un[v]);
+            }
+            st_cs(a.v64 + row, vv[d]);
+            st_wb(a.ug_next + row, un);
+        }
+    } else if constexpr (FORM == kFP32Force) {
+        // binary64 u = (head ui, tail); the update runs in binary64, the bit splits and
+        // the conversion of the binary32 velocity increment on the integer pipe. A held
+        // dof is the same for every sample of the node, so the branch is uniform across
+        // the node's threads; the state words are read whether or not the dof is held.
+        double vv[3][V];
+        uint32_t tl[3][V];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            ld_cs(a.utail + row0 + d * Sp, tl[d]);
+#pragma unroll
+            for (int q = 0; q < V; q += 2) {
+                double h2[2];
+                ld_cs(a.v64 + row0 + d * Sp + q, h2);
+                vv[d][q] = h2[0];
+                vv[d][q + 1] = h2[1];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const bool held = (fx >> d) & 1u;
+            const int64_t row = row0 + d * Sp;
+            float ug[V];
+            if (held) {
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    vv[d][v] = 0.0;
+                    tl[d][v] = 0u;
+                    ug[v] = 0.0f;
+                }
+            } else {
+                const float c2 = a.c2f;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const float acc = (fe[d] - f[d][v]) * mi[v];
+                    const double vn = fma(a.c1, vv[d][v], f32_to_f64_ftz(c2 * acc));
+                    const double un = fma(a.dt, vn, join_state(ui[d][v], tl[d][v]));
+                    vv[d][v] = vn;
+                    bad |= !split_state(un, ug[v], tl[d][v]);
+                }
+            }
+            st_cs(a.utail + row, tl[d]);
+#pragma unroll
+            for (int q = 0; q < V; q += 2) st_cs(a.v64 + row + q, {vv[d][q], vv[d][q + 1]});
+            st_wb(a.ug_next + row, ug);
+        }
+    } else {  // kKahan32
+        float lo[3][V], vv[3][V];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            ld_cs(a.ulo + row0 + d * Sp, lo[d]);  // read whether or not held, as above
+            ld_cs(a.v32 + row0 + d * Sp, vv[d]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const bool held = (fx >> d) & 1u;
+            const int64_t row = row0 + d * Sp;
+            float hi[V];
+            if (held) {  // uniform across the node's threads
+#pragma unroll
+                for (int v = 0; v < V; v++) lo[d][v] = vv[d][v] = hi[v] = 0.0f;
+            } else {
+                const float c1 = a.c1f, c2 = a.c2f, dt = a.dtf;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const float acc = (fe[d] - f[d][v]) * mi[v];
+                    const float vn = fmaf(c1, vv[d][v], c2 * acc);
+                    // (hi, lo) += dt * vn as an error-free sum of hi and the small part.
+                    const float y = fmaf(dt, vn, lo[d][v]);
+                    const float sum = ui[d][v] + y;
+                    const float bb = sum - ui[d][v];
+                    hi[v] = sum;
+                    lo[d][v] = (ui[d][v] - (sum - bb)) + (y - bb);
+                    vv[d][v] = vn;
+                    bad |= !isfinite(sum);
+                }
+            }
+            st_cs(a.ulo + row, lo[d]);
+            st_cs(a.v32 + row, vv[d]);
+            st_wb(a.ug_next + row, hi);
+        }
+    }
+    if (bad) atomicOr(a.flags, 1);
+}
+
+// The update used by every step kernel: the three dofs' loads issued together where the
+// shape has the registers for them (four samples per thread), one dof after the other
+// otherwise. Both evaluate the same operations (bitwise identical results).
+template <int FORM, typename R, int V>
+__device__ __forceinline__ void node_update(const StepArgs<R> &a, int32_t i, int32_t s0,
+                                            const R (&ui)[3][V], const R (&f)[3][V],
+                                            const R (&fe)[3]) {
+    if constexpr (V >= 4)
+        node_update_hoisted<FORM, R, V>(a, i, s0, ui, f, fe);
+    else
+        node_update_per_dof<FORM, R, V>(a, i, s0, ui, f, fe);
+}
+
 template <typename R, int V>
 __device__ __forceinline__ void store_force(const StepArgs<R> &a, int32_t i, int32_t s0,
                                             const R (&f)[3][V]) {
@@ -383,6 +518,114 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
         store_force<R, V>(a, i, s0, f);
     else
         node_update<FORM, R, V>(a, i, s0, ui, f, fe);
+}
+
+// Geometry update (Section 2.3, K(u) re-assembled on the deformed surface): the internal
+// force with per-realisation coupling blocks kcs [nnz][18][Sp], the same operations in
+// the same order as node_force, the 18 coefficients read per sample (six at a time).
+template <typename R, int V>
+__device__ __forceinline__ void node_force_geom(const ForceView<R> &w, const R *__restrict__ kcs,
+                                                const R *__restrict__ ug, int32_t i, int32_t s0,
+                                                const R (&ui)[3][V], R (&f)[3][V]) {
+    const int64_t Sp = w.Sp;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int v = 0; v < V; v++) f[d][v] = R(0);
+    const GatherBase<R> g(ug, w.eh, (int32_t)Sp, s0);
+    const int32_t p0 = __ldg(w.rowptr + i);
+    const int32_t p1 = __ldg(w.rowptr + i + 1);
+    for (int32_t p = p0; p < p1; ++p) {
+        const int4 en = __ldg(w.ent + p);
+        R ua[3][V], ub[3][V], e[V];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            ld_nc(g.row(en.y, d), ua[d]);
+            ld_nc(g.row(en.z, d), ub[d]);
+        }
+        ld_nc(g.ehrow(en.x), e);
+        const R *kp = kcs + (int64_t)p * 18 * Sp + s0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            R k0[V], k1[V], k2[V], k3[V], k4[V], k5[V];
+            ld_nc(kp + (3 * d) * Sp, k0);
+            ld_nc(kp + (3 * d + 1) * Sp, k1);
+            ld_nc(kp + (3 * d + 2) * Sp, k2);
+            ld_nc(kp + (9 + 3 * d) * Sp, k3);
+            ld_nc(kp + (9 + 3 * d + 1) * Sp, k4);
+            ld_nc(kp + (9 + 3 * d + 2) * Sp, k5);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const R a0 = ua[0][v] - ui[0][v], a1 = ua[1][v] - ui[1][v], a2 = ua[2][v] - ui[2][v];
+                const R b0 = ub[0][v] - ui[0][v], b1 = ub[1][v] - ui[1][v], b2 = ub[2][v] - ui[2][v];
+                R t = k0[v] * a0;
+                t = fma(k1[v], a1, t);
+                t = fma(k2[v], a2, t);
+                t = fma(k3[v], b0, t);
+                t = fma(k4[v], b1, t);
+                t = fma(k5[v], b2, t);
+                f[d][v] = fma(e[v], t, f[d][v]);
+            }
+        }
+    }
+}
+
+template <int FORM, typename R, int V = Vw<R>::V>
+__global__ void __launch_bounds__(kBlock) step_geom_kernel(const StepArgs<R> a) {
+    const int32_t Q = a.fv.Q;
+    const int64_t Sp = a.fv.Sp;
+    const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (g >= (int64_t)a.fv.N * Q) return;
+    const int32_t i = (int32_t)(g / Q);
+    const int32_t s0 = (int32_t)(g - (int64_t)i * Q) * V;
+    R fe[3] = {R(0), R(0), R(0)};
+    step_traction<R>(a, i, fe);
+    R ui[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++) ld_nc(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
+    R f[3][V];
+    node_force_geom<R, V>(a.fv, a.kcs, a.ug_cur, i, s0, ui, f);
+    // f_int(u_n) = K_m u_n + (f_int(u_m) - K_m u_m)
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        R cv[V];
+        ld_nc(a.kcorr + ((int64_t)i * 3 + d) * Sp + s0, cv);
+#pragma unroll
+        for (int v = 0; v < V; v++) f[d][v] += cv[v];
+    }
+    node_update<FORM, R, V>(a, i, s0, ui, f, fe);
+}
+
+// Geometry update, at a re-assembly on the state u = a.ug_cur: c64 += K_old u - K_new u,
+// each force evaluated as the step evaluates it (shared blocks when kcs_old is null).
+template <typename R, int V = Vw<R>::V>
+__global__ void __launch_bounds__(kBlock) geo_correct_kernel(const StepArgs<R> a, const R *__restrict__ kcs_old,
+                                                             const R *__restrict__ kcs_new, double *__restrict__ c64,
+                                                             R *__restrict__ cR) {
+    const int32_t Q = a.fv.Q;
+    const int64_t Sp = a.fv.Sp;
+    const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    if (g >= (int64_t)a.fv.N * Q) return;
+    const int32_t i = (int32_t)(g / Q);
+    const int32_t s0 = (int32_t)(g - (int64_t)i * Q) * V;
+    R ui[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++) ld_nc(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
+    R fo[3][V], fn[3][V];
+    if (kcs_old)
+        node_force_geom<R, V>(a.fv, kcs_old, a.ug_cur, i, s0, ui, fo);
+    else
+        node_force<R, V>(a.fv, a.ug_cur, i, s0, ui, fo);
+    node_force_geom<R, V>(a.fv, kcs_new, a.ug_cur, i, s0, ui, fn);
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const int64_t idx = ((int64_t)i * 3 + d) * Sp + s0 + v;
+            const double c = c64[idx] + ((double)fo[d][v] - (double)fn[d][v]);
+            c64[idx] = c;
+            cR[idx] = (R)c;
+        }
 }
 
 // Staged kernel. Block b owns nodes [b nb, b nb + nb). One thread issues bulk copies
@@ -443,6 +686,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     R *kc_s = reinterpret_cast<R *>(ent_s + cnt_max);
     R *ug_s = kc_s + (size_t)cnt_max * KS;
 
+    grid_launch_dependents();  // the next step's blocks may stage their records early
     const int32_t Q = a.fv.Q;
     const int64_t Sp = a.fv.Sp;
     const int32_t N = a.fv.N;
@@ -476,6 +720,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
         const uint32_t b_ent = (uint32_t)(hw + cnt) * 16u;
         const uint32_t b_kc = (uint32_t)cnt * KS * (uint32_t)sizeof(R);
         mbar_expect_tx(bar, b_ent + b_kc + row_bytes);
+        // the incidence records never change: staged before the previous step ends
         if constexpr (REC) {
             bulk_g2s(rec_s, pl.rec_ent + (size_t)blockIdx.x * (hw + cnt_max), b_ent, bar);
             bulk_g2s(kc_s, static_cast<const R *>(pl.rec_kc) + (size_t)blockIdx.x * cnt_max * KS, b_kc, bar);
@@ -483,6 +728,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
             bulk_g2s(ent_s, a.fv.ent + pb, b_ent, bar);
             bulk_g2s(kc_s, a.fv.kc + (size_t)pb * KS, b_kc, bar);
         }
+    }
+    grid_dependency_wait();  // the state below is written by the previous step
+    if (threadIdx.x == 0) {
         bulk_g2s(ug_s, a.ug_cur + (size_t)n0 * 3 * Sp, row_bytes, bar);
         if constexpr (!FORCE_ONLY) {
             const size_t r0 = (size_t)n0 * 3 * Sp;
@@ -552,6 +800,141 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
         if constexpr (!HOIST) node_traction<R>(a, i, lds_step(smem + 8), fe);
         node_update<FORM, R, V>(a, i, s0, ui, f, fe);
     }
+}
+
+// Halo-staged kernel (binary32 forms). Thread 0 bulk-copies the block's halo record
+// (row offsets, halo node and element ids, slot-indexed entries) and coupling blocks;
+// then every thread issues cp.async copies of the halo rows: the 3 Sp displacement
+// values of every distinct node the block's incidences touch (its own nodes first) and
+// the Sp (E h) values of every distinct element. After one wait the force loop reads
+// only shared memory: one dependent round trip for all gathers instead of one per
+// incidence. Same operations in the same order as the other shapes (bitwise equal).
+template <int FORM, int BLOCK, int MINB, int V>
+__global__ void __launch_bounds__(BLOCK, MINB) step_halo_kernel(const StepArgs<float> a,
+                                                                const StagePlan pl) {
+    using R = float;
+    constexpr int KS = Kc<R>::stride;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const int32_t nb_block = pl.nb, cnt_max = pl.cnt_max;
+    const int32_t hw = pl.rec_h, hx = pl.halo_w;
+    const int32_t words = hw + hx + cnt_max;
+    int4 *rec_s = reinterpret_cast<int4 *>(smem + 16);
+    const int32_t *hdr = reinterpret_cast<const int32_t *>(rec_s);
+    const int32_t *nid = reinterpret_cast<const int32_t *>(rec_s + hw);
+    const int32_t *eid = nid + ((pl.h_max + 3) & ~3);
+    const int4 *ent_s = rec_s + hw + hx;
+    R *kc_s = reinterpret_cast<R *>(rec_s + words);
+    const int32_t Q = a.fv.Q;
+    const int32_t Sp = a.fv.Sp;
+    R *uh = kc_s + (size_t)cnt_max * KS;          // [h_max][3][Sp]
+    R *ehh = uh + (size_t)pl.h_max * 3 * Sp;      // [he_max][Sp]
+    const int32_t N = a.fv.N;
+    const int32_t n0 = blockIdx.x * nb_block;
+    const int32_t nb = min(nb_block, N - n0);
+    const int32_t li = threadIdx.x / Q;
+    const int32_t s0 = (threadIdx.x - li * Q) * V;
+    const bool valid = li < nb;
+    const int32_t i = n0 + li;
+    grid_launch_dependents();  // the next step's blocks may stage their records early
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+        const uint32_t b_rec = (uint32_t)words * 16u;
+        const uint32_t b_kc = (uint32_t)cnt_max * KS * (uint32_t)sizeof(R);
+        mbar_expect_tx(bar, b_rec + b_kc);
+        bulk_g2s(rec_s, pl.rec_ent + (size_t)blockIdx.x * words, b_rec, bar);
+        bulk_g2s(kc_s, static_cast<const R *>(pl.rec_kc) + (size_t)blockIdx.x * cnt_max * KS, b_kc, bar);
+    }
+    grid_dependency_wait();  // the state below is written by the previous step
+    if (threadIdx.x == 0) {
+        const size_t r0 = (size_t)n0 * 3 * Sp;
+        bulk_prefetch_l2(a.minv + (size_t)n0 * Sp, (uint32_t)(nb * Sp * sizeof(R)));
+        if constexpr (FORM == kKahan32) {
+            bulk_prefetch_l2(a.ulo + r0, (uint32_t)(nb * 3 * Sp * 4));
+            bulk_prefetch_l2(a.v32 + r0, (uint32_t)(nb * 3 * Sp * 4));
+        } else {
+            bulk_prefetch_l2(a.utail + r0, (uint32_t)(nb * 3 * Sp * 4));
+            bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
+        }
+        if (a.J <= 4)
+            for (int32_t j = 0; j < a.J; j++)
+                prefetch_range_l2(a.modes + ((int64_t)j * N + n0) * 3, (uint32_t)(nb * 3 * sizeof(R)));
+        *reinterpret_cast<int64_t *>(smem + 8) = *a.step_ctr + a.k_off;
+    }
+    __syncthreads();
+    if (!mbar_wait(bar, 0, kWaitLimit)) {
+        if (threadIdx.x == 0) atomicOr(a.flags, 2);
+        mbar_wait(bar, 0, kWaitLimit);
+        return;
+    }
+    const int32_t n_hn = hdr[nb_block + 1], n_he = hdr[nb_block + 2];
+    if (n_hn < nb || n_hn > pl.h_max || n_he < 0 || n_he > pl.he_max) {  // not a record of this plan
+        if (threadIdx.x == 0) atomicOr(a.flags, 4);
+        return;
+    }
+    // halo rows in 16-byte chunks, (3 Sp / 4) per node and Sp / 4 per element: the block's
+    // threads cover whole rows per pass (the thread's row and chunk fixed, one division)
+    {
+        const int32_t cpn = 3 * Sp / 4, cpe = Sp / 4;
+        if (cpn <= BLOCK) {  // rows per pass >= 1
+            const int32_t rpn = BLOCK / cpn;
+            const int32_t jn = threadIdx.x / cpn, cn = threadIdx.x - jn * cpn;
+            if (jn < rpn)
+                for (int32_t j = jn; j < n_hn; j += rpn)
+                    cp_async16(uh + (size_t)j * 3 * Sp + 4 * cn, a.ug_cur + (size_t)nid[j] * 3 * Sp + 4 * cn);
+        } else {  // wide rows: every thread strides along each row
+            for (int32_t j = 0; j < n_hn; j++)
+                for (int32_t c = threadIdx.x; c < cpn; c += BLOCK)
+                    cp_async16(uh + (size_t)j * 3 * Sp + 4 * c, a.ug_cur + (size_t)nid[j] * 3 * Sp + 4 * c);
+        }
+        if (cpe <= BLOCK) {
+            const int32_t rpe = BLOCK / cpe;
+            const int32_t je = threadIdx.x / cpe, ce = threadIdx.x - je * cpe;
+            if (je < rpe)
+                for (int32_t j = je; j < n_he; j += rpe)
+                    cp_async16(ehh + (size_t)j * Sp + 4 * ce, a.fv.eh + (size_t)eid[j] * Sp + 4 * ce);
+        } else {
+            for (int32_t j = 0; j < n_he; j++)
+                for (int32_t c = threadIdx.x; c < cpe; c += BLOCK)
+                    cp_async16(ehh + (size_t)j * Sp + 4 * c, a.fv.eh + (size_t)eid[j] * Sp + 4 * c);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!valid) return;
+    const int32_t p0 = hdr[li], p1 = hdr[li + 1];
+    if (p0 < 0 || p1 < p0 || p1 > cnt_max) {
+        atomicOr(a.flags, 4);
+        return;
+    }
+    R ui[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int v = 0; v < V; v++) ui[d][v] = uh[((size_t)li * 3 + d) * Sp + s0 + v];
+    R f[3][V];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int v = 0; v < V; v++) f[d][v] = R(0);
+    for (int32_t p = p0; p < p1; ++p) {
+        const int4 en = ent_s[p];
+        R ua[3][V], ub[3][V], ev[V];
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                ua[d][v] = uh[((size_t)en.y * 3 + d) * Sp + s0 + v];
+                ub[d][v] = uh[((size_t)en.z * 3 + d) * Sp + s0 + v];
+            }
+#pragma unroll
+        for (int v = 0; v < V; v++) ev[v] = ehh[(size_t)en.x * Sp + s0 + v];
+        apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
+    }
+    R fe[3];
+    node_traction<R>(a, i, lds_step(smem + 8), fe);
+    node_update<FORM, R, V>(a, i, s0, ui, f, fe);
 }
 
 // Persistent, double-buffered form of the staged kernel. Each CTA walks the node tiles
@@ -910,6 +1293,27 @@ void note_launch(const char *what, int block, int minb, uint32_t smem, cudaError
              block, minb, smem, cudaGetErrorString(e));
 }
 
+// Launch with programmatic stream serialisation: the kernel may begin while the previous
+// kernel on the stream finishes (once every block of that kernel has signalled
+// griddepcontrol.launch_dependents, or it has exited); the staged kernels then stage
+// only their constant records before griddepcontrol.wait. Inside stream capture this
+// becomes a programmatic dependency edge of the graph.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, int block, uint32_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <int FORM, typename R, bool FO, int BLOCK, int MINB, int V = Vw<R>::V, bool HOIST = false,
           bool REC = false>
 cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
@@ -925,9 +1329,28 @@ cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan
         }
     }
     const unsigned grid = (unsigned)((a.fv.N + plan->nb - 1) / plan->nb);
-    k<<<grid, BLOCK, plan->smem, s>>>(a, *plan);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k, grid, BLOCK, plan->smem, s, a, *plan);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) note_launch("staged launch", BLOCK, MINB, plan->smem, e);
+    return e;
+}
+
+template <int FORM, int BLOCK, int MINB, int V>
+cudaError_t launch_halo(const StepArgs<float> &a0, cudaStream_t s, const StagePlan *plan) {
+    auto *k = step_halo_kernel<FORM, BLOCK, MINB, V>;
+    StepArgs<float> a = a0;
+    a.fv.Q = a.fv.Sp / V;
+    if (plan->smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+        if (e != cudaSuccess) {
+            note_launch("cudaFuncSetAttribute", BLOCK, MINB, plan->smem, e);
+            return e;
+        }
+    }
+    const unsigned grid = (unsigned)((a.fv.N + plan->nb - 1) / plan->nb);
+    cudaError_t e = launch_pdl(k, grid, BLOCK, plan->smem, s, a, *plan);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) note_launch("halo launch", BLOCK, MINB, plan->smem, e);
     return e;
 }
 
@@ -962,6 +1385,12 @@ cudaError_t launch_pipelined(const StepArgs<R> &a0, cudaStream_t s, const StageP
 template <int FORM, typename R, bool FO>
 cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
     const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
+    if constexpr (!FO) {
+        if (a.kcs) {  // geometry update: per-realisation blocks, one launch shape
+            step_geom_kernel<FORM, R><<<blocks_for(threads, kBlock), kBlock, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if (plan && plan->staged) {
         if constexpr (FO) {
             // force-only evaluations have one staged shape; other plans run unstaged
@@ -971,6 +1400,11 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
                 if (plan->pipelined) {
                     if (plan->block == 128) return launch_pipelined<FORM, R, 128, 8, 2>(a, s, plan);
                     return launch_pipelined<FORM, R, 256, 4, 2>(a, s, plan);
+                }
+                if (plan->halo) {
+                    if (plan->vw == 4) return launch_halo<FORM, 128, 6, 4>(a, s, plan);
+                    if (plan->block == 256) return launch_halo<FORM, 256, 5, 2>(a, s, plan);
+                    return launch_halo<FORM, 128, 10, 2>(a, s, plan);
                 }
                 if (plan->rec) {
                     if (plan->vw == 2) return launch_staged<FORM, R, FO, 128, 10, 2, false, true>(a, s, plan);
@@ -1010,6 +1444,21 @@ cudaError_t launch_step(int form, const StepArgs<R> &a, bool force_only, cudaStr
         return launch_one<kKahan32, float, false>(a, s, plan);
     }
 }
+
+template <typename R>
+cudaError_t launch_geo_correct(const StepArgs<R> &a0, const R *kcs_old, const R *kcs_new, double *c64, R *cR,
+                               cudaStream_t s) {
+    StepArgs<R> a = a0;
+    a.fv.Q = a.fv.Sp / Vw<R>::V;
+    const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
+    if (threads == 0) return cudaSuccess;
+    geo_correct_kernel<R><<<blocks_for(threads, kBlock), kBlock, 0, s>>>(a, kcs_old, kcs_new, c64, cR);
+    return cudaGetLastError();
+}
+template cudaError_t launch_geo_correct<double>(const StepArgs<double> &, const double *, const double *, double *,
+                                                double *, cudaStream_t);
+template cudaError_t launch_geo_correct<float>(const StepArgs<float> &, const float *, const float *, double *,
+                                               float *, cudaStream_t);
 
 template cudaError_t launch_step<double>(int, const StepArgs<double> &, bool, cudaStream_t,
                                          const StagePlan *);

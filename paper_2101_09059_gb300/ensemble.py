@@ -262,6 +262,11 @@ class Ensemble:
                    _ptr(quant) if quant is not None else None)
         return mean, var, quant
 
+    def set_geometry_update(self, k: int):
+        """Re-assemble every realisation's stiffness on its deformed surface every k steps
+        (Section 2.3); k = 0 returns to the linear method."""
+        self._call("ens_set_geometry_update", int(k))
+
     def set_peak(self, stride: int = 1):
         """Track the running peak of |u| per node and realisation on every step index that
         is a multiple of stride (0: off); read it with QTY_PEAK_MAGNITUDE."""

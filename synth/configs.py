@@ -37,9 +37,9 @@ def cfl_dt(mesh, E: np.ndarray, rho: float = RHO, safety: float = 0.5) -> float:
 
 
 def _case(mesh, S, seed, n_steps, load, uniform=False, alpha=ALPHA, dt=None, corr=0.02,
-          std=0.1, E_mean=0.7e6, h_mean=1.0e-3, pressure=10.0e3):
+          std=0.1, E_mean=0.7e6, h_mean=1.0e-3, pressure=10.0e3, sample0=0):
     E, h = lognormal_fields(mesh, S, E_mean=E_mean, h_mean=h_mean, corr_length=corr, std=std,
-                            seed=seed, uniform=uniform)
+                            seed=seed, uniform=uniform, sample0=sample0)
     if dt is None:
         dt = cfl_dt(mesh, E if S > 0 else np.array([E_mean]))
     if load == "step":
@@ -137,6 +137,18 @@ def make_case(name: str, S: int | None = None, n_steps: int | None = None, seed:
         c.update(modes=modes, amp=amp, n_steps=steps)
         return c
     raise ValueError(f"unknown case {name}")
+
+
+def with_dt(name: str, case: dict, dt: float) -> dict:
+    """The workload `name` with time step dt: the shards of one ensemble drawn on several
+    processes agree on the step of its stiffest realisation. The load table is rebuilt
+    where it depends on dt (the pulsatile and travelling-wave loads)."""
+    c = dict(case, dt=float(dt))
+    if name in ("aneurysm", "aneurysm_50k"):
+        c["amp"] = pulsatile_amplitudes(c["n_steps"], c["dt"], with_shear=True)
+    elif name == "arch":
+        c["modes"], c["amp"] = delayed_pressure(c["mesh"], _arch_path_length(c["mesh"]), c["n_steps"], c["dt"])
+    return c
 
 
 def _arch_path_length(m) -> np.ndarray:

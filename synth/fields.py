@@ -57,9 +57,11 @@ def surface_mass_stiffness(xyz: np.ndarray, tri: np.ndarray):
 
 
 def gmrf_fields(xyz: np.ndarray, tri: np.ndarray, n_samples: int, corr_length: float,
-                std: float, seed: int, streams=(1,)) -> list:
+                std: float, seed: int, streams=(1,), sample0: int = 0) -> list:
     """Zero-mean Matern (nu = 1) fields with marginal std `std`: one [N][S] array per
-    entry of `streams` (independent draws sharing one factorisation)."""
+    entry of `streams` (independent draws sharing one factorisation). Realisation j of the
+    result is realisation sample0 + j of the seeded ensemble (its normals are keyed by that
+    index), so shards of one ensemble can be drawn apart."""
     N = xyz.shape[0]
     if n_samples == 0:
         return [np.zeros((N, 0)) for _ in streams]
@@ -71,7 +73,7 @@ def gmrf_fields(xyz: np.ndarray, tri: np.ndarray, n_samples: int, corr_length: f
     for stream in streams:
         z = np.empty((N, n_samples))
         for s in range(n_samples):
-            z[:, s] = _philox(seed, stream, s).standard_normal(N)
+            z[:, s] = _philox(seed, stream, sample0 + s).standard_normal(N)
         x = lu.solve(np.sqrt(Cl)[:, None] * z)
         out.append(x * (std * np.sqrt(4.0 * np.pi) * kappa))
     return out
@@ -79,7 +81,7 @@ def gmrf_fields(xyz: np.ndarray, tri: np.ndarray, n_samples: int, corr_length: f
 
 def lognormal_fields(mesh, n_samples: int, E_mean: float = 0.7e6, h_mean: float = 1.0e-3,
                      corr_length: float = 0.02, std: float = 0.1, seed: int = 0,
-                     uniform: bool = False):
+                     uniform: bool = False, sample0: int = 0):
     """Nodal E = E_mean exp(g_E), h = h_mean exp(g_h) with independent Matern fields g_E, g_h.
 
     Returns (E, h), each [N][S] float64 with the sample index innermost.
@@ -88,7 +90,8 @@ def lognormal_fields(mesh, n_samples: int, E_mean: float = 0.7e6, h_mean: float 
     N = mesh.n_nodes
     if uniform or std == 0.0:
         return np.full((N, n_samples), E_mean), np.full((N, n_samples), h_mean)
-    gE, gh = gmrf_fields(mesh.xyz, mesh.tri, n_samples, corr_length, std, seed, streams=(1, 2))
+    gE, gh = gmrf_fields(mesh.xyz, mesh.tri, n_samples, corr_length, std, seed, streams=(1, 2),
+                         sample0=sample0)
     return E_mean * np.exp(gE), h_mean * np.exp(gh)
 
 

@@ -53,7 +53,8 @@ def _create(L, xyz, tri, En, hn, S, **kw):
 
 @pytest.mark.parametrize("bad", [
     dict(nu=1.0), dict(nu=-0.1), dict(rho=0.0), dict(dt=0.0), dict(dt=float("nan")),
-    dict(alpha=-1.0), dict(kshear=0.0), dict(precision=3), dict(flags=8), dict(flags=13 << 8),
+    dict(alpha=-1.0), dict(kshear=0.0), dict(precision=3), dict(flags=8), dict(flags=1 << 12),
+    dict(flags=16 | 32),
 ])
 def test_create_rejects_bad_parameters(L, bad):
     xyz, tri, En, hn = _args()

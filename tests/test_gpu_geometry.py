@@ -1,0 +1,86 @@
+"""Geometry update with selective stiffness re-assembly on the device
+(ens_set_geometry_update, Section 2.3) against the oracle (oracle/geometry.py).
+
+Tolerances: the trajectory tolerances of the linear method (1e-10 relative L2 for the
+FP64 form, 1e-5 for the binary32 forms). The re-assembly evaluates the element frame and
+coupling blocks with the set-up kernel's arithmetic on the deformed coordinates, and the
+per-realisation step applies them in the linear kernel's operation order, so a run that
+never re-assembles is the linear run bit for bit."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import geometry as og
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2101_09059_gb300 as ens  # noqa: E402
+
+TOL = {"fp64": 1e-10, "fp32_force": 1e-5, "kahan32": 1e-5}
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _case():
+    """The 40 x 40 tube of the configuration (10 kPa step, S = 8)."""
+    return synth.make_case("tube_40x40", S=8, seed=2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+def test_without_reassembly_the_run_is_the_linear_run_bitwise(precision):
+    case = _case()
+    lin = ens.Ensemble.from_case(case, precision=precision)
+    lin.step(300)
+    geo = ens.Ensemble.from_case(case, precision=precision)
+    geo.set_geometry_update(100000)
+    geo.step(300)
+    assert np.array_equal(geo.displacement(), lin.displacement())
+    lin.close()
+    geo.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_force", "kahan32"])
+def test_geometry_update_matches_oracle(precision):
+    case = _case()
+    n, k = case["n_steps"], 10
+    ref = og.run_updated(case, n, k)
+    e = ens.Ensemble.from_case(case, precision=precision)
+    e.set_geometry_update(k)
+    for part in (1, 733, 266, n - 1000):
+        e.step(part)
+    u = e.displacement()
+    err = _rel(u, ref)
+    print(f"geometry update {precision}, k = {k}: rel-L2 {err:.3e}")
+    assert err < TOL[precision]
+    # the update changes the response by far more than the tolerance
+    lin = ens.Ensemble.from_case(case, precision=precision)
+    lin.step(n)
+    assert _rel(lin.displacement(), ref) > 1e-3
+    # reset re-assembles on the reference surface: the rerun is identical
+    e.reset()
+    e.step(n)
+    assert np.array_equal(e.displacement(), u)
+    e.set_geometry_update(0)            # back to the linear method
+    e.reset()
+    e.step(n)
+    assert np.array_equal(e.displacement(), lin.displacement())
+    e.close()
+    lin.close()
+
+
+def test_geometry_update_members_cannot_join_a_batch():
+    case = synth.make_case("tube_small", S=4, n_steps=20)
+    a = ens.Ensemble.from_case(case, precision="kahan32")
+    b = ens.Ensemble.from_case(case, precision="kahan32")
+    a.set_geometry_update(5)
+    with pytest.raises(ens.EnsError) as ei:
+        ens.Batch([a, b])
+    assert ei.value.code == -8
+    a.close()
+    b.close()

@@ -106,3 +106,13 @@ def test_cylinder_workload_follows_section_3_1():
     inlet = m.xyz[:, 2] < 0.05
     outlet = m.xyz[:, 2] > 0.25
     assert np.linalg.norm(P1[inlet], axis=1).mean() > 3 * np.linalg.norm(P1[outlet], axis=1).mean()
+
+
+def test_shards_of_one_ensemble_are_its_realisations():
+    """Realisations are keyed by their index in the seeded ensemble, so a rank that draws
+    realisations [k, k + S) gets those of the whole ensemble (sample-sharded runs)."""
+    whole = synth.make_case("tube_small", S=6, seed=3)
+    for k in (0, 2, 5):
+        part = synth.make_case("tube_small", S=6 - k, seed=3, sample0=k)
+        assert np.allclose(part["E"], whole["E"][:, k:], rtol=1e-14, atol=0)
+        assert np.allclose(part["h"], whole["h"][:, k:], rtol=1e-14, atol=0)
