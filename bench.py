@@ -408,6 +408,68 @@ def bench_outputs(args, local, stream, hbm_peak):
     e.close()
     return res
 
+def bench_over_time(args, local, stream, hbm_peak):
+    """Cost of the two time-history features. Running peak of |u| (ens_set_peak) on the
+    200k-node aneurysm, S = 64, FP32-force: time per step without tracking and with the
+    peak recorded every step and every 16 steps. Geometry update (ens_set_geometry_update)
+    on the paper's cylinder at its finest Table-2 mesh (32,994 triangles), S = 100,
+    compensated FP32: time per step before and after the first re-assembly, and per
+    re-assembly (k = 50)."""
+    import torch
+    import synth
+    import paper_2101_09059_gb300 as pkg
+
+    def per_step(e, n, reps=3):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            e.step(n)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3 / (reps * n)
+
+    S = args.samples
+    case = synth.make_case("aneurysm", S=S, n_steps=2000, seed=0)
+    N = case["mesh"].n_nodes
+    e = pkg.Ensemble.from_case(case, precision=HEADLINE, stream=stream, device=local)
+    e.step(64)
+    t_plain = per_step(e, 192)
+    peak = {}
+    for stride in (1, 16):
+        e.set_peak(stride)
+        e.step(64)
+        peak[stride] = per_step(e, 192)
+    e.close()
+    peak_bytes = N * S * (12.0 + 16.0)
+    res = {"peak": {"workload": f"aneurysm tube, {N} nodes, S={S}, {HEADLINE}",
+                    "step_us": t_plain * 1e6, "step_with_peak_every_step_us": peak[1] * 1e6,
+                    "step_with_peak_every_16_steps_us": peak[16] * 1e6,
+                    "peak_kernel_bytes": peak_bytes,
+                    "peak_kernel_hbm_frac": peak_bytes / max(peak[1] - t_plain, 1e-9) / 1e9 / hbm_peak}}
+    cyl = synth.make_case("cylinder", level=2, S=100, n_steps=4000)
+    e = pkg.Ensemble.from_case(cyl, precision="kahan32", stream=stream, device=local)
+    e.step(100)
+    t_lin = per_step(e, 100)
+    e.set_geometry_update(1000000)          # per-realisation data allocated, no re-assembly yet
+    e.set_geometry_update(50)
+    e.step(50 - e.info()["step"] % 50)      # first re-assembly
+    t_geo = per_step(e, 49, reps=1)         # steps between re-assemblies
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    e.step(50)                              # 50 steps and one re-assembly
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_cycle = ev0.elapsed_time(ev1) / 1e3
+    info = e.info()
+    e.close()
+    res["geometry_update"] = {
+        "workload": f"paper cylinder, {cyl['mesh'].n_nodes} nodes, {cyl['mesh'].n_elems} triangles, S=100, "
+                    "kahan32, re-assembly every 50 steps",
+        "linear_step_us": t_lin * 1e6, "updated_step_us": t_geo * 1e6,
+        "reassembly_us": max(t_cycle - 50 * t_geo, 0.0) * 1e6,
+        "per_realisation_block_bytes": 2 * info["nnz"] * 18 * 100 * 4.0}
+    return res
+
 
 # Sample-steps/s the paper prints for its cylinder meshes (Tables 1-3, times read as
 # h:mm:ss over 1000 steps) on GeForce RTX 2080 Ti cards, FP64 implied: context only.
@@ -467,14 +529,14 @@ def bench_paper_tables(args, local, stream):
             "rows": rows}
 
 
-def bench_batched(args, local, stream, world):
-    """Five clamped tubes (20k, 50k, 100k, 200k, 400k nodes; S = 256, 128, 64, 32, 16; each
-    with its own CFL time step; 10 kPa step load) advanced by one batched launch per step
-    (or one persistent launch), against the same members stepped one after another."""
+def bench_batched(args, local, stream, world, sizes=(20, 50, 100, 200, 400), widths=(256, 128, 64, 32, 16)):
+    """Five clamped tubes (by default 20k, 50k, 100k, 200k, 400k nodes; S = 256, 128, 64,
+    32, 16; each with its own CFL time step; 10 kPa step load) advanced by one batched
+    launch per step (or one persistent launch), against the same members stepped one after
+    another (each replaying its own captured time-loop graphs)."""
     import torch
     import synth
     import paper_2101_09059_gb300 as pkg
-    sizes, widths = [20, 50, 100, 200, 400], [256, 128, 64, 32, 16]
     C, W, K = args.batch_chunk, 2, args.batch_steps
     need = 2 * C * (W + K) + 1
     cases = [synth.make_case(f"tube_{n}k", S=S, n_steps=need, seed=k + 100 * local)
@@ -516,8 +578,8 @@ def bench_batched(args, local, stream, world):
     hbm_peak, _ = peaks()
     gbs = info["bytes_per_step"] * steps / t_batch / 1e9
     return {
-        "workload": "5 clamped tubes, 20k/50k/100k/200k/400k nodes, S=256/128/64/32/16, own CFL dt, "
-                    "10 kPa step load, compensated FP32",
+        "workload": f"5 clamped tubes, {'/'.join(f'{n}k' for n in sizes)} nodes, "
+                    f"S={'/'.join(str(w) for w in widths)}, own CFL dt, 10 kPa step load, compensated FP32",
         "value": sum_over_ranks(ss * steps / t_batch, world), "unit": "sample-steps/s",
         "node_sample_steps_per_s": sum_over_ranks(nss * steps / t_batch, world),
         "ms_per_step": 1e3 * t_batch / K, "time_steps_per_step": C,
@@ -870,10 +932,14 @@ def main():
 
     tiny = bench_tiny(args, local, stream) if rank == 0 else None
     batched = None if args.no_batched else bench_batched(args, local, stream, world)
+    # small members, where a step of each is a few microseconds and launches dominate
+    batched_small = None if args.no_batched else bench_batched(args, local, stream, world, sizes=(2, 4, 6, 8, 10),
+                                                               widths=(64, 64, 32, 32, 16))
     surrogate = None if (args.no_surrogate or rank != 0) else bench_surrogate(args, local, stream)
     fields = None if (args.no_fields or rank != 0) else bench_fields(args, local, stream, hbm_peak)
     outputs = None if (args.no_outputs or rank != 0) else bench_outputs(args, local, stream, hbm_peak)
     tables = None if (args.no_paper_tables or rank != 0) else bench_paper_tables(args, local, stream)
+    over_time = None if (args.no_outputs or rank != 0) else bench_over_time(args, local, stream, hbm_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -914,10 +980,12 @@ def main():
         "forms": results,
         "tiny_tube_40x40": tiny,
         "batched_uneven": batched,
+        "batched_small": batched_small,
         "surrogate": surrogate,
         "field_sampler": fields,
         "output_statistics": outputs,
         "paper_tables": tables,
+        "over_time": over_time,
         "fp64_peak_tflops_derived": FP64_PEAK_TFLOPS,
     }
     if rank == 0:

@@ -397,15 +397,17 @@ int ens_row_stats_device(int64_t n_rows, int32_t S, const double *rows, int32_t 
 
 /* Running peak of the displacement magnitude per node and realisation (the peak and
  * band quantities of Section 3 over a heart cycle): with stride >= 1, every step that
- * ends on an index k that is a multiple of stride updates peak = max(peak, |u_k|), |u|
- * formed in binary64 from the state of any form; read it as ENS_QTY_PEAK_MAGNITUDE.
- * The call zeroes the peak (so it covers steps after the call), as does ens_reset;
- * stride = 0 switches tracking off and frees it. The peak is updated by a separate
- * kernel after each step launch (also inside the captured time-loop graphs): per
- * recorded step it reads the state once (24 B per node and sample) and reads and writes
- * the peak (16 B). It is not part of ens_get_state's checkpoint, and contexts that
- * track a peak cannot join a batch (ens_batch_create / ens_batch_step return
- * ENS_ERR_STATE).                                                                     */
+ * ends on an index k that is a multiple of stride updates peak = max(peak, |u_k|); read
+ * it as ENS_QTY_PEAK_MAGNITUDE. |u| is formed in binary64 for ENS_FP64 and in binary32
+ * from the displacement words the binary32 forms gather (the FP32-force head, the
+ * compensated hi part: within one binary32 rounding of the state). The call zeroes the
+ * peak (so it covers steps after the call), as does ens_reset; stride = 0 switches
+ * tracking off and frees it. The peak is kept squared by a separate kernel after each
+ * step launch (also inside the captured time-loop graphs): per recorded step it reads
+ * the gathered state once (12 B per node and sample in binary32, 24 B in binary64) and
+ * reads and writes the peak (16 B). It is not part of ens_get_state's checkpoint, and
+ * contexts that track a peak cannot join a batch (ens_batch_create / ens_batch_step
+ * return ENS_ERR_STATE).                                                              */
 int ens_set_peak(ens_ctx *ctx, int32_t stride);
 
 /* Probe time histories: after every ens_step segment that ends on a step index that is

@@ -69,6 +69,35 @@ int sur_adam_step(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B,
 int sur_train(sur_ctx *c, const float *X_dev, const float *T_dev, int64_t n, int32_t batch,
               int32_t epochs, float lr, uint64_t seed, float *loss_host);
 
+/* Proper orthogonal decomposition of solver snapshots (the basis whose coefficients the
+ * network predicts): X_dev [n][D] binary32 snapshots (device), 2 <= n <= 32768,
+ * 1 <= r <= min(48, n - 1). Writes mean_dev [D] (column means), phi_dev [D][r] (the r
+ * leading orthonormal modes of the centred snapshots X_c), coef_dev [n][r] (X_c phi) and,
+ * if not NULL, lam_host [r] (eigenvalues of X_c X_c^T, descending), frac_host (their share
+ * of the trace) and iters_host (subspace iterations taken). Each mode's sign makes its
+ * largest-magnitude coefficient positive. Method of snapshots: the Gram matrix X_c X_c^T
+ * (n x n binary64 on the device; binary32 products summed 32 at a time, accumulated in
+ * binary64), its leading eigenvectors by subspace iteration with Rayleigh-Ritz in binary64
+ * (block of min(n - 1, r + 16) vectors, until every residual is below 1e-11 of the top
+ * eigenvalue, at most 1000 iterations), phi = X_c^T V / sqrt(lambda) in binary64.
+ * Allocates its work space (n^2 + 3 n (r + 16) + D doubles) with cudaMalloc; runs on
+ * stream and synchronises it.                                                           */
+int sur_pod(const float *X_dev, int64_t n, int64_t D, int32_t r, float *mean_dev, float *phi_dev,
+            float *coef_dev, double *lam_host, double *frac_host, int32_t *iters_host, void *stream);
+
+/* Trust region of the trained network, so that the plain solver stays the fallback for
+ * realisations the network was not trained on (the surrogate's inputs are KL
+ * coefficients drawn from N(0, I)). The radius is the smallest Euclidean norm with at
+ * least q n of the n training inputs X_dev [n][n_in] at or below it (0 < q <= 1; q = 1
+ * gives the largest training norm); norms in binary64 on the device. radius_out (may be
+ * NULL) receives it. Synchronises the stream.                                           */
+int sur_fit_trust(sur_ctx *c, const float *X_dev, int64_t n, double q, double *radius_out);
+
+/* flags_dev [B] (device int32): 1 where the input row x_dev [B][n_in] has a norm within
+ * the trust radius, 0 where its prediction should be replaced by a solver run.
+ * SUR_ERR_INVALID_ARG before sur_fit_trust. Asynchronous on the stream.                */
+int sur_trust(sur_ctx *c, const float *x_dev, int64_t B, int32_t *flags_dev);
+
 /* POD reconstruction u_dev [B][D] = mean_dev [D] + coef_dev [B][r] phi_dev [D][r]^T.     */
 int sur_reconstruct(const float *coef_dev, const float *mean_dev, const float *phi_dev, int32_t B,
                     int64_t D, int32_t r, float *u_dev, void *stream);

@@ -177,6 +177,10 @@ def load(build_if_missing: bool = True):
         "sur_adam_step": ([vp, dp, dp, i64, ctypes.c_float], ctypes.c_int),
         "sur_train": ([vp, dp, dp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, dp], ctypes.c_int),
         "sur_reconstruct": ([dp, dp, dp, i32, i64, i32, dp, vp], ctypes.c_int),
+        "sur_pod": ([dp, i64, i64, i32, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_double),
+                     ctypes.POINTER(ctypes.c_int32), vp], ctypes.c_int),
+        "sur_fit_trust": ([vp, dp, i64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "sur_trust": ([vp, dp, i64, dp], ctypes.c_int),
         "sur_matmul": ([dp, i64, i64, dp, i64, i64, dp, i32, i32, i32, i32, vp], ctypes.c_int),
         "sur_field_stats": ([dp, i32, i32, dp, dp, i64, dp, dp, dp, vp], ctypes.c_int),
         "sur_last_error": ([vp], ctypes.c_char_p),

@@ -208,9 +208,10 @@ cudaError_t launch_element_mean(const int32_t *tri, const double *En, int32_t E,
                                 cudaStream_t s);
 cudaError_t launch_row_stats(const double *rows, int64_t n_rows, int32_t S, int32_t n_q, const double *q_dev,
                              double *mean, double *var, double *quant, cudaStream_t s);
-// Running peak of |u| (ens_outputs.cu): after the step launch k_off of a chunk whose
-// first state index is *step_ctr, peak = max(peak, |u|) when the new index is a multiple
-// of stride; u_main / aux: the state written by that launch.
+// Running peak of |u| (ens_outputs.cu), kept squared: after the step launch k_off of a
+// chunk whose first state index is *step_ctr, peak2 = max(peak2, |u|^2) when the new
+// index is a multiple of stride; u_main: the gathered state words written by that launch
+// (aux unused).
 cudaError_t launch_peak(int form, const void *u_main, const void *aux, int32_t N, int32_t Sp,
                         const int64_t *step_ctr, int32_t k_off, int32_t stride, double *peak, cudaStream_t s);
 cudaError_t launch_pad_fields(const double *src, int32_t N, int32_t S, int32_t Sp, double *dst,

@@ -20,6 +20,7 @@
 // j = floor h, Q(p) = x_j + (h - j)(x_{j+1} - x_j), evaluated without fused multiply-adds
 // so that the result is the formula's. One warp owns a row and sorts it in shared memory
 // (bitonic network).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -45,22 +46,45 @@ __device__ __forceinline__ double u_at(const void *u_main, const void *aux, int6
         return ((const double *)u_main)[idx];
 }
 
-// Running peak of |u| per node and sample (ens_set_peak): after a step launch, the state
-// just written has index n = *ctr + k_off + 1; when n is a multiple of the stride the
-// peak takes max(peak, |u_n|) with |u| formed in binary64 from the form's state.
+// Running peak of |u| per node and sample (ens_set_peak), kept squared: after a step
+// launch, the state just written has index n = *ctr + k_off + 1; when n is a multiple of
+// the stride, peak2 = max(peak2, |u_n|^2). The binary32 forms form |u|^2 in binary32 from
+// the words their forces gather (the FP32-force head, the compensated hi part: within one
+// binary32 rounding of u), the FP64 form in binary64; the square root is taken when the
+// peak is read (a binary64 square root per node and sample would occupy GB300's binary64
+// pipe for longer than the step itself).
+// A grid of a few blocks per SM strides over the node-samples, so that the launches after
+// steps that record nothing retire at once.
 template <int FORM>
-__global__ void peak_kernel(const void *__restrict__ u_main, const void *__restrict__ aux, int32_t N,
-                            int32_t Sp, const int64_t *__restrict__ ctr, int32_t k_off, int32_t stride,
-                            double *__restrict__ peak) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)N * Sp) return;
+__global__ void peak_kernel(const void *__restrict__ u_main, int32_t N, int32_t Sp,
+                            const int64_t *__restrict__ ctr, int32_t k_off, int32_t stride,
+                            double *__restrict__ peak2) {
     if ((*ctr + k_off + 1) % stride != 0) return;
-    const int64_t i = t / Sp;
-    const int64_t r0 = i * 3 * Sp + (t - i * Sp);
-    const double x = u_at<FORM>(u_main, aux, r0);
-    const double y = u_at<FORM>(u_main, aux, r0 + Sp);
-    const double z = u_at<FORM>(u_main, aux, r0 + 2 * Sp);
-    peak[t] = fmax(peak[t], sqrt(x * x + y * y + z * z));
+    const uint32_t n = (uint32_t)N * (uint32_t)Sp;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint32_t i = t / (uint32_t)Sp;
+        const size_t r0 = (size_t)i * 3 * Sp + (t - i * (uint32_t)Sp);
+        double m2;
+        if constexpr (FORM == kFP64) {
+            const double *u = (const double *)u_main;
+            const double x = u[r0], y = u[r0 + Sp], z = u[r0 + 2 * (size_t)Sp];
+            m2 = x * x + y * y + z * z;
+        } else {
+            const float *u = (const float *)u_main;
+            const float x = u[r0], y = u[r0 + Sp], z = u[r0 + 2 * (size_t)Sp];
+            m2 = (double)(x * x + y * y + z * z);
+        }
+        if (m2 > peak2[t]) peak2[t] = m2;
+    }
+}
+
+// rows [N][S] = sqrt(peak2) [N][Sp]
+__global__ void peak_rows_kernel(const double *__restrict__ peak2, int32_t N, int32_t S, int32_t Sp,
+                                 double *__restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * S) return;
+    const int64_t i = t / S;
+    out[t] = sqrt(peak2[i * Sp + (t - i * S)]);
 }
 
 // E_e,s = (E_a + E_b + E_c) / 3 over the element's nodes.
@@ -376,15 +400,20 @@ cudaError_t launch_element_mean(const int32_t *tri, const double *En, int32_t E,
 
 cudaError_t launch_peak(int form, const void *u_main, const void *aux, int32_t N, int32_t Sp,
                         const int64_t *step_ctr, int32_t k_off, int32_t stride, double *peak, cudaStream_t s) {
+    (void)aux;
     const int64_t n = (int64_t)N * Sp;
     if (n == 0) return cudaSuccess;
-    const unsigned g = blocks_for(n, 256);
+    static int sms = 0;  // multiprocessors of the device (looked up once)
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 132;
+    }
+    const unsigned g = (unsigned)std::min<int64_t>(blocks_for(n, 256), (int64_t)sms * 8);
     if (form == kFP64)
-        peak_kernel<kFP64><<<g, 256, 0, s>>>(u_main, aux, N, Sp, step_ctr, k_off, stride, peak);
-    else if (form == kFP32Force)
-        peak_kernel<kFP32Force><<<g, 256, 0, s>>>(u_main, aux, N, Sp, step_ctr, k_off, stride, peak);
+        peak_kernel<kFP64><<<g, 256, 0, s>>>(u_main, N, Sp, step_ctr, k_off, stride, peak);
     else
-        peak_kernel<kKahan32><<<g, 256, 0, s>>>(u_main, aux, N, Sp, step_ctr, k_off, stride, peak);
+        peak_kernel<kKahan32><<<g, 256, 0, s>>>(u_main, N, Sp, step_ctr, k_off, stride, peak);
     return cudaGetLastError();
 }
 
@@ -448,9 +477,12 @@ cudaError_t launch_quantity_t(ens_ctx *c, int32_t qty, double *out) {
 cudaError_t launch_quantity(ens_ctx *c, int32_t qty, double *out) {
     if (qty == ENS_QTY_DISPLACEMENT)
         return launch_export(c->form, c->ug[c->cur], aux_of(c), c->N, c->S, c->Sp, out, ENS_LAYOUT_NCS, c->stream);
-    if (qty == ENS_QTY_PEAK_MAGNITUDE)  // [N][Sp] -> rows [N][S]
-        return cudaMemcpy2DAsync(out, 8 * (size_t)c->S, c->peak, 8 * (size_t)c->Sp, 8 * (size_t)c->S, (size_t)c->N,
-                                 cudaMemcpyDeviceToDevice, c->stream);
+    if (qty == ENS_QTY_PEAK_MAGNITUDE) {  // sqrt of the squared peak [N][Sp] -> rows [N][S]
+        const int64_t n = (int64_t)c->N * c->S;
+        if (n == 0) return cudaSuccess;
+        peak_rows_kernel<<<blocks_for(n, 256), 256, 0, c->stream>>>(c->peak, c->N, c->S, c->Sp, out);
+        return cudaGetLastError();
+    }
     if (c->form == kFP64) return launch_quantity_t<kFP64>(c, qty, out);
     if (c->form == kFP32Force) return launch_quantity_t<kFP32Force>(c, qty, out);
     return launch_quantity_t<kKahan32>(c, qty, out);

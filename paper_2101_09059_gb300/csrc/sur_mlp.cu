@@ -294,6 +294,26 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// Euclidean norm of every input row x [B][n] in binary64 (one warp per row, fixed
+// shuffle tree); with radius >= 0 also flags[b] = 1 where the norm is <= radius.
+__global__ void row_norm_kernel(const float *__restrict__ x, long long B, int n, double *__restrict__ norm,
+                                double radius, int *__restrict__ flags) {
+    const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x & 31;
+    if (row >= B) return;
+    double s = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double v = (double)x[row * n + k];
+        s = fma(v, v, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const double r = sqrt(s);
+        if (norm) norm[row] = r;
+        if (flags) flags[row] = r <= radius ? 1 : 0;
+    }
+}
+
 // u[b][d] = mean[d] + sum_r c[b][r] phi[d][r]  (POD reconstruction, FP32)
 __global__ void reconstruct_kernel(const float *__restrict__ c, const float *__restrict__ mean,
                                    const float *__restrict__ phi, int B, long long D, int r,
@@ -409,6 +429,7 @@ struct sur_ctx {
     float *dy = nullptr, *d2 = nullptr, *d1 = nullptr;
     float *xb = nullptr, *tb = nullptr, *loss = nullptr;
     float *corr = nullptr;  // Adam bias corrections {1 - b1^t, 1 - b2^t} of the current step
+    double trust_radius = -1.0;  // inputs with a larger norm are not trusted (sur_fit_trust)
     int *tstep = nullptr, *perm = nullptr;
     long long perm_n = 0;
     float *loss_hist = nullptr;
@@ -711,6 +732,39 @@ int sur_loss(sur_ctx *c, const float *x_dev, const float *t_dev, int64_t B, floa
         acc += (double)l * nb;
     }
     *loss_host = (float)(acc / B);
+    return SUR_OK;
+}
+
+int sur_fit_trust(sur_ctx *c, const float *X_dev, int64_t n, double q, double *radius_out) {
+    if (!c || !X_dev || n < 1 || !(q > 0.0 && q <= 1.0)) return SUR_ERR_INVALID_ARG;
+    double *norm_d = nullptr;
+    if (cudaMalloc(&norm_d, sizeof(double) * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(c, SUR_ERR_ALLOC, "%lld norms", (long long)n);
+    }
+    std::vector<double> norms((size_t)n);
+    row_norm_kernel<<<(unsigned)cdiv(n * 32, 256), 256, 0, c->stream>>>(X_dev, n, c->nin, norm_d, -1.0, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(norms.data(), norm_d, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(norm_d);
+    if (e != cudaSuccess) return sfail(c, SUR_ERR_CUDA, "training norms: %s", cudaGetErrorString(e));
+    // the smallest norm with at least q n training norms at or below it
+    const int64_t k = std::min<int64_t>(n, std::max<int64_t>(1, (int64_t)std::ceil(q * (double)n)));
+    std::nth_element(norms.begin(), norms.begin() + (k - 1), norms.end());
+    c->trust_radius = norms[(size_t)(k - 1)];
+    if (radius_out) *radius_out = c->trust_radius;
+    return SUR_OK;
+}
+
+int sur_trust(sur_ctx *c, const float *x_dev, int64_t B, int32_t *flags_dev) {
+    if (!c || B < 0 || (B > 0 && (!x_dev || !flags_dev))) return SUR_ERR_INVALID_ARG;
+    if (c->trust_radius < 0.0) return sfail(c, SUR_ERR_INVALID_ARG, "no trust radius (sur_fit_trust)");
+    if (B == 0) return SUR_OK;
+    row_norm_kernel<<<(unsigned)cdiv(B * 32, 256), 256, 0, c->stream>>>(x_dev, B, c->nin, nullptr,
+                                                                        c->trust_radius, flags_dev);
+    SCK(cudaGetLastError());
     return SUR_OK;
 }
 

@@ -114,6 +114,22 @@ class Surrogate:
                                     seed, ctypes.c_void_p(hist.ctypes.data)))
         return hist[:epochs]
 
+    def fit_trust(self, X, q=0.99) -> float:
+        """Trust radius from the training inputs X (CUDA float32 [n][n_in]): the q-quantile
+        of their norms (sur_fit_trust); returns it."""
+        _check_f32(X)
+        r = ctypes.c_double()
+        self._chk(self._L.sur_fit_trust(self._c, _dp(X), X.shape[0], float(q), ctypes.byref(r)))
+        return r.value
+
+    def trusted(self, x):
+        """Bool CUDA tensor [B]: inputs within the trust radius (sur_trust)."""
+        import torch
+        _check_f32(x)
+        flags = torch.empty(x.shape[0], dtype=torch.int32, device=x.device)
+        self._chk(self._L.sur_trust(self._c, _dp(x), x.shape[0], _dp(flags)))
+        return flags.bool()
+
     def close(self):
         if getattr(self, "_c", None):
             self._L.sur_destroy(self._c)
@@ -198,19 +214,59 @@ def solver_fields(mesh, fields_for, n_runs, S, params, modes, amp, n_steps, prec
     return out
 
 
-def pod(snapshots, r):
-    """POD of snapshot rows: (mean [D], modes phi [D][r] orthonormal, coefficients [n][r],
-    captured fraction of the fluctuation energy). Host linear algebra (set-up, not the
-    time loop): eigenpairs of the snapshot Gram matrix."""
-    X = np.asarray(snapshots, dtype=np.float32)
-    mean = X.mean(axis=0, dtype=np.float64)
-    Xc = X - mean.astype(np.float32)[None, :]
-    G = (Xc @ Xc.T).astype(np.float64)
-    w, V = np.linalg.eigh(G)
-    order = np.argsort(-w)
-    w, V = w[order], V[:, order]
-    sig = np.sqrt(np.maximum(w[:r], 1e-300))
-    phi = (Xc.T.astype(np.float64) @ V[:, :r]) / sig[None, :]
-    coef = V[:, :r] * sig[None, :]
-    frac = float(w[:r].sum() / max(w.sum(), 1e-300))
-    return mean, np.ascontiguousarray(phi), np.ascontiguousarray(coef), frac
+def pod(snapshots, r, stream=None):
+    """POD of snapshot rows on the device (sur_pod): (mean [D], modes phi [D][r]
+    orthonormal, coefficients [n][r], captured fraction of the fluctuation energy) as
+    numpy arrays. snapshots: numpy [n][D] or a CUDA float32 tensor."""
+    import torch
+    L = _lib.load()
+    X = snapshots if isinstance(snapshots, torch.Tensor) else torch.from_numpy(
+        np.ascontiguousarray(snapshots, dtype=np.float32)).cuda()
+    _check_f32(X)
+    n, D = X.shape
+    mean = torch.empty(D, dtype=torch.float32, device=X.device)
+    phi = torch.empty((D, r), dtype=torch.float32, device=X.device)
+    coef = torch.empty((n, r), dtype=torch.float32, device=X.device)
+    frac = ctypes.c_double()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.sur_pod(_dp(X), n, D, int(r), _dp(mean), _dp(phi), _dp(coef), None, ctypes.byref(frac), None,
+                   ctypes.c_void_p(s.cuda_stream))
+    if rc != 0:
+        raise EnsError(rc, "sur_pod failed")
+    return mean.cpu().numpy(), phi.cpu().numpy(), coef.cpu().numpy(), frac.value
+
+
+def pod_device(X, r, stream=None):
+    """sur_pod on a CUDA float32 tensor X [n][D]: (mean, phi, coef) CUDA tensors, the
+    eigenvalues [r] and captured fraction (host), and the iterations taken."""
+    import torch
+    L = _lib.load()
+    _check_f32(X)
+    n, D = X.shape
+    mean = torch.empty(D, dtype=torch.float32, device=X.device)
+    phi = torch.empty((D, r), dtype=torch.float32, device=X.device)
+    coef = torch.empty((n, r), dtype=torch.float32, device=X.device)
+    lam = np.zeros(r)
+    frac, iters = ctypes.c_double(), ctypes.c_int32()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.sur_pod(_dp(X), n, D, int(r), _dp(mean), _dp(phi), _dp(coef), ctypes.c_void_p(lam.ctypes.data),
+                   ctypes.byref(frac), ctypes.byref(iters), ctypes.c_void_p(s.cuda_stream))
+    if rc != 0:
+        raise EnsError(rc, "sur_pod failed")
+    return mean, phi, coef, lam, frac.value, iters.value
+
+def predict_with_fallback(net, xi, mean, phi, solve):
+    """Fields of the realisations xi [B][n_in] (CUDA float32): the network's prediction
+    u = mean + phi c (sur_forward, sur_reconstruct) where the input lies within the trust
+    radius (sur_trust), and the solver's own fields where it does not: solve(rows) runs the
+    plain solver on those rows' realisations and returns their fields [len(rows)][D] (for
+    example solver_fields), which are copied in unchanged. Returns (u [B][D] CUDA float32,
+    trusted [B] bool)."""
+    import torch
+    u = reconstruct(net.forward(xi), mean, phi)
+    trusted = net.trusted(xi)
+    bad = torch.nonzero(~trusted).flatten()
+    if bad.numel():
+        fields = np.ascontiguousarray(solve(bad.cpu().numpy()), dtype=np.float32)
+        u[bad] = torch.from_numpy(fields).to(u.device)
+    return u, trusted

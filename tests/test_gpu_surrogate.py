@@ -194,6 +194,58 @@ def test_surrogate_pipeline_beats_plain_ensemble_on_time_to_statistics():
     net.close()
 
 
+def test_untrusted_realisations_fall_back_to_the_solver():
+    """The plain solver is the surrogate's fallback: inputs outside the trust radius (the
+    0.99-quantile of the training inputs' norms) are flagged, and their fields in the
+    pipeline's output are the solver's, bit for bit; trusted rows are the network's
+    reconstruction. Four of the twelve test inputs are training-like draws scaled by 4
+    (norm about 11 against a radius near 4.5 for 8 standard-normal coefficients)."""
+    import synth
+    m = synth.aneurysm_mesh(24, 30)
+    basis = synth.kl_basis(m, 4)
+    n_train, S = 256, 64
+    xi = synth.kl_coefficients(n_train, 4, seed=9)
+    E_all, h_all = synth.kl_fields(basis, xi)
+    xt = synth.kl_coefficients(12, 4, seed=10)
+    xt[8:] *= 4.0
+    E_t, h_t = synth.kl_fields(basis, xt)
+    dt = synth.cfl_dt(m, np.concatenate([E_all, E_t], axis=1))
+    n_steps = int(round(0.01 / dt))
+    params = dict(rho=synth.configs.RHO, nu=synth.configs.NU, kshear=synth.configs.KSHEAR,
+                  alpha=synth.configs.ALPHA, dt=dt)
+    modes = synth.pressure_shear_modes(m, with_shear=True)
+    amp = synth.peak_amplitudes(n_steps, dt)
+    U = sur.solver_fields(m, lambda r: (E_all[:, r].copy(), h_all[:, r].copy()), n_train, S, params, modes,
+                          amp, n_steps)
+    mean, phi, coef, _ = sur.pod(U, 4)
+    cs = coef.std(axis=0)
+    net = sur.Surrogate(8, 32, 4, max_batch=256, seed=2)
+    X = _dev(xi)
+    net.train(X, _dev(coef / cs), epochs=60, batch=64, lr=3e-3, seed=1)
+    net.scale_outputs(cs)
+    radius = net.fit_trust(X, 0.99)
+    norms = np.sort(np.linalg.norm(xi.astype(np.float32).astype(np.float64), axis=1))
+    assert radius == pytest.approx(norms[int(np.ceil(0.99 * n_train)) - 1], rel=1e-12)
+
+    def solve(rows):
+        return sur.solver_fields(m, lambda r: (E_t[:, rows[r]].copy(), h_t[:, rows[r]].copy()), len(rows), S,
+                                 params, modes, amp, n_steps)
+
+    Xt, mean_d, phi_d = _dev(xt), _dev(mean), _dev(phi)
+    u, trusted = sur.predict_with_fallback(net, Xt, mean_d, phi_d, solve)
+    trusted = trusted.cpu().numpy()
+    expect = np.linalg.norm(xt.astype(np.float32).astype(np.float64), axis=1) <= radius
+    assert np.array_equal(trusted, expect) and not trusted[8:].any() and trusted[:8].sum() >= 6
+    u = u.cpu().numpy()
+    bad = np.flatnonzero(~trusted)
+    assert np.array_equal(u[bad], solve(bad))
+    plain = sur.reconstruct(net.forward(Xt), mean_d, phi_d).cpu().numpy()
+    assert np.array_equal(u[trusted], plain[trusted])
+    with pytest.raises(ens.EnsError):
+        sur.Surrogate(8, 32, 4, max_batch=16, seed=3).trusted(Xt)     # no radius fitted yet
+    net.close()
+
+
 def _bf16(a):
     """Round float32 values to BF16 (nearest, ties to even) and back, in numpy."""
     u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
