@@ -160,12 +160,9 @@ typedef struct {
                                the force loop, 8 and 9 persistent double-buffered
                                forms of 5 and 6, 10 and 11 the shapes of 6 and 4
                                staged from fixed-stride block records (binary32
-                               forms), 12 and 13 the shapes of 6 and 5 with every
-                               neighbour row staged in shared memory from halo
-                               records, 14 halo-staged 128x6 with four samples
-                               per thread (binary32 forms)                        */
-    float variant_us[16];   /* autotuner's time per step of shapes 0..14 (-1: n/a,
-                               0: not timed)                                      */
+                               forms)                                             */
+    float variant_us[16];   /* autotuner's time per step of shapes 0..11 (-1: n/a,
+                               0: not timed; entries 12..15 unused)               */
 } ens_info_t;
 
 /* Create a context: copies the mesh, builds the node-to-element incidence lists,

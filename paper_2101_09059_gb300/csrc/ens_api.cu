@@ -219,78 +219,6 @@ StagePlan record_plan(StagePlan p) {
     return p;
 }
 
-// The halo form of a staged plan (binary32 forms): for every block of nb nodes, the
-// distinct nodes its incidences touch (its own nodes first) and the distinct elements,
-// with every incidence re-expressed as slots into those lists. Fills the host records
-// (layout in StagePlan) and returns the plan, unstaged if the rows do not fit in shared
-// memory.
-StagePlan halo_plan(const ens_ctx *c, const std::vector<int32_t> &rowptr, const std::vector<int4> &ent,
-                    StagePlan base, std::vector<int4> *rec) {
-    StagePlan p = base;
-    p.staged = 0;
-    rec->clear();
-    if (!base.staged || c->form == kFP64) return p;
-    const int32_t N = c->N, nb = base.nb, Sp = c->Sp;
-    const int64_t nblk = (N + nb - 1) / nb;
-    std::vector<int32_t> nodes, elems;
-    auto slot = [](std::vector<int32_t> &v, int32_t id) -> int32_t {
-        for (size_t k = 0; k < v.size(); k++)
-            if (v[k] == id) return (int32_t)k;
-        v.push_back(id);
-        return (int32_t)v.size() - 1;
-    };
-    auto collect = [&](int64_t b) {
-        const int64_t n0 = b * nb, n1 = std::min<int64_t>(N, n0 + nb);
-        nodes.clear();
-        elems.clear();
-        for (int64_t i = n0; i < n1; i++) nodes.push_back((int32_t)i);
-        for (int32_t q = rowptr[n0]; q < rowptr[n1]; q++) {
-            slot(elems, ent[q].x);
-            slot(nodes, ent[q].y);
-            slot(nodes, ent[q].z);
-        }
-    };
-    int32_t hmax = 0, hemax = 0;
-    for (int64_t b = 0; b < nblk; b++) {
-        collect(b);
-        hmax = std::max<int32_t>(hmax, (int32_t)nodes.size());
-        hemax = std::max<int32_t>(hemax, (int32_t)elems.size());
-    }
-    p.rec = 1;
-    p.halo = 1;
-    p.h_max = hmax;
-    p.he_max = hemax;
-    p.rec_h = (nb + 3 + 3) / 4;
-    const int32_t hn4 = (hmax + 3) & ~3, he4 = (hemax + 3) & ~3;
-    p.halo_w = (hn4 + he4) / 4;
-    const int64_t words = (int64_t)p.rec_h + p.halo_w + p.cnt_max;
-    const size_t bytes = 16 + (size_t)words * 16 + (size_t)p.cnt_max * 80 + (size_t)hmax * 3 * Sp * 4 +
-                         (size_t)hemax * Sp * 4;
-    if (bytes > 200 * 1024) return p;
-    p.smem = (uint32_t)((bytes + 127) / 128 * 128);
-    rec->assign((size_t)(nblk * words), make_int4(0, 0, 0, 0));
-    for (int64_t b = 0; b < nblk; b++) {
-        collect(b);
-        const int64_t n0 = b * nb, n1 = std::min<int64_t>(N, n0 + nb);
-        int4 *r = rec->data() + b * words;
-        int32_t *hdr = reinterpret_cast<int32_t *>(r);
-        const int32_t pb = rowptr[n0];
-        for (int32_t k = 0; k <= nb; k++) hdr[k] = rowptr[std::min<int64_t>(n0 + k, n1)] - pb;
-        hdr[nb + 1] = (int32_t)nodes.size();
-        hdr[nb + 2] = (int32_t)elems.size();
-        int32_t *ids = reinterpret_cast<int32_t *>(r + p.rec_h);
-        for (size_t k = 0; k < nodes.size(); k++) ids[k] = nodes[k];
-        for (size_t k = 0; k < elems.size(); k++) ids[hn4 + k] = elems[k];
-        int4 *en = r + p.rec_h + p.halo_w;
-        for (int32_t q = pb; q < rowptr[n1]; q++) {
-            const int4 g = ent[q];
-            en[q - pb] = make_int4(slot(elems, g.x), slot(nodes, g.y), slot(nodes, g.z), g.w);
-        }
-    }
-    p.staged = 1;
-    return p;
-}
-
 // The pipelined (persistent, double-buffered) form of a staged plan.
 StagePlan pipelined_plan(StagePlan p) {
     if (!p.staged) return p;
@@ -658,11 +586,6 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                     cand[10] = record_plan(cand[6]);
                     cand[11] = record_plan(cand[4]);
                     if (cand[11].nb != cand[10].nb) cand[11].staged = 0;
-                    // every neighbour row staged from halo records: shapes of 6 and 5,
-                    // and 128 x 8 with four samples per thread
-                    cand[12] = cand[6];
-                    cand[13] = cand[5];
-                    if (rcp == ENS_OK) rcp = make_stage_plan(c, rowptr, 128, 6, &cand[14], 4);
                 }
             }
             if (rcp != ENS_OK) return rcp;
@@ -704,43 +627,6 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                 cand[k].rec_kc = c->rec_kc;
             }
             if (c->plan.rec) c->plan = cand[c->variant];  // a forced record shape
-        }
-        // halo records: one set per distinct block size among shapes 12..14
-        {
-            int hs = 0;
-            int32_t nb_of[2] = {0, 0};
-            for (int k = 12; k <= 14; k++) {
-                if (!cand[k].staged || cand[k].halo) continue;
-                std::vector<int4> hrec;
-                StagePlan hp = halo_plan(c, rowptr, ent, cand[k], &hrec);
-                int set = -1;
-                for (int q = 0; q < hs; q++)
-                    if (nb_of[q] == hp.nb) set = q;
-                if (hp.staged && set < 0 && hs < 2) {
-                    set = hs++;
-                    nb_of[set] = hp.nb;
-                    const int64_t nblk = (N + hp.nb - 1) / hp.nb;
-                    c->halo_ent[set] = (int4 *)dev_alloc(c, sizeof(int4) * hrec.size());
-                    c->halo_kc[set] = dev_alloc(c, sizeof(float) * (size_t)nblk * hp.cnt_max * 20);
-                    if (!c->halo_ent[set] || !c->halo_kc[set]) return fail(c, ENS_ERR_ALLOC, "halo records");
-                    CK(cudaMemcpyAsync(c->halo_ent[set], hrec.data(), sizeof(int4) * hrec.size(),
-                                       cudaMemcpyHostToDevice, c->stream));
-                    CK(launch_pack_records((const float *)c->kc, c->rowptr, N, hp.nb, hp.cnt_max,
-                                           (float *)c->halo_kc[set], c->stream));
-                    CK(cudaStreamSynchronize(c->stream));  // the host records leave scope
-                }
-                if (hp.staged && set >= 0) {
-                    hp.rec_ent = c->halo_ent[set];
-                    hp.rec_kc = c->halo_kc[set];
-                    cand[k] = hp;
-                } else {
-                    cand[k].staged = 0;
-                }
-            }
-            if (forced_v >= 12) {
-                c->plan = cand[forced_v];
-                c->variant = c->plan.staged ? forced_v : 0;
-            }
         }
         CK(launch_convert(m64, NSp, c->minv, to_f, 1, c->stream));
         if (to_f) {
@@ -815,19 +701,12 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
             rc0 = autotune(c, cand, kVariants);
             if (rc0 != ENS_OK) return rc0;
         }
-        if (!(c->plan.rec && !c->plan.halo) && c->rec_ent) {  // the records serve no chosen shape
+        if (!c->plan.rec && c->rec_ent) {  // the records serve no chosen shape
             dev_free(c, c->rec_ent);
             dev_free(c, c->rec_kc);
             c->rec_ent = nullptr;
             c->rec_kc = nullptr;
         }
-        for (int q = 0; q < 2; q++)
-            if (c->halo_ent[q] && !(c->plan.halo && c->plan.rec_ent == c->halo_ent[q])) {
-                dev_free(c, c->halo_ent[q]);
-                dev_free(c, c->halo_kc[q]);
-                c->halo_ent[q] = nullptr;
-                c->halo_kc[q] = nullptr;
-            }
         return ens_reset(c);
     }();
     if (rc != ENS_OK) {

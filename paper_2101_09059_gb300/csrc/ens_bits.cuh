@@ -146,17 +146,6 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
-// Per-thread asynchronous 16-byte copy global -> shared (cp.async, L2 only), and the wait
-// for every copy this thread issued. The copies hold no registers while in flight, so a
-// thread can have many outstanding; a __syncthreads after the wait publishes them to
-// the block. dst and src 16-byte aligned.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 // Programmatic dependent launch (PTX griddepcontrol). launch_dependents lets the next
 // kernel on the stream, launched with programmatic stream serialisation, start its
 // blocks before this grid finishes; wait blocks the calling thread until the grids this

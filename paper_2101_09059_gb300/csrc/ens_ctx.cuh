@@ -9,7 +9,7 @@
 #include "ens_internal.cuh"
 
 namespace ens {
-constexpr int kVariants = 15;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kVariants = 12;  // launch shapes the autotuner can time (see ens_info_t)
 constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
 }
 
@@ -48,8 +48,6 @@ struct ens_ctx {
     ens::StagePlan plan_fo{};  // launch shape of force-only evaluations
     int4 *rec_ent = nullptr;     // fixed-stride block records (record shapes only)
     void *rec_kc = nullptr;
-    int4 *halo_ent[2] = {nullptr, nullptr};  // halo records of the halo shapes (two block sizes)
-    void *halo_kc[2] = {nullptr, nullptr};
     int32_t variant = 0;
     float variant_us[ens::kVariants] = {};
     int32_t flags_in = 0;

@@ -96,15 +96,6 @@ struct StagePlan {
     int32_t rec_h;
     const int4 *rec_ent;
     const void *rec_kc;
-    // Halo records (halo = 1, binary32 forms, with rec = 1): block b's record holds rec_h
-    // header words (the nb + 1 block-local row offsets, then the counts of distinct halo
-    // nodes and elements), halo_w words of halo ids (h_max node ids with the block's own
-    // nodes first, then he_max element ids, each list padded to a multiple of 4), and
-    // cnt_max entries {element slot, node slot a, node slot b, corner} whose slots index
-    // the block's staged halo rows. The block copies those rows into shared memory once
-    // (cp.async by every thread), so its force loop reads shared memory only.
-    int32_t halo;
-    int32_t h_max, he_max, halo_w;
 };
 
 // One member of a batched launch (several contexts advanced by one kernel per step or

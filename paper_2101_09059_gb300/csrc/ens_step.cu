@@ -802,141 +802,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) step_staged_kernel(const StepArgs
     }
 }
 
-// Halo-staged kernel (binary32 forms). Thread 0 bulk-copies the block's halo record
-// (row offsets, halo node and element ids, slot-indexed entries) and coupling blocks;
-// then every thread issues cp.async copies of the halo rows: the 3 Sp displacement
-// values of every distinct node the block's incidences touch (its own nodes first) and
-// the Sp (E h) values of every distinct element. After one wait the force loop reads
-// only shared memory: one dependent round trip for all gathers instead of one per
-// incidence. Same operations in the same order as the other shapes (bitwise equal).
-template <int FORM, int BLOCK, int MINB, int V>
-__global__ void __launch_bounds__(BLOCK, MINB) step_halo_kernel(const StepArgs<float> a,
-                                                                const StagePlan pl) {
-    using R = float;
-    constexpr int KS = Kc<R>::stride;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    const int32_t nb_block = pl.nb, cnt_max = pl.cnt_max;
-    const int32_t hw = pl.rec_h, hx = pl.halo_w;
-    const int32_t words = hw + hx + cnt_max;
-    int4 *rec_s = reinterpret_cast<int4 *>(smem + 16);
-    const int32_t *hdr = reinterpret_cast<const int32_t *>(rec_s);
-    const int32_t *nid = reinterpret_cast<const int32_t *>(rec_s + hw);
-    const int32_t *eid = nid + ((pl.h_max + 3) & ~3);
-    const int4 *ent_s = rec_s + hw + hx;
-    R *kc_s = reinterpret_cast<R *>(rec_s + words);
-    const int32_t Q = a.fv.Q;
-    const int32_t Sp = a.fv.Sp;
-    R *uh = kc_s + (size_t)cnt_max * KS;          // [h_max][3][Sp]
-    R *ehh = uh + (size_t)pl.h_max * 3 * Sp;      // [he_max][Sp]
-    const int32_t N = a.fv.N;
-    const int32_t n0 = blockIdx.x * nb_block;
-    const int32_t nb = min(nb_block, N - n0);
-    const int32_t li = threadIdx.x / Q;
-    const int32_t s0 = (threadIdx.x - li * Q) * V;
-    const bool valid = li < nb;
-    const int32_t i = n0 + li;
-    grid_launch_dependents();  // the next step's blocks may stage their records early
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        fence_barrier_init();
-        const uint32_t b_rec = (uint32_t)words * 16u;
-        const uint32_t b_kc = (uint32_t)cnt_max * KS * (uint32_t)sizeof(R);
-        mbar_expect_tx(bar, b_rec + b_kc);
-        bulk_g2s(rec_s, pl.rec_ent + (size_t)blockIdx.x * words, b_rec, bar);
-        bulk_g2s(kc_s, static_cast<const R *>(pl.rec_kc) + (size_t)blockIdx.x * cnt_max * KS, b_kc, bar);
-    }
-    grid_dependency_wait();  // the state below is written by the previous step
-    if (threadIdx.x == 0) {
-        const size_t r0 = (size_t)n0 * 3 * Sp;
-        bulk_prefetch_l2(a.minv + (size_t)n0 * Sp, (uint32_t)(nb * Sp * sizeof(R)));
-        if constexpr (FORM == kKahan32) {
-            bulk_prefetch_l2(a.ulo + r0, (uint32_t)(nb * 3 * Sp * 4));
-            bulk_prefetch_l2(a.v32 + r0, (uint32_t)(nb * 3 * Sp * 4));
-        } else {
-            bulk_prefetch_l2(a.utail + r0, (uint32_t)(nb * 3 * Sp * 4));
-            bulk_prefetch_l2(a.v64 + r0, (uint32_t)(nb * 3 * Sp * 8));
-        }
-        if (a.J <= 4)
-            for (int32_t j = 0; j < a.J; j++)
-                prefetch_range_l2(a.modes + ((int64_t)j * N + n0) * 3, (uint32_t)(nb * 3 * sizeof(R)));
-        *reinterpret_cast<int64_t *>(smem + 8) = *a.step_ctr + a.k_off;
-    }
-    __syncthreads();
-    if (!mbar_wait(bar, 0, kWaitLimit)) {
-        if (threadIdx.x == 0) atomicOr(a.flags, 2);
-        mbar_wait(bar, 0, kWaitLimit);
-        return;
-    }
-    const int32_t n_hn = hdr[nb_block + 1], n_he = hdr[nb_block + 2];
-    if (n_hn < nb || n_hn > pl.h_max || n_he < 0 || n_he > pl.he_max) {  // not a record of this plan
-        if (threadIdx.x == 0) atomicOr(a.flags, 4);
-        return;
-    }
-    // halo rows in 16-byte chunks, (3 Sp / 4) per node and Sp / 4 per element: the block's
-    // threads cover whole rows per pass (the thread's row and chunk fixed, one division)
-    {
-        const int32_t cpn = 3 * Sp / 4, cpe = Sp / 4;
-        if (cpn <= BLOCK) {  // rows per pass >= 1
-            const int32_t rpn = BLOCK / cpn;
-            const int32_t jn = threadIdx.x / cpn, cn = threadIdx.x - jn * cpn;
-            if (jn < rpn)
-                for (int32_t j = jn; j < n_hn; j += rpn)
-                    cp_async16(uh + (size_t)j * 3 * Sp + 4 * cn, a.ug_cur + (size_t)nid[j] * 3 * Sp + 4 * cn);
-        } else {  // wide rows: every thread strides along each row
-            for (int32_t j = 0; j < n_hn; j++)
-                for (int32_t c = threadIdx.x; c < cpn; c += BLOCK)
-                    cp_async16(uh + (size_t)j * 3 * Sp + 4 * c, a.ug_cur + (size_t)nid[j] * 3 * Sp + 4 * c);
-        }
-        if (cpe <= BLOCK) {
-            const int32_t rpe = BLOCK / cpe;
-            const int32_t je = threadIdx.x / cpe, ce = threadIdx.x - je * cpe;
-            if (je < rpe)
-                for (int32_t j = je; j < n_he; j += rpe)
-                    cp_async16(ehh + (size_t)j * Sp + 4 * ce, a.fv.eh + (size_t)eid[j] * Sp + 4 * ce);
-        } else {
-            for (int32_t j = 0; j < n_he; j++)
-                for (int32_t c = threadIdx.x; c < cpe; c += BLOCK)
-                    cp_async16(ehh + (size_t)j * Sp + 4 * c, a.fv.eh + (size_t)eid[j] * Sp + 4 * c);
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (!valid) return;
-    const int32_t p0 = hdr[li], p1 = hdr[li + 1];
-    if (p0 < 0 || p1 < p0 || p1 > cnt_max) {
-        atomicOr(a.flags, 4);
-        return;
-    }
-    R ui[3][V];
-#pragma unroll
-    for (int d = 0; d < 3; d++)
-#pragma unroll
-        for (int v = 0; v < V; v++) ui[d][v] = uh[((size_t)li * 3 + d) * Sp + s0 + v];
-    R f[3][V];
-#pragma unroll
-    for (int d = 0; d < 3; d++)
-#pragma unroll
-        for (int v = 0; v < V; v++) f[d][v] = R(0);
-    for (int32_t p = p0; p < p1; ++p) {
-        const int4 en = ent_s[p];
-        R ua[3][V], ub[3][V], ev[V];
-#pragma unroll
-        for (int d = 0; d < 3; d++)
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                ua[d][v] = uh[((size_t)en.y * 3 + d) * Sp + s0 + v];
-                ub[d][v] = uh[((size_t)en.z * 3 + d) * Sp + s0 + v];
-            }
-#pragma unroll
-        for (int v = 0; v < V; v++) ev[v] = ehh[(size_t)en.x * Sp + s0 + v];
-        apply_incidence<R, V>(ua, ub, ev, kc_s + (size_t)p * KS, ui, f);
-    }
-    R fe[3];
-    node_traction<R>(a, i, lds_step(smem + 8), fe);
-    node_update<FORM, R, V>(a, i, s0, ui, f, fe);
-}
-
 // Persistent, double-buffered form of the staged kernel. Each CTA walks the node tiles
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps the bulk copies (TMA) of the
 // tile after next in flight in the other half of a two-buffer shared-memory ring while the
@@ -1335,25 +1200,6 @@ cudaError_t launch_staged(const StepArgs<R> &a0, cudaStream_t s, const StagePlan
     return e;
 }
 
-template <int FORM, int BLOCK, int MINB, int V>
-cudaError_t launch_halo(const StepArgs<float> &a0, cudaStream_t s, const StagePlan *plan) {
-    auto *k = step_halo_kernel<FORM, BLOCK, MINB, V>;
-    StepArgs<float> a = a0;
-    a.fv.Q = a.fv.Sp / V;
-    if (plan->smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
-        if (e != cudaSuccess) {
-            note_launch("cudaFuncSetAttribute", BLOCK, MINB, plan->smem, e);
-            return e;
-        }
-    }
-    const unsigned grid = (unsigned)((a.fv.N + plan->nb - 1) / plan->nb);
-    cudaError_t e = launch_pdl(k, grid, BLOCK, plan->smem, s, a, *plan);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) note_launch("halo launch", BLOCK, MINB, plan->smem, e);
-    return e;
-}
-
 template <int FORM, typename R, int BLOCK, int MINB, int V>
 cudaError_t launch_pipelined(const StepArgs<R> &a0, cudaStream_t s, const StagePlan *plan) {
     auto *k = step_pipelined_kernel<FORM, R, BLOCK, MINB, V>;
@@ -1400,11 +1246,6 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
                 if (plan->pipelined) {
                     if (plan->block == 128) return launch_pipelined<FORM, R, 128, 8, 2>(a, s, plan);
                     return launch_pipelined<FORM, R, 256, 4, 2>(a, s, plan);
-                }
-                if (plan->halo) {
-                    if (plan->vw == 4) return launch_halo<FORM, 128, 6, 4>(a, s, plan);
-                    if (plan->block == 256) return launch_halo<FORM, 256, 5, 2>(a, s, plan);
-                    return launch_halo<FORM, 128, 10, 2>(a, s, plan);
                 }
                 if (plan->rec) {
                     if (plan->vw == 2) return launch_staged<FORM, R, FO, 128, 10, 2, false, true>(a, s, plan);

@@ -95,6 +95,64 @@ __device__ __forceinline__ uint32_t core_off(int r, int k) {
     return (uint32_t)(r >> 3) * kCoreMN + (uint32_t)(k >> 3) * kCoreK + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
 }
 
+// One K stage of an operand tile (ROWS rows x TK k) held in registers as 16-byte vectors
+// (VR = ROWS * TK / (4 kThreads) per thread). Layout 1: k contiguous in memory (row stride
+// sr, a multiple of 4), the vector runs along k; layout 2: rows contiguous (k stride sk, a
+// multiple of 4), the vector runs along the rows. Rows beyond R and k beyond K (both
+// multiples of 4 in these layouts) read as zero.
+template <int ROWS>
+struct VecStage {
+    static constexpr int VR = ROWS * TK / (4 * kThreads);
+    float4 v[VR];
+    __device__ __forceinline__ void load(const float *__restrict__ src, int layout, long long sr, long long sk, int r0,
+                                         int R, int k0, int K, int tid) {
+#pragma unroll
+        for (int j = 0; j < VR; j++) {
+            const int q = tid + j * kThreads;
+            int rr, kk;
+            if (layout == 1) {
+                rr = q / (TK / 4);
+                kk = (q - rr * (TK / 4)) * 4;
+            } else {
+                kk = q / (ROWS / 4);
+                rr = (q - kk * (ROWS / 4)) * 4;
+            }
+            const int r = r0 + rr, k = k0 + kk;
+            v[j] = (r < R && k < K) ? __ldg(reinterpret_cast<const float4 *>(src + (long long)r * sr + (long long)k * sk))
+                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+    __device__ __forceinline__ void store(unsigned char *dst, int layout, int tid) const {
+#pragma unroll
+        for (int j = 0; j < VR; j++) {
+            const int q = tid + j * kThreads;
+            const float x[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+            if (layout == 1) {
+                const int rr = q / (TK / 4), kk = (q - rr * (TK / 4)) * 4;
+                __nv_bfloat16 h[4];
+#pragma unroll
+                for (int t = 0; t < 4; t++) h[t] = __float2bfloat16_rn(x[t]);
+                // four consecutive k of one row: 8 contiguous bytes of a core matrix
+                *reinterpret_cast<uint2 *>(dst + core_off(rr, kk)) = *reinterpret_cast<const uint2 *>(h);
+            } else {
+                const int kk = q / (ROWS / 4), rr = (q - kk * (ROWS / 4)) * 4;
+#pragma unroll
+                for (int t = 0; t < 4; t++)
+                    *reinterpret_cast<__nv_bfloat16 *>(dst + core_off(rr + t, kk)) = __float2bfloat16_rn(x[t]);
+            }
+        }
+    }
+};
+
+// Vector layout of an operand with element (r, k) at src[r sr + k sk]: 1 or 2 as in
+// VecStage, 0 for the scalar path.
+__device__ __forceinline__ int vec_layout(const float *src, long long sr, long long sk, int R, int K) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) != 0) return 0;
+    if (sk == 1 && (sr & 3) == 0 && (K & 3) == 0) return 1;
+    if (sr == 1 && (sk & 3) == 0 && (R & 3) == 0) return 2;
+    return 0;
+}
+
 // C[M][N] (row stride ldc) = epilogue( sum_k A(m, k) B(k, n) ), FP32 sources staged to BF16.
 // A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn]. Out-of-range elements
 // are read as zero and not written.
@@ -127,7 +185,47 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
     const uint32_t tmem = *tslot;
     bool ok = true;
     uint32_t phase = 0;
-    for (int k0 = 0; k0 < K && ok; k0 += TK) {
+    const int la = vec_layout(A, sam, sak, M, K), lb = vec_layout(B, sbn, sbk, N, K);
+    if (la != 0 && lb != 0) {
+        // vector path: a stage's loads are issued together, and the next stage's while the
+        // tensor cores work on the current one
+        VecStage<TM> va;
+        VecStage<TN> vb;
+        va.load(A, la, sam, sak, m0, M, 0, K, tid);
+        vb.load(B, lb, sbn, sbk, n0, N, 0, K, tid);
+        for (int k0 = 0; k0 < K && ok; k0 += TK) {
+            va.store(As, la, tid);
+            vb.store(Bs, lb, tid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int ks = 0; ks < TK / 16; ks++) {
+                    const uint64_t ad = smem_desc(As + ks * 2 * kCoreK, kCoreK, kCoreMN);
+                    const uint64_t bd = smem_desc(Bs + ks * 2 * kCoreK, kCoreK, kCoreMN);
+                    const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 ens::smem_addr(bar))
+                             : "memory");
+            }
+            if (k0 + TK < K) {
+                va.load(A, la, sam, sak, m0, M, k0 + TK, K, tid);
+                vb.load(B, lb, sbn, sbk, n0, N, k0 + TK, K, tid);
+            }
+            ok = ens::mbar_wait(bar, phase, kTcWait);
+            phase ^= 1u;
+            tc_fence_after();
+            ok = __syncthreads_and(ok);
+        }
+    }
+    for (int k0 = 0; k0 < K && ok && (la == 0 || lb == 0); k0 += TK) {
         // loads in groups of 8 (issued together), then their conversions and shared stores
         constexpr int kA = TM * TK / kThreads, kB = TN * TK / kThreads, kG = 8;
 #pragma unroll 1
