@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--drift", action="store_true", help="long-run drift study instead of the benchmark")
     ap.add_argument("--drift-arch-elems", type=int, default=100_000)
     ap.add_argument("--drift-studies", default="energy,aneurysm,arch",
-                    help="comma list of: energy, aneurysm, arch, arch_full")
+                    help="comma list of: energy, aneurysm, arch, arch_full, oracle_period")
     ap.add_argument("--sur-train", type=int, default=4096)
     ap.add_argument("--sur-val", type=int, default=512)
     ap.add_argument("--sur-epochs", type=int, default=400)
@@ -753,6 +753,41 @@ def energy_drift(pkg, synth, name, stream, local, n_total, checkpoints):
     return out
 
 
+def oracle_period(pkg, synth, stream, local, n_total=20_000, picks=tuple(range(0, 64, 4)), checkpoints=16):
+    """The 200k-node aneurysm for n_total steps (34 times the damping horizon 1/(alpha dt))
+    for 16 of its 64 realisations (realisations are independent, so a 16-realisation
+    ensemble steps each exactly as the full one does; the oracle runs one realisation per
+    host core): every device form and the binary64 CPU oracle, rel-L2 of the device forms
+    against the oracle at `checkpoints` equally spaced steps."""
+    import oracle
+    case = synth.make_case("aneurysm", S=64, n_steps=n_total + 1, seed=0)
+    sub = dict(case, E=case["E"][:, list(picks)], h=case["h"][:, list(picks)], S=len(picks))
+    chunk = n_total // checkpoints
+    dev = {}
+    t0 = time.perf_counter()
+    for form in ("fp64", "fp32_force", "kahan32"):
+        e = pkg.Ensemble.from_case(sub, precision=form, stream=stream, device=local)
+        snaps = []
+        for _ in range(checkpoints):
+            e.step(chunk)
+            snaps.append(e.displacement())
+        e.close()
+        dev[form] = snaps
+    t_gpu = time.perf_counter() - t0
+    mod = oracle.Model(sub)
+    up, uc = mod.start()
+    curve = {f: [] for f in dev}
+    t0 = time.perf_counter()
+    for k in range(checkpoints):
+        mod.steps(up, uc, k * chunk, chunk)
+        for f in dev:
+            curve[f].append(float(np.linalg.norm(dev[f][k] - uc) / np.linalg.norm(uc)))
+    return {"workload": f"aneurysm: {case['mesh'].n_nodes} nodes, {len(picks)} of its 64 realisations, "
+                        f"dt {case['dt']:.3e} s, {chunk * checkpoints} steps",
+            "rel_l2_vs_oracle": curve, "max_rel_l2": {f: max(c) for f, c in curve.items()},
+            "gpu_s": t_gpu, "oracle_s": time.perf_counter() - t0, "oracle_threads": oracle.num_threads()}
+
+
 def run_drift(args, local):
     """Drift of the binary32 forms against the binary64 GPU form over long runs, on the same
     4 realisations (realisations are independent, so a 4-sample ensemble steps each of them
@@ -773,6 +808,8 @@ def run_drift(args, local):
         studies.append(("aneurysm", dict(name="aneurysm", S=64), [0, 21, 42, 63], 1, None))
     if "arch" in want:
         studies.append(("arch", dict(name="arch", S=8, target_elems=args.drift_arch_elems), [0, 3, 5, 7], 3, None))
+    if "oracle_period" in want:
+        out["oracle_period"] = oracle_period(pkg, synth, stream, local)
     if "arch_full" in want:  # the configuration's size: 256 realisations, binary64 on 16 of them
         studies.append(("arch_full", dict(name="arch", S=256), list(range(0, 256, 16)), 1, ("kahan32",)))
     for label, spec, picks, periods, only in studies:

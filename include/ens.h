@@ -160,9 +160,10 @@ typedef struct {
                                the force loop, 8 and 9 persistent double-buffered
                                forms of 5 and 6, 10 and 11 the shapes of 6 and 4
                                staged from fixed-stride block records (binary32
-                               forms)                                             */
-    float variant_us[16];   /* autotuner's time per step of shapes 0..11 (-1: n/a,
-                               0: not timed; entries 12..15 unused)               */
+                               forms), 12 shape 11 at 10 blocks per SM (more
+                               registers per thread)                              */
+    float variant_us[16];   /* autotuner's time per step of shapes 0..12 (-1: n/a,
+                               0: not timed; entries 13..15 unused)               */
 } ens_info_t;
 
 /* Create a context: copies the mesh, builds the node-to-element incidence lists,

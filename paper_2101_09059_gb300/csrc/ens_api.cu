@@ -586,6 +586,10 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
                     cand[10] = record_plan(cand[6]);
                     cand[11] = record_plan(cand[4]);
                     if (cand[11].nb != cand[10].nb) cand[11].staged = 0;
+                    // shape 11 with more registers per thread (10 resident blocks): the
+                    // binary64 update of the FP32-force form spills at 12
+                    cand[12] = cand[11];
+                    cand[12].minb = 10;
                 }
             }
             if (rcp != ENS_OK) return rcp;
@@ -622,7 +626,7 @@ int ens_create(const ens_mesh *mesh, int32_t S, const double *E_node, const doub
             CK(launch_pack_records((const float *)c->kc, c->rowptr, N, rp.nb, rp.cnt_max, (float *)c->rec_kc,
                                    c->stream));
             CK(cudaStreamSynchronize(c->stream));  // the host records leave scope
-            for (int k : {10, 11}) {
+            for (int k : {10, 11, 12}) {
                 cand[k].rec_ent = c->rec_ent;
                 cand[k].rec_kc = c->rec_kc;
             }

@@ -9,7 +9,7 @@
 #include "ens_internal.cuh"
 
 namespace ens {
-constexpr int kVariants = 12;  // launch shapes the autotuner can time (see ens_info_t)
+constexpr int kVariants = 13;  // launch shapes the autotuner can time (see ens_info_t)
 constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
 }
 

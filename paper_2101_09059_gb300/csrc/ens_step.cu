@@ -1249,6 +1249,7 @@ cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *pl
                 }
                 if (plan->rec) {
                     if (plan->vw == 2) return launch_staged<FORM, R, FO, 128, 10, 2, false, true>(a, s, plan);
+                    if (plan->minb == 10) return launch_staged<FORM, R, FO, 64, 10, 4, false, true>(a, s, plan);
                     return launch_staged<FORM, R, FO, 64, 12, 4, false, true>(a, s, plan);
                 }
                 if (plan->vw == 2) {

@@ -327,9 +327,12 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, con
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// loss = sum (y - t)^2 / count (one block, fixed order); dy = 2 (y - t) / count.
+// loss = sum (y - t)^2 / count (one block, fixed order); dy = 2 (y - t) / count; with db,
+// also the output layer's bias gradient db[n] = sum_m dy[m][n] (rows of `cols` values), in
+// the order of colsum_kernel.
 __global__ void mse_kernel(const float *__restrict__ y, const float *__restrict__ tgt, long long count,
-                           float *__restrict__ dy, float *__restrict__ loss_out) {
+                           float *__restrict__ dy, float *__restrict__ loss_out, int cols = 0,
+                           float *__restrict__ db = nullptr) {
     __shared__ double part[256];
     double s = 0.0;
     const float scale = 2.0f / (float)count;
@@ -345,6 +348,14 @@ __global__ void mse_kernel(const float *__restrict__ y, const float *__restrict_
         __syncthreads();
     }
     if (threadIdx.x == 0 && loss_out) *loss_out = (float)(part[0] / (double)count);
+    if (db && dy) {  // dy of this block is visible after the barriers above
+        const long long rows = count / cols;
+        for (int n = threadIdx.x; n < cols; n += blockDim.x) {
+            float t = 0.0f;
+            for (long long m = 0; m < rows; m++) t += dy[m * cols + n];
+            db[n] = t;
+        }
+    }
 }
 
 // db[n] = sum_m dz[m][n] (one thread per column, fixed order).
@@ -365,22 +376,42 @@ __global__ void gather_rows_kernel(const float *__restrict__ src, const int *__r
     dst[e] = src[(long long)perm[off + i] * cols + c];
 }
 
-// Advance the Adam step t and form its bias corrections 1 - b1^t and 1 - b2^t once, in
-// binary64 from the same binary32 betas the moment recurrences use: in binary32 the
-// subtraction 1 - b2^t cancels (b2 = 0.999 leaves about 3e-3 at t = 3) and its rounding
-// error of the power becomes a relative error of about 1e-5 in the second moment.
-__global__ void tick_kernel(int *t, float b1, float b2, float *corr) {
-    const int n = *t + 1;
-    *t = n;
-    corr[0] = (float)(1.0 - pow((double)b1, (double)n));
-    corr[1] = (float)(1.0 - pow((double)b2, (double)n));
+// One training step's inputs and targets gathered together (rows * (ca + cb) threads), and
+// the Adam step counter advanced for the update that ends the step.
+__global__ void gather_step_kernel(const float *__restrict__ A, const float *__restrict__ B, const int *__restrict__ perm,
+                                   int off, int rows, int ca, int cb, float *__restrict__ da, float *__restrict__ db,
+                                   int *tstep) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) *tstep += 1;
+    const long long na = (long long)rows * ca;
+    if (e < na) {
+        const int i = (int)(e / ca), c = (int)(e % ca);
+        da[e] = A[(long long)perm[off + i] * ca + c];
+    } else if (e < na + (long long)rows * cb) {
+        const long long f = e - na;
+        const int i = (int)(f / cb), c = (int)(f % cb);
+        db[f] = B[(long long)perm[off + i] * cb + c];
+    }
 }
 
+__global__ void tick_kernel(int *t) { *t += 1; }
+
 // Adam (bias-corrected): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
-// p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), corr = {1 - b1^t, 1 - b2^t}.
+// p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), t = *tstep (already advanced).
+// Each block forms the bias corrections once, in binary64 from the same binary32 betas the
+// moment recurrences use: in binary32 the subtraction 1 - b2^t cancels (b2 = 0.999 leaves
+// about 3e-3 at t = 3) and its rounding error of the power becomes a relative error of
+// about 1e-5 in the second moment.
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                            float *__restrict__ v, long long n, const float *__restrict__ corr, float lr,
+                            float *__restrict__ v, long long n, const int *__restrict__ tstep, float lr,
                             float b1, float b2, float eps) {
+    __shared__ float corr[2];
+    if (threadIdx.x == 0) {
+        const double t = (double)*tstep;
+        corr[0] = (float)(1.0 - pow((double)b1, t));
+        corr[1] = (float)(1.0 - pow((double)b2, t));
+    }
+    __syncthreads();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float c1 = corr[0], c2 = corr[1];
@@ -526,7 +557,6 @@ struct sur_ctx {
     float *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *y = nullptr;
     float *dy = nullptr, *d2 = nullptr, *d1 = nullptr;
     float *xb = nullptr, *tb = nullptr, *loss = nullptr;
-    float *corr = nullptr;  // Adam bias corrections {1 - b1^t, 1 - b2^t} of the current step
     double trust_radius = -1.0;  // inputs with a larger norm are not trusted (sur_fit_trust)
     int *tstep = nullptr, *perm = nullptr;
     long long perm_n = 0;
@@ -588,11 +618,10 @@ int backward(sur_ctx *c, cudaStream_t s, const float *x, const float *t, int B, 
     float *gb2 = c->g + c->off[3], *gW3 = c->g + c->off[4], *gb3 = c->g + c->off[5];
     int rc = forward(c, s, x, B);
     if (rc != SUR_OK) return rc;
-    mse_kernel<<<1, 256, 0, s>>>(c->y, t, (long long)B * no, c->dy, loss_dev);
+    mse_kernel<<<1, 256, 0, s>>>(c->y, t, (long long)B * no, c->dy, loss_dev, no, gb3);  // and db3
     SCK(cudaGetLastError());
-    // layer 3: dW3 = dy^T a2, db3 = colsum dy, d2 = (dy W3) * gelu'(z2)
+    // layer 3: dW3 = dy^T a2, db3 = colsum dy (above), d2 = (dy W3) * gelu'(z2)
     SCK((gemm<kStore>(s, no, H, B, c->dy, 1, no, c->a2, H, 1, gW3, H)));
-    colsum_kernel<<<cdiv(no, 128), 128, 0, s>>>(c->dy, B, no, gb3);
     SCK((gemm<kGeluGrad>(s, B, H, no, c->dy, no, 1, W3, H, 1, c->d2, H, nullptr, c->z2)));
     // layer 2
     SCK((gemm<kStore>(s, H, H, B, c->d2, 1, H, c->a1, H, 1, gW2, H)));
@@ -605,9 +634,11 @@ int backward(sur_ctx *c, cudaStream_t s, const float *x, const float *t, int B, 
     return SUR_OK;
 }
 
-int adam(sur_ctx *c, cudaStream_t s, float lr) {
-    tick_kernel<<<1, 1, 0, s>>>(c->tstep, c->b1, c->b2, c->corr);
-    adam_kernel<<<cdiv(c->np, 256), 256, 0, s>>>(c->p, c->g, c->m, c->v, c->np, c->corr, lr, c->b1,
+// The Adam update; tick = false when the step counter was already advanced (training
+// steps advance it in their gather kernel).
+int adam(sur_ctx *c, cudaStream_t s, float lr, bool tick = true) {
+    if (tick) tick_kernel<<<1, 1, 0, s>>>(c->tstep);
+    adam_kernel<<<cdiv(c->np, 256), 256, 0, s>>>(c->p, c->g, c->m, c->v, c->np, c->tstep, lr, c->b1,
                                                 c->b2, c->eps);
     SCK(cudaGetLastError());
     return SUR_OK;
@@ -659,7 +690,7 @@ int sur_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch,
             (r = salloc(c, &c->y, B * n_out)) || (r = salloc(c, &c->dy, B * n_out)) ||
             (r = salloc(c, &c->d2, B * H)) || (r = salloc(c, &c->d1, B * H)) ||
             (r = salloc(c, &c->xb, B * n_in)) || (r = salloc(c, &c->tb, B * n_out)) ||
-            (r = salloc(c, &c->loss, 1)) || (r = salloc(c, &c->tstep, 1)) || (r = salloc(c, &c->corr, 2)))
+            (r = salloc(c, &c->loss, 1)) || (r = salloc(c, &c->tstep, 1)))
             return r;
         // Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation from a seeded generator.
         std::vector<float> h(c->np, 0.0f);
@@ -770,12 +801,10 @@ int sur_train(sur_ctx *c, const float *X_dev, const float *T_dev, int64_t n, int
         SCK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         int rc = SUR_OK;
         for (long long st = 0; st < steps && rc == SUR_OK; st++) {
-            gather_rows_kernel<<<cdiv((long long)batch * c->nin, 256), 256, 0, c->cap>>>(
-                X_dev, c->perm, (int)(st * batch), batch, c->nin, c->xb);
-            gather_rows_kernel<<<cdiv((long long)batch * c->nout, 256), 256, 0, c->cap>>>(
-                T_dev, c->perm, (int)(st * batch), batch, c->nout, c->tb);
+            gather_step_kernel<<<cdiv((long long)batch * (c->nin + c->nout), 256), 256, 0, c->cap>>>(
+                X_dev, T_dev, c->perm, (int)(st * batch), batch, c->nin, c->nout, c->xb, c->tb, c->tstep);
             rc = backward(c, c->cap, c->xb, c->tb, batch, c->loss_hist + st);
-            if (rc == SUR_OK) rc = adam(c, c->cap, lr);
+            if (rc == SUR_OK) rc = adam(c, c->cap, lr, false);
         }
         cudaError_t e = cudaStreamEndCapture(c->cap, &g);
         if (rc != SUR_OK) {

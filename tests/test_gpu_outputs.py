@@ -206,3 +206,22 @@ def test_running_peak_members_cannot_join_a_batch():
     assert ei.value.code == -8
     a.close()
     b.close()
+
+
+def test_full_size_aneurysm_running_peak_sampled():
+    """The 200k-node aneurysm at S = 64, FP32-force, peak recorded every 10 steps over 1000
+    steps: two realisations against the oracle's peak (realisations are independent, so the
+    subset is exact), within the form's trajectory tolerance."""
+    from paper_2101_09059_gb300.ensemble import QTY_PEAK_MAGNITUDE
+    case = synth.make_case("aneurysm", S=64, n_steps=1000, seed=0)
+    e = ens.Ensemble.from_case(case, precision="fp32_force")
+    e.set_peak(10)
+    e.step(1000)
+    p = e.quantity_device(QTY_PEAK_MAGNITUDE).cpu().numpy()
+    e.close()
+    picks = [5, 50]
+    ref, _, _ = oo.peak_magnitude(oracle.Model(case, samples=picks), 1000, 10)
+    for k, s in enumerate(picks):
+        err = np.abs(p[:, s] - ref[:, k]).max() / np.abs(ref[:, k]).max()
+        print(f"aneurysm peak sample {s}: max rel {err:.2e}")
+        assert err < TOL["fp32_force"]

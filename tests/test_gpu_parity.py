@@ -439,7 +439,7 @@ def test_every_launch_shape_is_bitwise_identical(precision, S):
     # the tuned context timed every candidate shape that applies
     tuned = runs[0][1]["variant_us"]
     assert tuned[0] > 0 and tuned[1] > 0
-    for k in range(12):                # every launch shape, forced
+    for k in range(13):                # every launch shape, forced
         e = ens.Ensemble.from_case(case, precision=precision, flags=ens.ensemble.FLAG_FORCE_VARIANT(k))
         e.step(80)
         assert np.array_equal(e.displacement(), base), k
@@ -468,7 +468,7 @@ def test_block_records_with_uneven_blocks(precision, J):
     e.step(60)
     base = e.displacement()
     e.close()
-    for k in (10, 11):
+    for k in (10, 11, 12):
         e = ens.Ensemble.from_case(case, precision=precision, flags=ens.ensemble.FLAG_FORCE_VARIANT(k))
         assert e.info()["kernel_variant"] == k
         e.step(60)
