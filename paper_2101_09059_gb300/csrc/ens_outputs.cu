@@ -403,12 +403,10 @@ cudaError_t launch_peak(int form, const void *u_main, const void *aux, int32_t N
     (void)aux;
     const int64_t n = (int64_t)N * Sp;
     if (n == 0) return cudaSuccess;
-    static int sms = 0;  // multiprocessors of the device (looked up once)
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 132;
-    }
+    int dev = 0, sms = 0;  // multiprocessors of the current device
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+        sms = 148;
     const unsigned g = (unsigned)std::min<int64_t>(blocks_for(n, 256), (int64_t)sms * 8);
     if (form == kFP64)
         peak_kernel<kFP64><<<g, 256, 0, s>>>(u_main, N, Sp, step_ctr, k_off, stride, peak);
