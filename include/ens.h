@@ -218,13 +218,15 @@ int ens_reset(ens_ctx *ctx);
  * on its deformed surface X + u_s,m (scaled by the same (E h)_e,s), and the steps from m
  * use f_int(u_n) = f_int(u_m) + K(X + u_m) (u_n - u_m). Before the first re-assembly the
  * run is the linear method (bit for bit). k = 0 returns to the linear method and frees
- * the per-realisation data: two block buffers of nnz * 18 * Sp values in the form's force
- * precision (binary64 for ENS_FP64, binary32 otherwise) and the force correction
+ * the per-realisation data: two block buffers of E * 27 * Sp values (the element
+ * matrix's three corner blocks K_01, K_12, K_20, the others being their transposes) in
+ * the form's force precision (binary64 for ENS_FP64, binary32 otherwise) and the force correction
  * f_int(u_m) - K_m u_m, N * 3 * Sp values in binary64 plus its force-precision copy.
  * ens_reset and ens_set_state return to the linear stiffness with a zero correction (the
  * checkpoint holds neither); ens_internal_force keeps the reference blocks. A step with
- * per-realisation blocks streams them (72 B per incidence and sample in binary32)
- * instead of the shared ones, several times the bytes of a linear step; a re-assembly
+ * per-realisation blocks streams them (108 B per element and sample in binary32, each
+ * block read by the two corners it couples) instead of the shared ones, several times
+ * the bytes of a linear step; a re-assembly
  * costs one binary64 pass over the elements and samples and two force evaluations.
  * Selective re-assembly (k > 1) uses the stiffness of a segment's start for the whole
  * segment, a path error of order k. An element that degenerates on its deformed surface

@@ -354,7 +354,7 @@ void ctx_free(ens_ctx *c, void *p) { dev_free(c, p); }
 int geometry_reassemble(ens_ctx *c) {
     const void *aux = c->form == kFP32Force ? (const void *)c->utail : (const void *)c->ulo;
     const int next = c->geo_active ? c->kcs_cur ^ 1 : c->kcs_cur;
-    CK(launch_reassemble(c->form, c->xyz_d, c->tri_d, c->ec2ent_d, c->E, c->Sp, c->nu, c->ks, c->ug[c->cur], aux,
+    CK(launch_reassemble(c->form, c->xyz_d, c->tri_d, c->E, c->Sp, c->nu, c->ks, c->ug[c->cur], aux,
                          c->kcs[next], c->flags, c->stream));
     if (c->form == kFP64) {
         StepArgs<double> a = make_args<double>(c);
@@ -949,7 +949,7 @@ int ens_set_geometry_update(ens_ctx *c, int32_t k) {
     const size_t n = (size_t)c->N * 3 * c->Sp;
     for (int q = 0; q < 2; q++)
         if (!c->kcs[q]) {
-            c->kcs[q] = dev_alloc(c, elem_size(c->form) * (size_t)c->nnz * 18 * c->Sp);
+            c->kcs[q] = dev_alloc(c, elem_size(c->form) * (size_t)c->E * 27 * c->Sp);
             if (!c->kcs[q]) return fail(c, ENS_ERR_ALLOC, "per-realisation coupling blocks");
         }
     if (!c->geo_c64) {

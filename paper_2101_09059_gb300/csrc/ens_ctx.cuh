@@ -70,8 +70,8 @@ struct ens_ctx {
     // running peak of |u| per node and sample [N][Sp] (ens_set_peak)
     double *peak = nullptr;
     int32_t peak_stride = 0;
-    // geometry update (ens_set_geometry_update): per-realisation coupling blocks
-    // [nnz][18][Sp] of the deformed surface (two buffers: old and new during a
+    // geometry update (ens_set_geometry_update): per-realisation corner blocks
+    // [E][3][9][Sp] of the deformed surface (two buffers: old and new during a
     // re-assembly), re-assembled every geo_k steps, and the force correction
     // c = f_int(u_m) - K_m u_m [N][3][Sp] in binary64 and in the force precision.
     // Until the first re-assembly (geo_active false) the linear kernels run.

@@ -66,7 +66,7 @@ struct StepArgs {
     double c1, c2, dt;  // v_new = c1 v + c2 a ; u_new = u + dt v_new
     float c1f, c2f, dtf;  // the same constants rounded to binary32 (binary32 forms)
     double *force_out;  // force-only mode: [N][3][Sp] binary64
-    const R *kcs;       // geometry update: per-realisation coupling blocks [nnz][18][Sp]
+    const R *kcs;       // geometry update: per-realisation corner blocks [E][3][9][Sp]
     const R *kcorr;     // geometry update: force correction f_int(u_m) - K_m u_m [N][3][Sp]
     int *flags;         // [0] bit 0: non-finite seen, bit 1: a bounded wait gave up
 };
@@ -182,12 +182,12 @@ cudaError_t launch_setup_mass_elem(const int32_t *rowptr, const int4 *ent, const
                                    const double *rhoh, int32_t N, int32_t Sp, double *m64, cudaStream_t s);
 cudaError_t launch_modulus_from_coeffs(const double *eh64, const double *rhoh, int64_t n, double rho,
                                        double *ebar, cudaStream_t s);
-// Geometry update (ens_setup.cu): per-realisation coupling blocks kcs [nnz][18][Sp] of the
-// deformed surface xyz + u (u the state of the given form); bit 3 of *flags for an
-// element that degenerated.
-cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, const int32_t *ec2ent, int32_t E,
-                              int32_t Sp, double nu, double kshear, const void *u_main, const void *aux, void *kcs,
-                              int *flags, cudaStream_t s);
+// Geometry update (ens_setup.cu): per-realisation corner blocks kcs [E][3][9][Sp] (K_01,
+// K_12, K_20 of each element) of the deformed surface xyz + u (u the state of the given
+// form); bit 3 of *flags for an element that degenerated.
+cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, int32_t E, int32_t Sp, double nu,
+                              double kshear, const void *u_main, const void *aux, void *kcs, int *flags,
+                              cudaStream_t s);
 cudaError_t launch_pack_kc(const double *kc64, int64_t nnz, void *kc_out, int to_float,
                            cudaStream_t s);
 // Binary32 coupling blocks (stride 20) into fixed-stride block records of nb nodes and

@@ -168,15 +168,15 @@ __global__ void setup_elements_kernel(const double *__restrict__ xyz,
 
 // Geometry update (Section 2.3, selective re-assembly of K(u)): the coupling blocks of
 // element e for realisation s on its deformed surface X + u_s, with the same frame and
-// block arithmetic as setup_elements_kernel (so a zero displacement gives the reference
-// blocks bit for bit). u is read as binary64 from the state of any form; the blocks go
-// to kcs [nnz][18][Sp] (sample index innermost) in binary64 or rounded to binary32. An
-// element whose deformed area is zero or not finite sets bit 3 of *flags.
+// block arithmetic as setup_elements_kernel. The element matrix is symmetric, so its three
+// off-diagonal corner blocks K_01, K_12, K_20 determine the rest (K_ab = K_ba^T); they go to
+// kcs [E][3][9][Sp] (sample index innermost) in binary64 or rounded to binary32. u is read
+// as binary64 from the state of any form. An element whose deformed area is zero or not
+// finite sets bit 3 of *flags.
 template <int FORM>
 __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t *__restrict__ tri,
-                                  const int32_t *__restrict__ ec2ent, int32_t E, int32_t Sp, double nu,
-                                  double ks, const void *__restrict__ u_main, const void *__restrict__ aux,
-                                  void *__restrict__ kcs, int to_float, int *flags) {
+                                  int32_t E, int32_t Sp, double nu, double ks, const void *__restrict__ u_main,
+                                  const void *__restrict__ aux, void *__restrict__ kcs, int to_float, int *flags) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)E * Sp) return;
     const int32_t e = (int32_t)(t / Sp);
@@ -201,22 +201,16 @@ __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t 
         atomicOr(flags, 8);
         return;
     }
-    for (int c = 0; c < 3; c++) {
-        const int64_t p = ec2ent[3 * e + c];
-        const int a = (c + 1) % 3, b = (c + 2) % 3;
-        double Ga[3][3], Gb[3][3];
-        coupling_block(f, c, a, nu, ks, Ga);
-        coupling_block(f, c, b, nu, ks, Gb);
+    for (int c = 0; c < 3; c++) {  // block c couples corner c to corner (c + 1) mod 3
+        double G[3][3];
+        coupling_block(f, c, (c + 1) % 3, nu, ks, G);
         for (int r = 0; r < 3; r++)
             for (int q = 0; q < 3; q++) {
-                const int64_t ia = (p * 18 + 3 * r + q) * Sp + s, ib = (p * 18 + 9 + 3 * r + q) * Sp + s;
-                if (to_float) {
-                    ((float *)kcs)[ia] = (float)Ga[r][q];
-                    ((float *)kcs)[ib] = (float)Gb[r][q];
-                } else {
-                    ((double *)kcs)[ia] = Ga[r][q];
-                    ((double *)kcs)[ib] = Gb[r][q];
-                }
+                const int64_t i = (((int64_t)e * 3 + c) * 9 + 3 * r + q) * Sp + s;
+                if (to_float)
+                    ((float *)kcs)[i] = (float)G[r][q];
+                else
+                    ((double *)kcs)[i] = G[r][q];
             }
     }
 }
@@ -398,20 +392,18 @@ cudaError_t launch_setup_elements(const double *xyz, const int32_t *tri, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, const int32_t *ec2ent, int32_t E,
-                              int32_t Sp, double nu, double kshear, const void *u_main, const void *aux, void *kcs,
-                              int *flags, cudaStream_t s) {
+cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, int32_t E, int32_t Sp, double nu,
+                              double kshear, const void *u_main, const void *aux, void *kcs, int *flags,
+                              cudaStream_t s) {
     const int64_t n = (int64_t)E * Sp;
     if (n == 0) return cudaSuccess;
     const unsigned g = blocks_for(n, 128);
     if (form == kFP64)
-        reassemble_kernel<kFP64><<<g, 128, 0, s>>>(xyz, tri, ec2ent, E, Sp, nu, kshear, u_main, aux, kcs, 0, flags);
+        reassemble_kernel<kFP64><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, 0, flags);
     else if (form == kFP32Force)
-        reassemble_kernel<kFP32Force><<<g, 128, 0, s>>>(xyz, tri, ec2ent, E, Sp, nu, kshear, u_main, aux, kcs, 1,
-                                                        flags);
+        reassemble_kernel<kFP32Force><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, 1, flags);
     else
-        reassemble_kernel<kKahan32><<<g, 128, 0, s>>>(xyz, tri, ec2ent, E, Sp, nu, kshear, u_main, aux, kcs, 1,
-                                                      flags);
+        reassemble_kernel<kKahan32><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, 1, flags);
     return cudaGetLastError();
 }
 

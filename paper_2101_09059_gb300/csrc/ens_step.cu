@@ -521,8 +521,11 @@ __global__ void __launch_bounds__(kBlock) step_kernel(const StepArgs<R> a) {
 }
 
 // Geometry update (Section 2.3, K(u) re-assembled on the deformed surface): the internal
-// force with per-realisation coupling blocks kcs [nnz][18][Sp], the same operations in
-// the same order as node_force, the 18 coefficients read per sample (six at a time).
+// force with per-realisation corner blocks kcs [E][3][9][Sp] (block c = K_c,c+1 of the
+// element), the same operations in the same order as node_force. Node i at corner c of
+// element e couples to corner c + 1 through block c (read by rows) and to corner c + 2
+// through K_c,c+2 = (K_c+2,c)^T, block c + 2 read by columns. Each block is read by the two
+// corners it couples, neighbours in the node order, so the second read comes from L2.
 template <typename R, int V>
 __device__ __forceinline__ void node_force_geom(const ForceView<R> &w, const R *__restrict__ kcs,
                                                 const R *__restrict__ ug, int32_t i, int32_t s0,
@@ -544,16 +547,18 @@ __device__ __forceinline__ void node_force_geom(const ForceView<R> &w, const R *
             ld_nc(g.row(en.z, d), ub[d]);
         }
         ld_nc(g.ehrow(en.x), e);
-        const R *kp = kcs + (int64_t)p * 18 * Sp + s0;
+        const int cz = en.w == 0 ? 2 : en.w - 1;
+        const R *ky = kcs + ((int64_t)en.x * 3 + en.w) * 9 * Sp + s0;  // K_c,c+1, row d
+        const R *kz = kcs + ((int64_t)en.x * 3 + cz) * 9 * Sp + s0;     // K_c+2,c, column d
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             R k0[V], k1[V], k2[V], k3[V], k4[V], k5[V];
-            ld_nc(kp + (3 * d) * Sp, k0);
-            ld_nc(kp + (3 * d + 1) * Sp, k1);
-            ld_nc(kp + (3 * d + 2) * Sp, k2);
-            ld_nc(kp + (9 + 3 * d) * Sp, k3);
-            ld_nc(kp + (9 + 3 * d + 1) * Sp, k4);
-            ld_nc(kp + (9 + 3 * d + 2) * Sp, k5);
+            ld_nc(ky + (3 * d) * Sp, k0);
+            ld_nc(ky + (3 * d + 1) * Sp, k1);
+            ld_nc(ky + (3 * d + 2) * Sp, k2);
+            ld_nc(kz + d * Sp, k3);
+            ld_nc(kz + (3 + d) * Sp, k4);
+            ld_nc(kz + (6 + d) * Sp, k5);
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const R a0 = ua[0][v] - ui[0][v], a1 = ua[1][v] - ui[1][v], a2 = ua[2][v] - ui[2][v];

@@ -1,7 +1,7 @@
 // Device Matérn random-field sampler (Section 2.1): x = K^-1 C~^(1/2) z with
 // K = kappa^2 C~ + G, all S right-hand sides at once, vectors stored [N][Sp] with the
-// sample index innermost (Sp = S rounded up to even; each thread owns one node row and
-// two samples).
+// sample index innermost (Sp = S rounded up to a multiple of 4; each thread owns one node
+// row and two samples, four in the vector update).
 //
 // GB300 issues binary64 arithmetic at about 1/64 of its binary32 rate, and a binary64 CG
 // iteration is bound by that pipe (13 binary64 FMAs per row and sample), so the solve is
@@ -11,15 +11,19 @@
 //                     max(rtol, 1e-4), then x += ||r|| d.
 // Each refinement gains about four digits (K has condition ~1e3 on the workloads, so the
 // binary32 solve is accurate to ~1e-4), and the final residual is the binary64 one.
-// One inner iteration is five kernels:
-//   spmv_dot   q = K p (binary32 matrix), per-block partial sums of p.q;
-//   fin_alpha  alpha_s = rz_s / (p.q)_s (0 once sample s has converged);
-//   update     d += alpha p, r -= alpha q, partial sums of r.z and r.r with z = M^-1 r;
-//   fin_beta   beta_s, convergence test, active count;
-//   pupdate    p = M^-1 r + beta p.
-// Every reduction has a fixed shape (a grid fixed per context, fixed trees), so results are bitwise
-// reproducible; a converged sample takes alpha = beta = 0 from then on, so stopping a
-// few iterations later changes nothing. Inner iterations run as replays of a graph.
+// The inner solve takes Chronopoulos and Gear's form of preconditioned CG (one reduction
+// per iteration): with z = M^-1 r and w = K z, gamma = r.z and delta = z.w give
+// beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev), and the
+// recurrences p = z + beta p, Kp = w + beta Kp, d += alpha p, r -= alpha Kp; in exact
+// arithmetic these are the iterates of standard PCG. One inner iteration is two kernels:
+//   cg_matvec  w = (K M^-1) r with partial sums of r.z, z.w, r.r; the block that completes
+//              the reduction (a two-level, fixed-order sum through arrival counters) forms
+//              alpha, beta, the convergence test and the active count for every sample;
+//   cg_update  the four vector recurrences, four samples per thread.
+// Every reduction has a fixed shape (a grid fixed per context, fixed trees), so results are
+// bitwise reproducible; a converged sample takes alpha = beta = 0 from then on, so
+// stopping a few iterations later changes nothing. Inner iterations run as replays of a
+// graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,8 +57,8 @@ struct gmrf_ctx {
     int device = 0;
     int32_t *rowptr = nullptr, *col = nullptr;
     double *val = nullptr, *sqrtc = nullptr;
-    float *val32 = nullptr, *minv32 = nullptr;
-    // padded-row (ELL) copy of the binary32 matrix: ell_w entries per row (8 or 16; 0 when
+    float *valz = nullptr, *minv32 = nullptr;  // K M^-1 (binary32, CSR values), M^-1
+    // padded-row (ELL) copy of the binary32 K M^-1: ell_w entries per row (8 or 16; 0 when
     // some row is longer), padding entries (own column, value 0)
     int32_t ell_w = 0;
     // blocks of the row kernels: the device's SM count times the fewest blocks of 256
@@ -62,12 +66,15 @@ struct gmrf_ctx {
     // context (and so is every reduction shape)
     int32_t grid = 0;
     int32_t *ell_col = nullptr;
-    float *ell_val = nullptr;
+    float *ell_valz = nullptr;
     // work vectors, sized for cap_sp samples
     int32_t cap_sp = 0;
     double *b = nullptr, *x = nullptr, *r = nullptr;       // binary64 [N][Sp]
-    float *d = nullptr, *ri = nullptr, *p = nullptr, *q = nullptr;  // binary32 [N][Sp]
-    double *part = nullptr;  // [2][Sp][G]: per-sample partial sums, contiguous over blocks
+    // binary32 [N][Sp]: inner solution, residual, direction, K times direction, K M^-1 r
+    float *d = nullptr, *ri = nullptr, *p = nullptr, *ap = nullptr, *w = nullptr;
+    double *part = nullptr;   // [3][Sp][G]: per-sample partial sums, contiguous over blocks
+    double *gpart = nullptr;  // [3][Sp][groups]: sums of kGroup consecutive blocks
+    unsigned *ctr = nullptr;  // arrival counters of the groups and the top level
     double *scal = nullptr;  // [kScal][Sp], rows below
     float *scal32 = nullptr; // [2][Sp]: alpha, beta in binary32
     int *n_active = nullptr;
@@ -82,7 +89,10 @@ struct gmrf_ctx {
 namespace {
 
 // rows of scal
-enum { kRz = 0, kBbIn, kActIn, kBb, kRr, kScale, kActOut, kScal };
+// (kGam: r.z of the last iteration, kAlp: its alpha, kTot..kTot+2: the iteration's
+// totals of r.z, z.w, r.r)
+enum { kGam = 0, kBbIn, kActIn, kBb, kRr, kScale, kActOut, kAlp, kTot, kScal = kTot + 3 };
+#define SCS(row) scal[(size_t)(row) * Sp + s]
 
 int fail(gmrf_ctx *g, int code, const char *fmt, ...) {
     char *dst = g ? g->err : g_create_err;
@@ -218,153 +228,285 @@ __global__ void residual_kernel(const int32_t *__restrict__ rowptr, const int32_
     block_partial(rr, sm, part, 0, gridDim.x, Sp, lane_q);
 }
 
-// Inner start: r_i = r / ||r|| (binary32, 0 for converged samples), d = 0, p = M^-1 r_i;
-// partials of r_i.z and r_i.r_i.
-__global__ void inner_init_kernel(const double *__restrict__ r, const double *__restrict__ inv_scale,
-                                  const float *__restrict__ minv, float *d, float *ri, float *p, int32_t N,
-                                  int32_t Sp, int64_t tiles, double *part) {
-    extern __shared__ double2 sm[];
-    float2 rz = make_float2(0.f, 0.f), rr = rz;
+// Inner start: r_i = r / ||r|| (binary32, 0 for converged samples), d = p = K p = 0; the
+// samples active in the outer loop start the inner one (state 1: first iteration).
+__global__ void inner_init_kernel(const double *__restrict__ r, const double *__restrict__ inv_scale, float *d,
+                                  float *ri, float *p, float *ap, double *scal, int32_t N, int32_t Sp,
+                                  int64_t tiles) {
+    if (blockIdx.x == 0 && threadIdx.y == 0) {
+        const int lq = blockIdx.y * blockDim.x + threadIdx.x;
+        for (int k = 0; k < 2 && lq < Sp / 2; k++) {
+            const int32_t s = 2 * lq + k;
+            scal[(size_t)kActIn * Sp + s] = scal[(size_t)kActOut * Sp + s] != 0.0 ? 1.0 : 0.0;
+        }
+    }
     ROW_LOOP
         const double2 is = ld2(inv_scale + s0);
         const double2 rv = ld2(r + o);
         const float2 rf = make_float2(ens::f64_to_f32_rz(rv.x * is.x), ens::f64_to_f32_rz(rv.y * is.y));
-        const float m = minv[i];
-        const float2 zz = make_float2(m * rf.x, m * rf.y);
+        const float2 zero = make_float2(0.f, 0.f);
         stf2(ri + o, rf);
-        stf2(d + o, make_float2(0.f, 0.f));
-        stf2(p + o, zz);
-        rz.x = fmaf(rf.x, zz.x, rz.x);
-        rz.y = fmaf(rf.y, zz.y, rz.y);
-        rr.x = fmaf(rf.x, rf.x, rr.x);
-        rr.y = fmaf(rf.y, rf.y, rr.y);
+        stf2(d + o, zero);
+        stf2(p + o, zero);
+        stf2(ap + o, zero);
     }
-    block_partial(widen(rz), sm, part, 0, gridDim.x, Sp, lane_q);
-    block_partial(widen(rr), sm, part, 1, gridDim.x, Sp, lane_q);
 }
 
-// q = K p (binary32) and partials of p.q.
-__global__ void spmv_dot_kernel(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                const float *__restrict__ val, const float *__restrict__ p,
-                                float *__restrict__ q, int32_t N, int32_t Sp, int64_t tiles, double *part) {
-    extern __shared__ double2 sm[];
-    float2 pq = make_float2(0.f, 0.f);
-    ROW_LOOP
-        float2 acc = make_float2(0.f, 0.f);
-        const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
-        // the first kUnroll entries: all column indices first, then all vector loads, so a
-        // row costs two dependent round trips instead of one per entry
-        constexpr int kUnroll = 7;
-        int32_t cj[kUnroll];
-        float aj[kUnroll];
+// Sum NQ per-thread partial pairs over the block's rows (fixed pairwise tree, binary64) and
+// write them to part[w][s][blockIdx.x], w = 0..NQ-1; sm holds NQ x (block size) double2.
+template <int NQ>
+__device__ __forceinline__ void block_partials(const double2 (&v)[NQ], double2 *sm, double *part, int G,
+                                               int32_t Sp, int lane_q) {
+    const int R = blockDim.y, Qt = blockDim.x, nt = R * Qt;
+    const int y = threadIdx.y, xq = threadIdx.x;
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const bool ok = k0 + u < k1;
-            cj[u] = ok ? __ldg(col + k0 + u) : (int32_t)i;
-            aj[u] = ok ? __ldg(val + k0 + u) : 0.f;
-        }
+    for (int w = 0; w < NQ; w++) sm[w * nt + y * Qt + xq] = v[w];
+    __syncthreads();
+    int p2 = 1;
+    while (p2 < R) p2 <<= 1;
+    for (int st = p2 >> 1; st > 0; st >>= 1) {
+        if (y < st && y + st < R) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; u++) {
-            const float2 v = __ldg(reinterpret_cast<const float2 *>(p + (size_t)cj[u] * Sp + s0));
-            acc.x = fmaf(aj[u], v.x, acc.x);
-            acc.y = fmaf(aj[u], v.y, acc.y);
+            for (int w = 0; w < NQ; w++) {
+                const double2 a = sm[w * nt + y * Qt + xq], b = sm[w * nt + (y + st) * Qt + xq];
+                sm[w * nt + y * Qt + xq] = make_double2(a.x + b.x, a.y + b.y);
+            }
         }
-        for (int32_t k = k0 + kUnroll; k < k1; k++) {
-            const float a = __ldg(val + k);
-            const float2 v = __ldg(reinterpret_cast<const float2 *>(p + (size_t)__ldg(col + k) * Sp + s0));
-            acc.x = fmaf(a, v.x, acc.x);
-            acc.y = fmaf(a, v.y, acc.y);
-        }
-        stf2(q + o, acc);
-        const float2 pv = ldf2(p + o);
-        pq.x = fmaf(pv.x, acc.x, pq.x);
-        pq.y = fmaf(pv.y, acc.y, pq.y);
+        __syncthreads();
     }
-    block_partial(widen(pq), sm, part, 0, gridDim.x, Sp, lane_q);
+    if (y == 0 && lane_q < Sp / 2) {
+#pragma unroll
+        for (int w = 0; w < NQ; w++) {
+            const double2 t = sm[w * nt + xq];
+            double *dst = part + ((size_t)w * Sp + 2 * lane_q) * G + blockIdx.x;
+            dst[0] = t.x;
+            dst[G] = t.y;
+        }
+    }
 }
 
-// The same product from the padded rows: the column indices and values of a row are
-// WP / 4 vector loads that do not wait for the row pointers, so a row costs two dependent
-// round trips (indices, then the WP gathers).
+// Sum of cnt consecutive binary64 values src[0..cnt) by one warp, cnt <= 128: lane l adds
+// l, l + 32, l + 64, l + 96 in that order, then a butterfly; the same tree for every call.
+__device__ __forceinline__ double warp_sum_run(const double *src, int cnt, int lane) {
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (lane + 32 * k < cnt) a += __ldcg(src + lane + 32 * k);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+    return a;
+}
+
+// Two-level completion of the iteration's reduction. Every block has written its partials
+// part[w][s][b] (w < kNQ). A block adds itself to its group's counter (groups of kGroup
+// consecutive blockIdx.x, all chunks); the group's last block sums the group's partials
+// in block order into gpart[w][s][group] and adds itself to the top counter; the last of
+// those returns true, with every group sum visible to it. The last arrivals reset the
+// counters, so the next launch starts from zero. No block waits for another.
+constexpr int kGroup = 32;
+constexpr int kNQ = 3;  // r.z, z.w, r.r
+__device__ __forceinline__ bool reduce_arrive(const double *part, double *gpart, unsigned *ctr, int G,
+                                              int32_t Sp) {
+    __shared__ int s_last;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nwarps = (blockDim.x * blockDim.y) / 32, warp = tid / 32, lane = tid % 32;
+    const int ngroups = (G + kGroup - 1) / kGroup;
+    const int grp = blockIdx.x / kGroup;
+    const int g0 = grp * kGroup, cnt = min(kGroup, G - g0);
+    __threadfence();  // this thread's partials before the arrival
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned expect = (unsigned)cnt * gridDim.y;
+        const unsigned prev = atomicAdd(ctr + grp, 1u);
+        s_last = prev == expect - 1;
+        if (s_last) ctr[grp] = 0;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    const int npairs = kNQ * Sp;
+    for (int pr = warp; warp < nwarps && pr < npairs; pr += nwarps) {  // whole warps only
+        const double t = warp_sum_run(part + (size_t)pr * G + g0, cnt, lane);
+        if (lane == 0) gpart[(size_t)pr * ngroups + grp] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned prev = atomicAdd(ctr + ngroups, 1u);
+        s_last = prev == (unsigned)ngroups - 1;
+        if (s_last) ctr[ngroups] = 0;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    return true;
+}
+
+// The scalar part of an inner iteration, run by the block that completed the reduction:
+// totals per sample from the group sums, then for every sample s (state act_s: 0 inactive,
+// 1 first iteration, 2 later ones):
+//   convergence: r.r <= tol^2 ||r_0||^2 ends the inner solve of s (alpha = beta = 0 from
+//   then on, so its d, r stay as they are);
+//   beta = gamma / gamma_prev (0 on the first iteration), alpha = gamma / (delta - beta
+//   gamma / alpha_prev) (gamma / delta on the first), rounded toward zero to binary32; a
+//   non-positive denominator (the binary32 recurrence lost K's definiteness) also ends it;
+//   and the number of samples still active goes to *n_active.
+// Kept out of line: it runs once per launch, and its binary64 arithmetic would otherwise
+// set the register budget of the product loop.
+__device__ __noinline__ void finish_iteration(const double *gpart, double *scal, float *alpha32, float *beta32,
+                                              int *n_active, int32_t Sp, double tol2) {
+    __shared__ int s_count;
+    // the last block: totals per sample from the group sums, then the scalar recurrences
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const int nwarps = nt / 32, warp = tid / 32, lane = tid % 32;
+    const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+    for (int pr = warp; warp < nwarps && pr < kNQ * Sp; pr += nwarps) {
+        const double t = warp_sum_run(gpart + (size_t)pr * ngroups, ngroups, lane);
+        if (lane == 0) scal[(size_t)(kTot + pr / Sp) * Sp + pr % Sp] = t;
+    }
+    __syncthreads();
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    int count = 0;
+    for (int32_t s = tid; s < Sp; s += nt) {
+        const double gam = SCS(kTot), del = SCS(kTot + 1), rrs = SCS(kTot + 2);
+        const double act = SCS(kActIn);
+        double alpha = 0.0, beta = 0.0;
+        if (act != 0.0) {
+            if (act == 1.0) SCS(kBbIn) = rrs;
+            bool done = rrs <= tol2 * SCS(kBbIn);
+            if (!done) {
+                double den = del;
+                if (act == 2.0) {
+                    beta = ens::f32_to_f64(ens::f64_to_f32_rz(gam / SCS(kGam)));
+                    den = del - beta * gam / SCS(kAlp);
+                }
+                if (gam > 0.0 && den > 0.0) {
+                    alpha = ens::f32_to_f64(ens::f64_to_f32_rz(gam / den));
+                    SCS(kGam) = gam;
+                    SCS(kAlp) = alpha;
+                    SCS(kActIn) = 2.0;
+                    count++;
+                } else {
+                    done = true;
+                }
+            }
+            if (done) {
+                SCS(kActIn) = 0.0;
+                alpha = beta = 0.0;
+            }
+        }
+        alpha32[s] = (float)alpha;  // exact: already binary32 values
+        beta32[s] = (float)beta;
+    }
+    if (count) atomicAdd(&s_count, count);
+    __syncthreads();
+    if (tid == 0) *n_active = s_count;
+}
+
+// Inner iteration, part 1: w = (K M^-1) r_i, the product with the column-scaled binary32
+// matrix (z = M^-1 r_i never stored), and partials of r.z, z.w and r.r over the block's
+// rows (binary32 per thread, binary64 across threads). WP = 8 or 16: padded rows (ELL,
+// the indices and values of a row in WP / 4 vector loads); WP = 0: CSR rows. The block
+// that completes the reduction then finishes the iteration (finish_iteration).
 template <int WP>
-__global__ void spmv_ell_kernel(const int32_t *__restrict__ ell_col, const float *__restrict__ ell_val,
-                                const float *__restrict__ p, float *__restrict__ q, int32_t N, int32_t Sp,
-                                int64_t tiles, double *part) {
+__global__ void __launch_bounds__(kThreads, 4) cg_matvec_kernel(const int32_t *__restrict__ ell_col, const float *__restrict__ ell_valz,
+                                 const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                                 const float *__restrict__ valz, const float *__restrict__ minv,
+                                 const float *__restrict__ ri, float *__restrict__ w, int32_t N, int32_t Sp,
+                                 int64_t tiles, double *part, double *gpart, unsigned *ctr, double *scal,
+                                 float *alpha32, float *beta32, int *n_active, double tol2) {
     extern __shared__ double2 sm[];
-    float2 pq = make_float2(0.f, 0.f);
+    float2 rz = make_float2(0.f, 0.f), zw = rz, rr = rz;
     ROW_LOOP
-        int32_t cj[WP];
-        float aj[WP];
-        const int4 *cc = reinterpret_cast<const int4 *>(ell_col + (size_t)i * WP);
-        const float4 *vv = reinterpret_cast<const float4 *>(ell_val + (size_t)i * WP);
-#pragma unroll
-        for (int u = 0; u < WP / 4; u++) {
-            const int4 c = __ldg(cc + u);
-            const float4 v = __ldg(vv + u);
-            cj[4 * u] = c.x;
-            cj[4 * u + 1] = c.y;
-            cj[4 * u + 2] = c.z;
-            cj[4 * u + 3] = c.w;
-            aj[4 * u] = v.x;
-            aj[4 * u + 1] = v.y;
-            aj[4 * u + 2] = v.z;
-            aj[4 * u + 3] = v.w;
-        }
         float2 acc = make_float2(0.f, 0.f);
+        if constexpr (WP > 0) {
+            int32_t cj[WP];
+            float aj[WP];
+            const int4 *cc = reinterpret_cast<const int4 *>(ell_col + (size_t)i * WP);
+            const float4 *vv = reinterpret_cast<const float4 *>(ell_valz + (size_t)i * WP);
 #pragma unroll
-        for (int u = 0; u < WP; u++) {
-            const float2 v = __ldg(reinterpret_cast<const float2 *>(p + (size_t)cj[u] * Sp + s0));
-            acc.x = fmaf(aj[u], v.x, acc.x);
-            acc.y = fmaf(aj[u], v.y, acc.y);
+            for (int u = 0; u < WP / 4; u++) {
+                const int4 c = __ldg(cc + u);
+                const float4 v = __ldg(vv + u);
+                cj[4 * u] = c.x;
+                cj[4 * u + 1] = c.y;
+                cj[4 * u + 2] = c.z;
+                cj[4 * u + 3] = c.w;
+                aj[4 * u] = v.x;
+                aj[4 * u + 1] = v.y;
+                aj[4 * u + 2] = v.z;
+                aj[4 * u + 3] = v.w;
+            }
+#pragma unroll
+            for (int u = 0; u < WP; u++) {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(ri + (size_t)cj[u] * Sp + s0));
+                acc.x = fmaf(aj[u], v.x, acc.x);
+                acc.y = fmaf(aj[u], v.y, acc.y);
+            }
+        } else {
+            const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
+            for (int32_t k = k0; k < k1; k++) {
+                const float a = __ldg(valz + k);
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(ri + (size_t)__ldg(col + k) * Sp + s0));
+                acc.x = fmaf(a, v.x, acc.x);
+                acc.y = fmaf(a, v.y, acc.y);
+            }
         }
-        stf2(q + o, acc);
-        const float2 pv = ldf2(p + o);
-        pq.x = fmaf(pv.x, acc.x, pq.x);
-        pq.y = fmaf(pv.y, acc.y, pq.y);
-    }
-    block_partial(widen(pq), sm, part, 0, gridDim.x, Sp, lane_q);
-}
-
-// d += alpha p, r -= alpha q; partials of r.z (z = M^-1 r) and r.r.
-__global__ void update_kernel(const float *__restrict__ minv, const float *__restrict__ alpha, float *d,
-                              float *ri, const float *__restrict__ p, const float *__restrict__ q, int32_t N,
-                              int32_t Sp, int64_t tiles, double *part) {
-    extern __shared__ double2 sm[];
-    float2 rz = make_float2(0.f, 0.f), rr = rz;
-    const int lq = blockIdx.y * blockDim.x + threadIdx.x;
-    const float2 al = lq < Sp / 2 ? ldf2(alpha + 2 * lq) : make_float2(0.f, 0.f);
-    ROW_LOOP
-        const float2 pv = ldf2(p + o), qv = ldf2(q + o);
-        float2 dv = ldf2(d + o), rv = ldf2(ri + o);
-        dv.x = fmaf(al.x, pv.x, dv.x);
-        dv.y = fmaf(al.y, pv.y, dv.y);
-        rv.x = fmaf(-al.x, qv.x, rv.x);
-        rv.y = fmaf(-al.y, qv.y, rv.y);
-        stf2(d + o, dv);
-        stf2(ri + o, rv);
-        const float m = minv[i];
-        rz.x = fmaf(rv.x, m * rv.x, rz.x);
-        rz.y = fmaf(rv.y, m * rv.y, rz.y);
+        stf2(w + o, acc);
+        const float2 rv = ldf2(ri + o);
+        const float m = __ldg(minv + i);
+        const float2 zv = make_float2(m * rv.x, m * rv.y);
+        rz.x = fmaf(rv.x, zv.x, rz.x);
+        rz.y = fmaf(rv.y, zv.y, rz.y);
+        zw.x = fmaf(zv.x, acc.x, zw.x);
+        zw.y = fmaf(zv.y, acc.y, zw.y);
         rr.x = fmaf(rv.x, rv.x, rr.x);
         rr.y = fmaf(rv.y, rv.y, rr.y);
     }
-    block_partial(widen(rz), sm, part, 0, gridDim.x, Sp, lane_q);
-    block_partial(widen(rr), sm, part, 1, gridDim.x, Sp, lane_q);
+    const double2 v[kNQ] = {widen(rz), widen(zw), widen(rr)};
+    block_partials<kNQ>(v, sm, part, gridDim.x, Sp, lane_q);
+    if (reduce_arrive(part, gpart, ctr, gridDim.x, Sp)) finish_iteration(gpart, scal, alpha32, beta32, n_active, Sp, tol2);
 }
 
-// p = M^-1 r + beta p.
-__global__ void pupdate_kernel(const float *__restrict__ beta, const float *__restrict__ minv,
-                               const float *__restrict__ ri, float *p, int32_t N, int32_t Sp) {
+// Inner iteration, part 2, four samples per thread: z = M^-1 r, p = z + beta p,
+// Kp = w + beta Kp, d += alpha p, r -= alpha Kp.
+__global__ void cg_update_kernel(const float *__restrict__ minv, const float *__restrict__ alpha,
+                                 const float *__restrict__ beta, const float *__restrict__ w, float *d, float *ri,
+                                 float *p, float *ap, int32_t N, int32_t Sp) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)N * Sp / 2) return;
-    const int32_t s0 = (int32_t)(2 * (t % (Sp / 2)));
-    const float m = minv[t / (Sp / 2)];
-    const float2 b = ldf2(beta + s0);
-    const float2 rv = ldf2(ri + 2 * t);
-    float2 pv = ldf2(p + 2 * t);
-    pv.x = fmaf(b.x, pv.x, m * rv.x);
-    pv.y = fmaf(b.y, pv.y, m * rv.y);
-    stf2(p + 2 * t, pv);
+    const int32_t Q4 = Sp / 4;
+    if (t >= (int64_t)N * Q4) return;
+    const int32_t s0 = (int32_t)(4 * (t % Q4));
+    const float m = __ldg(minv + t / Q4);
+    const float4 al = __ldg(reinterpret_cast<const float4 *>(alpha + s0));
+    const float4 be = __ldg(reinterpret_cast<const float4 *>(beta + s0));
+    float4 *const d4 = reinterpret_cast<float4 *>(d) + t;
+    float4 *const r4 = reinterpret_cast<float4 *>(ri) + t;
+    float4 *const p4 = reinterpret_cast<float4 *>(p) + t;
+    float4 *const a4 = reinterpret_cast<float4 *>(ap) + t;
+    const float4 wv = __ldcs(reinterpret_cast<const float4 *>(w) + t);
+    float4 rv = *r4, pv = *p4, av = *a4, dv = *d4;
+    pv.x = fmaf(be.x, pv.x, m * rv.x);
+    pv.y = fmaf(be.y, pv.y, m * rv.y);
+    pv.z = fmaf(be.z, pv.z, m * rv.z);
+    pv.w = fmaf(be.w, pv.w, m * rv.w);
+    av.x = fmaf(be.x, av.x, wv.x);
+    av.y = fmaf(be.y, av.y, wv.y);
+    av.z = fmaf(be.z, av.z, wv.z);
+    av.w = fmaf(be.w, av.w, wv.w);
+    dv.x = fmaf(al.x, pv.x, dv.x);
+    dv.y = fmaf(al.y, pv.y, dv.y);
+    dv.z = fmaf(al.z, pv.z, dv.z);
+    dv.w = fmaf(al.w, pv.w, dv.w);
+    rv.x = fmaf(-al.x, av.x, rv.x);
+    rv.y = fmaf(-al.y, av.y, rv.y);
+    rv.z = fmaf(-al.z, av.z, rv.z);
+    rv.w = fmaf(-al.w, av.w, rv.w);
+    *p4 = pv;
+    *a4 = av;
+    *d4 = dv;
+    *r4 = rv;
 }
 
 // Sum of part[w][s][0..G) by the block of sample s (blockIdx.x = s): fixed strided
@@ -409,50 +551,6 @@ __global__ void fin_outer_kernel(const double *part, int G, int32_t Sp, double r
     }
 }
 
-__global__ void fin_inner_init_kernel(const double *part, int G, int32_t Sp, double *scal, int *n_active) {
-    FIN_SAMPLE
-    const double rz = block_total(part, 0, G, Sp, s);
-    const double bb = block_total(part, 1, G, Sp, s);
-    if (lead) {
-        const bool act = bb > 0.0;
-        SC(kRz) = rz;
-        SC(kBbIn) = bb;
-        SC(kActIn) = act ? 1.0 : 0.0;
-        if (act) atomicAdd(n_active, 1);
-    }
-}
-
-__global__ void fin_alpha_kernel(const double *part, int G, int32_t Sp, double *scal, float *alpha32,
-                                 int *n_active) {
-    FIN_SAMPLE
-    if (s == 0 && lead) *n_active = 0;
-    const double pq = block_total(part, 0, G, Sp, s);
-    if (lead) {
-        const bool act = SC(kActIn) != 0.0;
-        alpha32[s] = (act && pq > 0.0) ? ens::f64_to_f32_rz(SC(kRz) / pq) : 0.f;
-    }
-}
-
-__global__ void fin_beta_kernel(const double *part, int G, int32_t Sp, double tol2, double *scal, float *beta32,
-                                int *n_active) {
-    FIN_SAMPLE
-    const double rz = block_total(part, 0, G, Sp, s);
-    const double rr = block_total(part, 1, G, Sp, s);
-    if (lead) {
-        float beta = 0.f;
-        if (SC(kActIn) != 0.0) {
-            const bool done = rr <= tol2 * SC(kBbIn);
-            if (!done && SC(kRz) > 0.0) beta = ens::f64_to_f32_rz(rz / SC(kRz));
-            SC(kRz) = rz;
-            if (done)
-                SC(kActIn) = 0.0;
-            else
-                atomicAdd(n_active, 1);
-        }
-        beta32[s] = beta;
-    }
-}
-
 __global__ void transform_kernel(const double *__restrict__ x, int32_t N, int32_t S, int32_t Sp,
                                  double scale, double mean, int lognormal, double *out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -465,27 +563,33 @@ __global__ void transform_kernel(const double *__restrict__ x, int32_t N, int32_
 
 int alloc_work(gmrf_ctx *g, int32_t Sp) {
     if (Sp <= g->cap_sp) return GMRF_OK;
-    void *old[] = {g->b, g->x, g->r, g->d, g->ri, g->p, g->q, g->part, g->scal, g->scal32};
+    void *old[] = {g->b, g->x, g->r, g->d, g->ri, g->p, g->ap, g->w, g->part, g->gpart, g->ctr, g->scal, g->scal32};
     for (void *p : old)
         if (p) cudaFree(p);
     g->b = g->x = g->r = nullptr;
-    g->d = g->ri = g->p = g->q = nullptr;
-    g->part = g->scal = nullptr;
+    g->d = g->ri = g->p = g->ap = g->w = nullptr;
+    g->part = g->gpart = g->scal = nullptr;
+    g->ctr = nullptr;
     g->scal32 = nullptr;
     g->cap_sp = 0;
     const size_t n = (size_t)g->N * Sp;
     double **v64[3] = {&g->b, &g->x, &g->r};
-    float **v32[4] = {&g->d, &g->ri, &g->p, &g->q};
+    float **v32[5] = {&g->d, &g->ri, &g->p, &g->ap, &g->w};
     for (double **pp : v64)
         if (cudaMalloc((void **)pp, 8 * n) != cudaSuccess)
             return fail(g, GMRF_ERR_ALLOC, "%zu bytes for a work vector", 8 * n);
     for (float **pp : v32)
         if (cudaMalloc((void **)pp, 4 * n) != cudaSuccess)
             return fail(g, GMRF_ERR_ALLOC, "%zu bytes for a work vector", 4 * n);
-    if (cudaMalloc((void **)&g->part, 8 * (size_t)2 * kMaxBlocks * Sp) != cudaSuccess ||
+    constexpr int kMaxGroups = (kMaxBlocks + kGroup - 1) / kGroup;
+    if (cudaMalloc((void **)&g->part, 8 * (size_t)kNQ * kMaxBlocks * Sp) != cudaSuccess ||
+        cudaMalloc((void **)&g->gpart, 8 * (size_t)kNQ * kMaxGroups * Sp) != cudaSuccess ||
+        cudaMalloc((void **)&g->ctr, sizeof(unsigned) * (kMaxGroups + 1)) != cudaSuccess ||
         cudaMalloc((void **)&g->scal, 8 * (size_t)(kScal + 1) * Sp) != cudaSuccess ||
         cudaMalloc((void **)&g->scal32, 4 * (size_t)2 * Sp) != cudaSuccess)
         return fail(g, GMRF_ERR_ALLOC, "reduction buffers");
+    CKG(cudaMemsetAsync(g->ctr, 0, sizeof(unsigned) * (kMaxGroups + 1), g->stream));
+    CKG(cudaMemsetAsync(g->scal, 0, 8 * (size_t)(kScal + 1) * Sp, g->stream));
     g->cap_sp = Sp;
     if (g->graph) cudaGraphExecDestroy(g->graph);
     g->graph = nullptr;
@@ -493,27 +597,27 @@ int alloc_work(gmrf_ctx *g, int32_t Sp) {
     return GMRF_OK;
 }
 
-// One inner (binary32) CG iteration: five launches on g's stream.
+// One inner (binary32) CG iteration: two launches on g's stream.
 cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double tol2) {
     const Geo o = geometry(g->N, Sp, g->grid);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
-    const size_t sm = sizeof(double2) * o.Qt * o.R;
+    const size_t sm = sizeof(double2) * kNQ * o.Qt * o.R;
     float *alpha = g->scal32, *beta = g->scal32 + Sp;
+#define CG_MATVEC(WP)                                                                                         \
+    cg_matvec_kernel<WP><<<grid, block, sm, g->stream>>>(g->ell_col, g->ell_valz, g->rowptr, g->col, g->valz,  \
+                                                         g->minv32, g->ri, g->w, g->N, Sp, o.tiles, g->part,   \
+                                                         g->gpart, g->ctr, g->scal, alpha, beta, g->n_active,  \
+                                                         tol2)
     if (g->ell_w == 8)
-        spmv_ell_kernel<8><<<grid, block, sm, g->stream>>>(g->ell_col, g->ell_val, g->p, g->q, g->N, Sp, o.tiles,
-                                                           g->part);
+        CG_MATVEC(8);
     else if (g->ell_w == 16)
-        spmv_ell_kernel<16><<<grid, block, sm, g->stream>>>(g->ell_col, g->ell_val, g->p, g->q, g->N, Sp, o.tiles,
-                                                            g->part);
+        CG_MATVEC(16);
     else
-        spmv_dot_kernel<<<grid, block, sm, g->stream>>>(g->rowptr, g->col, g->val32, g->p, g->q, g->N, Sp, o.tiles,
-                                                        g->part);
-    fin_alpha_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, g->scal, alpha, g->n_active);
-    update_kernel<<<grid, block, sm, g->stream>>>(g->minv32, alpha, g->d, g->ri, g->p, g->q, g->N, Sp, o.tiles,
-                                                  g->part);
-    fin_beta_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, tol2, g->scal, beta, g->n_active);
-    const int64_t n2 = (int64_t)g->N * Sp / 2;
-    pupdate_kernel<<<(unsigned)((n2 + 255) / 256), 256, 0, g->stream>>>(beta, g->minv32, g->ri, g->p, g->N, Sp);
+        CG_MATVEC(0);
+#undef CG_MATVEC
+    const int64_t n4 = (int64_t)g->N * Sp / 4;
+    cg_update_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, g->stream>>>(g->minv32, alpha, beta, g->w, g->d, g->ri,
+                                                                         g->p, g->ap, g->N, Sp);
     return cudaGetLastError();
 }
 
@@ -621,24 +725,27 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
         }
         rowptr[i + 1] = (int32_t)col.size();
     }
-    std::vector<float> minv32(N), val32(val.size());
+    // the inner iteration multiplies by K M^-1 (M = diag K, the Jacobi preconditioner):
+    // entries K_ij / K_jj, formed in binary64 and rounded once
+    std::vector<float> minv32(N), valz(val.size());
     std::vector<double> sqrtc(N);
     for (int32_t i = 0; i < N; i++) {
         minv32[i] = (float)(1.0 / diag[i]);
         sqrtc[i] = std::sqrt(cl[i]);
     }
-    for (size_t k = 0; k < val.size(); k++) val32[k] = (float)val[k];
+    for (int32_t i = 0; i < N; i++)
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; k++) valz[k] = (float)(val[k] / diag[col[k]]);
     int32_t wmax = 0;
     for (int32_t i = 0; i < N; i++) wmax = std::max(wmax, rowptr[i + 1] - rowptr[i]);
     const int32_t ell_w = wmax <= 8 ? 8 : (wmax <= 16 ? 16 : 0);
     std::vector<int32_t> ell_col((size_t)N * std::max(ell_w, 1));
-    std::vector<float> ell_val((size_t)N * std::max(ell_w, 1));
+    std::vector<float> ell_valz((size_t)N * std::max(ell_w, 1));
     for (int32_t i = 0; ell_w > 0 && i < N; i++)
         for (int32_t u = 0; u < ell_w; u++) {
             const int32_t k = rowptr[i] + u;
             const bool ok = k < rowptr[i + 1];
             ell_col[(size_t)i * ell_w + u] = ok ? col[k] : i;
-            ell_val[(size_t)i * ell_w + u] = ok ? val32[k] : 0.f;
+            ell_valz[(size_t)i * ell_w + u] = ok ? valz[k] : 0.f;
         }
 
     g = new (std::nothrow) gmrf_ctx();
@@ -657,10 +764,10 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
     if (cudaMalloc((void **)&g->rowptr, 4 * (size_t)(N + 1)) != cudaSuccess ||
         cudaMalloc((void **)&g->col, 4 * (size_t)g->nnz) != cudaSuccess ||
         cudaMalloc((void **)&g->val, 8 * (size_t)g->nnz) != cudaSuccess ||
-        cudaMalloc((void **)&g->val32, 4 * (size_t)g->nnz) != cudaSuccess ||
+        cudaMalloc((void **)&g->valz, 4 * (size_t)g->nnz) != cudaSuccess ||
         cudaMalloc((void **)&g->minv32, 4 * (size_t)N) != cudaSuccess ||
         cudaMalloc((void **)&g->ell_col, 4 * ell_col.size()) != cudaSuccess ||
-        cudaMalloc((void **)&g->ell_val, 4 * ell_val.size()) != cudaSuccess ||
+        cudaMalloc((void **)&g->ell_valz, 4 * ell_valz.size()) != cudaSuccess ||
         cudaMalloc((void **)&g->sqrtc, 8 * (size_t)N) != cudaSuccess ||
         cudaMalloc((void **)&g->n_active, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void **)&g->h_active, sizeof(int)) != cudaSuccess)
@@ -668,10 +775,10 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
     cudaError_t e = cudaMemcpyAsync(g->rowptr, rowptr.data(), 4 * (size_t)(N + 1), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->col, col.data(), 4 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->val, val.data(), 8 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->val32, val32.data(), 4 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->valz, valz.data(), 4 * (size_t)g->nnz, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->minv32, minv32.data(), 4 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->ell_col, ell_col.data(), 4 * ell_col.size(), cudaMemcpyHostToDevice, g->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->ell_val, ell_val.data(), 4 * ell_val.size(), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->ell_valz, ell_valz.data(), 4 * ell_valz.size(), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->sqrtc, sqrtc.data(), 8 * (size_t)N, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return bail(fail(g, GMRF_ERR_CUDA, "copying the operator: %s", cudaGetErrorString(e)));
@@ -679,11 +786,14 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
         int sms = 0, per = 0, least = 1 << 20;
         const size_t smb = sizeof(double2) * kThreads;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const void *fns[] = {(const void *)spmv_ell_kernel<8>, (const void *)spmv_ell_kernel<16>,
-                             (const void *)spmv_dot_kernel, (const void *)update_kernel, (const void *)inner_init_kernel,
-                             (const void *)residual_kernel, (const void *)rhs_kernel};
-        for (const void *f : fns)
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, f, kThreads, smb) == cudaSuccess && per > 0)
+        const struct {
+            const void *f;
+            size_t smem;
+        } fns[] = {{(const void *)cg_matvec_kernel<8>, kNQ * smb}, {(const void *)cg_matvec_kernel<16>, kNQ * smb},
+                   {(const void *)cg_matvec_kernel<0>, kNQ * smb}, {(const void *)inner_init_kernel, 0},
+                   {(const void *)residual_kernel, smb}, {(const void *)rhs_kernel, smb}};
+        for (const auto &k : fns)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.f, kThreads, k.smem) == cudaSuccess && per > 0)
                 least = std::min(least, per);
         if (sms <= 0 || least == (1 << 20)) return bail(fail(g, GMRF_ERR_CUDA, "occupancy query failed"));
         g->grid = std::min(kMaxBlocks, sms * least);
@@ -705,7 +815,7 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
     // Matern variance Gamma(nu) / (Gamma(nu + d/2) (4 pi)^(d/2) kappa^(2 nu))), so the
     // factor sigma sqrt(4 pi) kappa gives marginal standard deviation sigma
     const double scale = sigma > 0.0 ? sigma * std::sqrt(4.0 * 3.14159265358979323846) * g->info.kappa : 1.0;
-    const int32_t Sp = (S + 1) / 2 * 2;
+    const int32_t Sp = (S + 3) / 4 * 4;
     int rc = alloc_work(g, Sp);
     if (rc != GMRF_OK) return rc;
     const Geo o = geometry(g->N, Sp, g->grid);
@@ -726,13 +836,11 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
     }
     int iters = 0, refinements = 0;
     while (*g->h_active > 0 && iters < max_iter && refinements < kMaxRefinements) {
-        // inner binary32 solve of K d = r / ||r||
-        CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
-        inner_init_kernel<<<grid, block, sm, g->stream>>>(g->r, inv_scale, g->minv32, g->d, g->ri, g->p, g->N, Sp,
-                                                          o.tiles, g->part);
-        fin_inner_init_kernel<<<Sp, kFinThreads, 0, g->stream>>>(g->part, o.G, Sp, g->scal, g->n_active);
+        // inner binary32 solve of K d = r / ||r||, started by the samples the outer test
+        // left active (their count is in h_active)
+        inner_init_kernel<<<grid, block, 0, g->stream>>>(g->r, inv_scale, g->d, g->ri, g->p, g->ap, g->scal, g->N,
+                                                         Sp, o.tiles);
         CKG(cudaGetLastError());
-        if ((rc = read_active(g)) != GMRF_OK) return rc;
         while (*g->h_active > 0 && iters < max_iter) {
             const int k = std::min(kGraphIters, max_iter - iters);
             if (k == kGraphIters) {
@@ -792,8 +900,9 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
     g->info.refinements = refinements;
     g->info.max_relres = worst;
     g->info.last_S = S;
-    // per inner iteration: 11 passes over binary32 [N][Sp] vectors, the binary32 matrix
-    // (4 + 4 B per entry), row pointers and the binary32 preconditioner
+    // per inner iteration: 11 passes over binary32 [N][Sp] vectors (r read and w written by
+    // the product; r, p, Kp, w, d read and p, Kp, d, r written by the update), the binary32
+    // matrix (4 + 4 B per entry) and the binary32 preconditioner
     g->info.bytes_per_iter = 11.0 * 4.0 * (double)g->N * Sp + 8.0 * (double)g->nnz + 8.0 * g->N;  // stored entries only
     // per refinement: correction (x, d) and residual (x gathered, b, r) in binary64
     g->info.bytes_per_refinement = (8.0 * 2 + 4.0 + 8.0 * 3) * (double)g->N * Sp + 12.0 * (double)g->nnz;
@@ -814,8 +923,9 @@ const char *gmrf_last_error(const gmrf_ctx *g) { return g ? g->err : g_create_er
 void gmrf_destroy(gmrf_ctx *g) {
     if (!g) return;
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    void *dev[] = {g->rowptr, g->col, g->val, g->val32, g->minv32, g->ell_col, g->ell_val, g->sqrtc, g->b, g->x, g->r, g->d, g->ri,
-                   g->p, g->q, g->part, g->scal, g->scal32, g->n_active};
+    void *dev[] = {g->rowptr, g->col, g->val, g->valz, g->minv32, g->ell_col, g->ell_valz, g->sqrtc, g->b,
+                   g->x, g->r, g->d, g->ri, g->p, g->ap, g->w, g->part, g->gpart, g->ctr, g->scal,
+                   g->scal32, g->n_active};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (g->h_active) cudaFreeHost(g->h_active);

@@ -125,3 +125,36 @@ def test_full_size_aneurysm_sampled():
     err = np.linalg.norm(x[:, pick] - ref, axis=0)
     assert np.all(err <= bound(m, z[:, pick], rtol))
     fs.close()
+
+
+def test_rows_longer_than_sixteen_take_the_csr_product():
+    """A flat fan around one hub node of degree 24, so the hub's row of K holds 25 entries
+    and the product runs over the CSR rows instead of the padded ones: the same bound
+    against the oracle's direct solve."""
+    n_ring = 24
+    ang = 2.0 * np.pi * np.arange(n_ring) / n_ring
+    ring1 = np.stack([0.01 * np.cos(ang), 0.01 * np.sin(ang), np.zeros(n_ring)], 1)
+    a2 = ang + np.pi / n_ring
+    ring2 = np.stack([0.02 * np.cos(a2), 0.02 * np.sin(a2), np.zeros(n_ring)], 1)
+    xyz = np.vstack([[[0.0, 0.0, 0.0]], ring1, ring2])
+    tri = []
+    for k in range(n_ring):
+        k1 = (k + 1) % n_ring
+        tri.append([0, 1 + k, 1 + k1])
+        tri.append([1 + k, 1 + n_ring + k, 1 + k1])
+        tri.append([1 + k1, 1 + n_ring + k, 1 + n_ring + k1])
+    tri = np.asarray(tri, dtype=np.int32)
+
+    class Mesh:
+        pass
+    m = Mesh()
+    m.xyz, m.tri, m.n_nodes = xyz, tri, xyz.shape[0]
+    S, rtol = 6, 1e-10
+    z = normals(m.n_nodes, S, 31)
+    fs = pkg.FieldSampler(xyz, tri, RHO)
+    x = fs.sample(torch.from_numpy(z).cuda(), rtol=rtol).cpu().numpy()
+    assert fs.info()["max_relres"] <= rtol
+    ref = og.sample(xyz, tri, og.kappa_of(RHO), z)
+    err = np.linalg.norm(x - ref, axis=0)
+    assert np.all(err <= bound(m, z, rtol)), (err, bound(m, z, rtol))
+    fs.close()
