@@ -540,13 +540,20 @@ __device__ __forceinline__ void node_force_geom(const ForceView<R> &w, const R *
     const int32_t p1 = __ldg(w.rowptr + i + 1);
     for (int32_t p = p0; p < p1; ++p) {
         const int4 en = __ldg(w.ent + p);
-        R ua[3][V], ub[3][V], e[V];
+        R da[3][V], db[3][V], e[V];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            ld_nc(g.row(en.y, d), ua[d]);
-            ld_nc(g.row(en.z, d), ub[d]);
+            ld_nc(g.row(en.y, d), da[d]);
+            ld_nc(g.row(en.z, d), db[d]);
         }
         ld_nc(g.ehrow(en.x), e);
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                da[d][v] -= ui[d][v];
+                db[d][v] -= ui[d][v];
+            }
         const int cz = en.w == 0 ? 2 : en.w - 1;
         const R *ky = kcs + ((int64_t)en.x * 3 + en.w) * 9 * Sp + s0;  // K_c,c+1, row d
         const R *kz = kcs + ((int64_t)en.x * 3 + cz) * 9 * Sp + s0;     // K_c+2,c, column d
@@ -561,14 +568,12 @@ __device__ __forceinline__ void node_force_geom(const ForceView<R> &w, const R *
             ld_nc(kz + (6 + d) * Sp, k5);
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                const R a0 = ua[0][v] - ui[0][v], a1 = ua[1][v] - ui[1][v], a2 = ua[2][v] - ui[2][v];
-                const R b0 = ub[0][v] - ui[0][v], b1 = ub[1][v] - ui[1][v], b2 = ub[2][v] - ui[2][v];
-                R t = k0[v] * a0;
-                t = fma(k1[v], a1, t);
-                t = fma(k2[v], a2, t);
-                t = fma(k3[v], b0, t);
-                t = fma(k4[v], b1, t);
-                t = fma(k5[v], b2, t);
+                R t = k0[v] * da[0][v];
+                t = fma(k1[v], da[1][v], t);
+                t = fma(k2[v], da[2][v], t);
+                t = fma(k3[v], db[0][v], t);
+                t = fma(k4[v], db[1][v], t);
+                t = fma(k5[v], db[2][v], t);
                 f[d][v] = fma(e[v], t, f[d][v]);
             }
         }
@@ -1237,8 +1242,11 @@ template <int FORM, typename R, bool FO>
 cudaError_t launch_one(const StepArgs<R> &a, cudaStream_t s, const StagePlan *plan) {
     const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
     if constexpr (!FO) {
-        if (a.kcs) {  // geometry update: per-realisation blocks, one launch shape
-            step_geom_kernel<FORM, R><<<blocks_for(threads, kBlock), kBlock, 0, s>>>(a);
+        if (a.kcs) {  // geometry update: per-realisation blocks, one launch shape, two samples
+                      // per thread (the per-incidence block loads need the registers)
+            StepArgs<R> g = a;
+            g.fv.Q = g.fv.Sp / 2;
+            step_geom_kernel<FORM, R, 2><<<blocks_for((int64_t)g.fv.N * g.fv.Q, kBlock), kBlock, 0, s>>>(g);
             return cudaGetLastError();
         }
     }

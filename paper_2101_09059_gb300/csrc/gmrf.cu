@@ -89,8 +89,8 @@ struct gmrf_ctx {
 namespace {
 
 // rows of scal
-// (kGam: r.z of the last iteration, kAlp: its alpha, kTot..kTot+2: the iteration's
-// totals of r.z, z.w, r.r)
+// (kGam: r.z of the last inner iteration, kAlp: its alpha, kTot..kTot+2: this
+// iteration's totals of r.z, z.w, r.r)
 enum { kGam = 0, kBbIn, kActIn, kBb, kRr, kScale, kActOut, kAlp, kTot, kScal = kTot + 3 };
 #define SCS(row) scal[(size_t)(row) * Sp + s]
 
@@ -118,9 +118,9 @@ struct Geo {
     int64_t tiles;
 };
 
-Geo geometry(int32_t N, int32_t Sp, int32_t grid) {
+Geo geometry(int32_t N, int32_t Sp, int32_t grid, int V = 2) {
     Geo o;
-    o.Q = Sp / 2;
+    o.Q = Sp / V;
     o.Qt = std::min(o.Q, kThreads);
     o.R = std::max(1, kThreads / o.Qt);
     o.tiles = ((int64_t)N + o.R - 1) / o.R;
@@ -252,64 +252,19 @@ __global__ void inner_init_kernel(const double *__restrict__ r, const double *__
     }
 }
 
-// Sum NQ per-thread partial pairs over the block's rows (fixed pairwise tree, binary64) and
-// write them to part[w][s][blockIdx.x], w = 0..NQ-1; sm holds NQ x (block size) double2.
-template <int NQ>
-__device__ __forceinline__ void block_partials(const double2 (&v)[NQ], double2 *sm, double *part, int G,
-                                               int32_t Sp, int lane_q) {
-    const int R = blockDim.y, Qt = blockDim.x, nt = R * Qt;
-    const int y = threadIdx.y, xq = threadIdx.x;
-#pragma unroll
-    for (int w = 0; w < NQ; w++) sm[w * nt + y * Qt + xq] = v[w];
-    __syncthreads();
-    int p2 = 1;
-    while (p2 < R) p2 <<= 1;
-    for (int st = p2 >> 1; st > 0; st >>= 1) {
-        if (y < st && y + st < R) {
-#pragma unroll
-            for (int w = 0; w < NQ; w++) {
-                const double2 a = sm[w * nt + y * Qt + xq], b = sm[w * nt + (y + st) * Qt + xq];
-                sm[w * nt + y * Qt + xq] = make_double2(a.x + b.x, a.y + b.y);
-            }
-        }
-        __syncthreads();
-    }
-    if (y == 0 && lane_q < Sp / 2) {
-#pragma unroll
-        for (int w = 0; w < NQ; w++) {
-            const double2 t = sm[w * nt + xq];
-            double *dst = part + ((size_t)w * Sp + 2 * lane_q) * G + blockIdx.x;
-            dst[0] = t.x;
-            dst[G] = t.y;
-        }
-    }
-}
-
-// Sum of cnt consecutive binary64 values src[0..cnt) by one warp, cnt <= 128: lane l adds
-// l, l + 32, l + 64, l + 96 in that order, then a butterfly; the same tree for every call.
-__device__ __forceinline__ double warp_sum_run(const double *src, int cnt, int lane) {
-    double a = 0.0;
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-        if (lane + 32 * k < cnt) a += __ldcg(src + lane + 32 * k);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-    return a;
-}
-
 // Two-level completion of the iteration's reduction. Every block has written its partials
 // part[w][s][b] (w < kNQ). A block adds itself to its group's counter (groups of kGroup
 // consecutive blockIdx.x, all chunks); the group's last block sums the group's partials
 // in block order into gpart[w][s][group] and adds itself to the top counter; the last of
 // those returns true, with every group sum visible to it. The last arrivals reset the
-// counters, so the next launch starts from zero. No block waits for another.
-constexpr int kGroup = 32;
+// counters, so the next launch starts from zero. No block waits for another. Each sum is
+// one thread's, over loads issued together, in a fixed order.
+constexpr int kGroup = 16;
 constexpr int kNQ = 3;  // r.z, z.w, r.r
-__device__ __forceinline__ bool reduce_arrive(const double *part, double *gpart, unsigned *ctr, int G,
-                                              int32_t Sp) {
+constexpr int kMatvecV = 4;  // samples per thread in the product
+__device__ __noinline__ bool reduce_arrive(const double *part, double *gpart, unsigned *ctr, int G, int32_t Sp) {
     __shared__ int s_last;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nwarps = (blockDim.x * blockDim.y) / 32, warp = tid / 32, lane = tid % 32;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     const int ngroups = (G + kGroup - 1) / kGroup;
     const int grp = blockIdx.x / kGroup;
     const int g0 = grp * kGroup, cnt = min(kGroup, G - g0);
@@ -324,10 +279,15 @@ __device__ __forceinline__ bool reduce_arrive(const double *part, double *gpart,
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
-    const int npairs = kNQ * Sp;
-    for (int pr = warp; warp < nwarps && pr < npairs; pr += nwarps) {  // whole warps only
-        const double t = warp_sum_run(part + (size_t)pr * G + g0, cnt, lane);
-        if (lane == 0) gpart[(size_t)pr * ngroups + grp] = t;
+    for (int pr = tid; pr < kNQ * Sp; pr += nt) {
+        const double *src = part + (size_t)pr * G + g0;
+        double v[kGroup];
+#pragma unroll
+        for (int b = 0; b < kGroup; b++) v[b] = b < cnt ? __ldcg(src + b) : 0.0;
+        double a = 0.0;
+#pragma unroll
+        for (int b = 0; b < kGroup; b++) a += v[b];
+        gpart[(size_t)pr * ngroups + grp] = a;
     }
     __threadfence();
     __syncthreads();
@@ -342,9 +302,22 @@ __device__ __forceinline__ bool reduce_arrive(const double *part, double *gpart,
     return true;
 }
 
-// The scalar part of an inner iteration, run by the block that completed the reduction:
-// totals per sample from the group sums, then for every sample s (state act_s: 0 inactive,
-// 1 first iteration, 2 later ones):
+// Sum of src[0..n) in index order, loads issued kGroup at a time.
+__device__ __forceinline__ double sum_run(const double *src, int n) {
+    double a = 0.0;
+    for (int b0 = 0; b0 < n; b0 += kGroup) {
+        double v[kGroup];
+#pragma unroll
+        for (int b = 0; b < kGroup; b++) v[b] = b0 + b < n ? __ldcg(src + b0 + b) : 0.0;
+#pragma unroll
+        for (int b = 0; b < kGroup; b++) a += v[b];
+    }
+    return a;
+}
+
+// The scalar part of an inner iteration, run by the block that completed the reduction,
+// one thread per sample s: the totals of r.z, z.w, r.r from the group sums, then (state
+// act_s: 0 inactive, 1 first iteration, 2 later ones)
 //   convergence: r.r <= tol^2 ||r_0||^2 ends the inner solve of s (alpha = beta = 0 from
 //   then on, so its d, r stay as they are);
 //   beta = gamma / gamma_prev (0 on the first iteration), alpha = gamma / (delta - beta
@@ -356,16 +329,11 @@ __device__ __forceinline__ bool reduce_arrive(const double *part, double *gpart,
 __device__ __noinline__ void finish_iteration(const double *gpart, double *scal, float *alpha32, float *beta32,
                                               int *n_active, int32_t Sp, double tol2) {
     __shared__ int s_count;
-    // the last block: totals per sample from the group sums, then the scalar recurrences
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-    const int nwarps = nt / 32, warp = tid / 32, lane = tid % 32;
     const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
-    for (int pr = warp; warp < nwarps && pr < kNQ * Sp; pr += nwarps) {
-        const double t = warp_sum_run(gpart + (size_t)pr * ngroups, ngroups, lane);
-        if (lane == 0) scal[(size_t)(kTot + pr / Sp) * Sp + pr % Sp] = t;
-    }
-    __syncthreads();
     if (tid == 0) s_count = 0;
+    for (int pr = tid; pr < kNQ * Sp; pr += nt)  // one thread per (quantity, sample)
+        scal[(size_t)kTot * Sp + pr] = sum_run(gpart + (size_t)pr * ngroups, ngroups);
     __syncthreads();
     int count = 0;
     for (int32_t s = tid; s < Sp; s += nt) {
@@ -404,69 +372,153 @@ __device__ __noinline__ void finish_iteration(const double *gpart, double *scal,
     if (tid == 0) *n_active = s_count;
 }
 
+// Loads and stores of four consecutive binary32 samples (16 bytes aligned).
+__device__ __forceinline__ void ldv(const float *p, float (&x)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+}
+__device__ __forceinline__ void stv(float *p, const float (&x)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+
 // Inner iteration, part 1: w = (K M^-1) r_i, the product with the column-scaled binary32
 // matrix (z = M^-1 r_i never stored), and partials of r.z, z.w and r.r over the block's
-// rows (binary32 per thread, binary64 across threads). WP = 8 or 16: padded rows (ELL,
-// the indices and values of a row in WP / 4 vector loads); WP = 0: CSR rows. The block
-// that completes the reduction then finishes the iteration (finish_iteration).
-template <int WP>
-__global__ void __launch_bounds__(kThreads, 4) cg_matvec_kernel(const int32_t *__restrict__ ell_col, const float *__restrict__ ell_valz,
-                                 const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-                                 const float *__restrict__ valz, const float *__restrict__ minv,
-                                 const float *__restrict__ ri, float *__restrict__ w, int32_t N, int32_t Sp,
-                                 int64_t tiles, double *part, double *gpart, unsigned *ctr, double *scal,
-                                 float *alpha32, float *beta32, int *n_active, double tol2) {
-    extern __shared__ double2 sm[];
-    float2 rz = make_float2(0.f, 0.f), zw = rz, rr = rz;
-    ROW_LOOP
-        float2 acc = make_float2(0.f, 0.f);
+// rows (binary32 per thread, binary64 across threads). A thread owns one row and V
+// samples; blockDim = (Qt lanes, R rows), grid = (G blocks, lane chunks) as in
+// geometry(Sp / V lanes), and block b owns the contiguous row tiles
+// [b tiles / G, (b + 1) tiles / G). WP = 8 or 16: padded rows (ELL); the block copies the
+// indices and values of up to kStageEntries entries of its rows into shared memory at
+// once, so each tile then costs one global round trip (its neighbour rows) instead of
+// two. WP = 0: CSR rows, read directly. The block that completes the reduction then
+// finishes the iteration (finish_iteration).
+constexpr int kStageEntries = 2048;
+template <int WP, int V>
+__global__ void __launch_bounds__(kThreads, 4) cg_matvec_kernel(
+    const int32_t *__restrict__ ell_col, const float *__restrict__ ell_valz, const int32_t *__restrict__ rowptr,
+    const int32_t *__restrict__ col, const float *__restrict__ valz, const float *__restrict__ minv,
+    const float *__restrict__ ri, float *__restrict__ w, int32_t N, int32_t Sp, int64_t tiles, double *part,
+    double *gpart, unsigned *ctr, double *scal, float *alpha32, float *beta32, int *n_active, double tol2) {
+    // dynamic shared memory: the staged rows (int32 indices, then binary32 values,
+    // max(kStageEntries, WP R) each), later the block's partial tree
+    extern __shared__ double smd[];
+    float rz[V], zw[V], rr[V];
+#pragma unroll
+    for (int k = 0; k < V; k++) rz[k] = zw[k] = rr[k] = 0.f;
+    const int R = blockDim.y, Qt = blockDim.x, nt = R * Qt;
+    const int y = threadIdx.y, xq = threadIdx.x, tid = y * Qt + xq;
+    const int lane = blockIdx.y * Qt + xq;
+    const bool lane_ok = lane < Sp / V;
+    const int s0 = V * lane;
+    const int64_t t0 = (int64_t)blockIdx.x * tiles / gridDim.x;
+    const int64_t t1 = (int64_t)(blockIdx.x + 1) * tiles / gridDim.x;
+    const int cap = WP > 0 ? max(kStageEntries, WP * R) : 0;
+    const int ct = WP > 0 ? max(1, kStageEntries / (WP * R)) : 1;  // tiles per staged chunk
+    int32_t *scol = reinterpret_cast<int32_t *>(smd);
+    float *sval = reinterpret_cast<float *>(scol + cap);
+    for (int64_t tc = t0; tc < t1; tc += ct) {
+        const int64_t te = min(tc + (int64_t)ct, t1);
         if constexpr (WP > 0) {
-            int32_t cj[WP];
-            float aj[WP];
-            const int4 *cc = reinterpret_cast<const int4 *>(ell_col + (size_t)i * WP);
-            const float4 *vv = reinterpret_cast<const float4 *>(ell_valz + (size_t)i * WP);
-#pragma unroll
-            for (int u = 0; u < WP / 4; u++) {
-                const int4 c = __ldg(cc + u);
-                const float4 v = __ldg(vv + u);
-                cj[4 * u] = c.x;
-                cj[4 * u + 1] = c.y;
-                cj[4 * u + 2] = c.z;
-                cj[4 * u + 3] = c.w;
-                aj[4 * u] = v.x;
-                aj[4 * u + 1] = v.y;
-                aj[4 * u + 2] = v.z;
-                aj[4 * u + 3] = v.w;
+            const int64_t r0 = tc * R, r1 = min(te * R, (int64_t)N);
+            const int n4 = (int)((r1 - r0) * WP / 4);
+            const int4 *gc = reinterpret_cast<const int4 *>(ell_col + r0 * WP);
+            const int4 *gv = reinterpret_cast<const int4 *>(ell_valz + r0 * WP);
+            __syncthreads();  // the previous chunk's reads are done
+            for (int k = tid; k < n4; k += nt) {
+                reinterpret_cast<int4 *>(scol)[k] = __ldg(gc + k);
+                reinterpret_cast<int4 *>(sval)[k] = __ldg(gv + k);
             }
+            __syncthreads();
+        }
+        for (int64_t t = tc; t < te; t++) {
+            const int64_t i = t * R + y;
+            if (i >= N || !lane_ok) continue;
+            const size_t o = (size_t)i * Sp + s0;
+            float acc[V];
 #pragma unroll
-            for (int u = 0; u < WP; u++) {
-                const float2 v = __ldg(reinterpret_cast<const float2 *>(ri + (size_t)cj[u] * Sp + s0));
-                acc.x = fmaf(aj[u], v.x, acc.x);
-                acc.y = fmaf(aj[u], v.y, acc.y);
+            for (int k = 0; k < V; k++) acc[k] = 0.f;
+            if constexpr (WP > 0) {
+                int32_t cj[WP];
+                float aj[WP];
+                const int4 *cc = reinterpret_cast<const int4 *>(scol + (i - tc * R) * WP);
+                const float4 *vv = reinterpret_cast<const float4 *>(sval + (i - tc * R) * WP);
+#pragma unroll
+                for (int u = 0; u < WP / 4; u++) {
+                    const int4 c = cc[u];
+                    const float4 v = vv[u];
+                    cj[4 * u] = c.x;
+                    cj[4 * u + 1] = c.y;
+                    cj[4 * u + 2] = c.z;
+                    cj[4 * u + 3] = c.w;
+                    aj[4 * u] = v.x;
+                    aj[4 * u + 1] = v.y;
+                    aj[4 * u + 2] = v.z;
+                    aj[4 * u + 3] = v.w;
+                }
+#pragma unroll
+                for (int u = 0; u < WP; u++) {
+                    float v[V];
+                    ldv(ri + (size_t)cj[u] * Sp + s0, v);
+#pragma unroll
+                    for (int k = 0; k < V; k++) acc[k] = fmaf(aj[u], v[k], acc[k]);
+                }
+            } else {
+                const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
+                for (int32_t e = k0; e < k1; e++) {
+                    const float a = __ldg(valz + e);
+                    float v[V];
+                    ldv(ri + (size_t)__ldg(col + e) * Sp + s0, v);
+#pragma unroll
+                    for (int k = 0; k < V; k++) acc[k] = fmaf(a, v[k], acc[k]);
+                }
             }
-        } else {
-            const int32_t k0 = __ldg(rowptr + i), k1 = __ldg(rowptr + i + 1);
-            for (int32_t k = k0; k < k1; k++) {
-                const float a = __ldg(valz + k);
-                const float2 v = __ldg(reinterpret_cast<const float2 *>(ri + (size_t)__ldg(col + k) * Sp + s0));
-                acc.x = fmaf(a, v.x, acc.x);
-                acc.y = fmaf(a, v.y, acc.y);
+            stv(w + o, acc);
+            float rv[V];
+            ldv(ri + o, rv);
+            const float m = __ldg(minv + i);
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                const float zv = m * rv[k];
+                rz[k] = fmaf(rv[k], zv, rz[k]);
+                zw[k] = fmaf(zv, acc[k], zw[k]);
+                rr[k] = fmaf(rv[k], rv[k], rr[k]);
             }
         }
-        stf2(w + o, acc);
-        const float2 rv = ldf2(ri + o);
-        const float m = __ldg(minv + i);
-        const float2 zv = make_float2(m * rv.x, m * rv.y);
-        rz.x = fmaf(rv.x, zv.x, rz.x);
-        rz.y = fmaf(rv.y, zv.y, rz.y);
-        zw.x = fmaf(zv.x, acc.x, zw.x);
-        zw.y = fmaf(zv.y, acc.y, zw.y);
-        rr.x = fmaf(rv.x, rv.x, rr.x);
-        rr.y = fmaf(rv.y, rv.y, rr.y);
     }
-    const double2 v[kNQ] = {widen(rz), widen(zw), widen(rr)};
-    block_partials<kNQ>(v, sm, part, gridDim.x, Sp, lane_q);
-    if (reduce_arrive(part, gpart, ctr, gridDim.x, Sp)) finish_iteration(gpart, scal, alpha32, beta32, n_active, Sp, tol2);
+    // per-block sums over the rows: a fixed pairwise tree in binary64, [kNQ][V][threads]
+    __syncthreads();  // the staging buffer becomes the tree
+#pragma unroll
+    for (int k = 0; k < V; k++) {
+        smd[(0 * V + k) * nt + tid] = ens::f32_to_f64(rz[k]);
+        smd[(1 * V + k) * nt + tid] = ens::f32_to_f64(zw[k]);
+        smd[(2 * V + k) * nt + tid] = ens::f32_to_f64(rr[k]);
+    }
+    __syncthreads();
+    int p2 = 1;
+    while (p2 < R) p2 <<= 1;
+    for (int st = p2 >> 1; st > 0; st >>= 1) {
+        if (y < st && y + st < R)
+#pragma unroll
+            for (int q = 0; q < kNQ * V; q++) smd[q * nt + tid] += smd[q * nt + tid + st * Qt];
+        __syncthreads();
+    }
+    if (y == 0 && lane_ok)
+#pragma unroll
+        for (int q = 0; q < kNQ; q++)
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                part[((size_t)q * Sp + s0 + k) * gridDim.x + blockIdx.x] = smd[(q * V + k) * nt + xq];
+    if (reduce_arrive(part, gpart, ctr, gridDim.x, Sp))
+        finish_iteration(gpart, scal, alpha32, beta32, n_active, Sp, tol2);
+}
+
+// Dynamic shared memory of cg_matvec_kernel<WP, V> for a block of (Qt, R).
+size_t matvec_smem(int WP, int V, int Qt, int R) {
+    const size_t tree = sizeof(double) * kNQ * V * Qt * R;
+    const size_t stage = WP > 0 ? 8 * (size_t)std::max(kStageEntries, WP * R) : 0;
+    return std::max(tree, stage);
 }
 
 // Inner iteration, part 2, four samples per thread: z = M^-1 r, p = z + beta p,
@@ -599,15 +651,15 @@ int alloc_work(gmrf_ctx *g, int32_t Sp) {
 
 // One inner (binary32) CG iteration: two launches on g's stream.
 cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double tol2) {
-    const Geo o = geometry(g->N, Sp, g->grid);
+    constexpr int V = kMatvecV;
+    const Geo o = geometry(g->N, Sp, g->grid, V);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
-    const size_t sm = sizeof(double2) * kNQ * o.Qt * o.R;
     float *alpha = g->scal32, *beta = g->scal32 + Sp;
-#define CG_MATVEC(WP)                                                                                         \
-    cg_matvec_kernel<WP><<<grid, block, sm, g->stream>>>(g->ell_col, g->ell_valz, g->rowptr, g->col, g->valz,  \
-                                                         g->minv32, g->ri, g->w, g->N, Sp, o.tiles, g->part,   \
-                                                         g->gpart, g->ctr, g->scal, alpha, beta, g->n_active,  \
-                                                         tol2)
+#define CG_MATVEC(WP)                                                                                           \
+    cg_matvec_kernel<WP, V><<<grid, block, matvec_smem(WP, V, o.Qt, o.R), g->stream>>>(g->ell_col, g->ell_valz, g->rowptr, g->col, g->valz, \
+                                                            g->minv32, g->ri, g->w, g->N, Sp, o.tiles, g->part,  \
+                                                            g->gpart, g->ctr, g->scal, alpha, beta, g->n_active, \
+                                                            tol2)
     if (g->ell_w == 8)
         CG_MATVEC(8);
     else if (g->ell_w == 16)
@@ -789,8 +841,10 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
         const struct {
             const void *f;
             size_t smem;
-        } fns[] = {{(const void *)cg_matvec_kernel<8>, kNQ * smb}, {(const void *)cg_matvec_kernel<16>, kNQ * smb},
-                   {(const void *)cg_matvec_kernel<0>, kNQ * smb}, {(const void *)inner_init_kernel, 0},
+        } fns[] = {{(const void *)cg_matvec_kernel<8, kMatvecV>, kNQ * kMatvecV * 8 * kThreads},
+                   {(const void *)cg_matvec_kernel<16, kMatvecV>, kNQ * kMatvecV * 8 * kThreads},
+                   {(const void *)cg_matvec_kernel<0, kMatvecV>, kNQ * kMatvecV * 8 * kThreads},
+                   {(const void *)inner_init_kernel, 0},
                    {(const void *)residual_kernel, smb}, {(const void *)rhs_kernel, smb}};
         for (const auto &k : fns)
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k.f, kThreads, k.smem) == cudaSuccess && per > 0)
