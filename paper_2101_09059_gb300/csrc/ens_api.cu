@@ -64,6 +64,7 @@ void *dev_alloc(ens_ctx *c, size_t bytes) {
     }
     if (p) {
         c->bufs.emplace_back(p, bytes);
+        c->buf_epoch.push_back(c->captures);
         c->held_bytes += bytes;
     }
     return p;
@@ -79,7 +80,9 @@ void dev_free(ens_ctx *c, void *p) {
             else
                 cudaFree(p);
             c->held_bytes -= bytes;
+            if (c->buf_epoch[k] < c->captures) c->buf_generation++;
             c->bufs.erase(c->bufs.begin() + k);
+            c->buf_epoch.erase(c->buf_epoch.begin() + k);
             return;
         }
     }
@@ -396,7 +399,8 @@ const char *ens_last_error(const ens_ctx *c) { return c ? c->err.c_str() : g_cre
 void ens_destroy(ens_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaGraphExec_t g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
     if (c->cap) cudaStreamDestroy(c->cap);
     while (!c->bufs.empty()) dev_free(c, c->bufs.back().first);
     if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -823,8 +827,10 @@ int ens_set_amplitudes(ens_ctx *c, int64_t first_row, int64_t n_rows, const doub
 
 namespace {
 // Steps through a captured graph: kGraphSteps launches and one counter advance, replayed.
-// The graph bakes buffer pointers, the launch shape and the parity of the first step, so
-// it is rebuilt when any of them changed. Returns the number of steps done this way.
+// A graph bakes buffer pointers, the launch shape and the parity of the first step. Its
+// key holds those, the current geometry-update block buffer and the buffer generation
+// (advanced when a buffer that a capture may have baked is released), and a graph is
+// captured when no kept one has the key. Returns the number of steps done this way.
 int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
     *done = 0;
     const int K = kGraphSteps;
@@ -832,11 +838,18 @@ int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
     std::vector<uintptr_t> key = {(uintptr_t)(c->cur & 1), (uintptr_t)c->amp, (uintptr_t)c->modes,
                                   (uintptr_t)c->J, (uintptr_t)c->variant, (uintptr_t)c->plan.staged,
                                   (uintptr_t)c->peak, (uintptr_t)c->peak_stride,
-                                  (uintptr_t)(c->geo_active ? c->kcs[c->kcs_cur] : nullptr)};
-    if (!c->graph || c->graph_key != key) {
-        if (c->graph) cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
+                                  (uintptr_t)(c->geo_active ? c->kcs[c->kcs_cur] : nullptr),
+                                  (uintptr_t)c->buf_generation};
+    int slot = -1;
+    for (int q = 0; q < kGraphSlots && slot < 0; q++)
+        if (c->graph[q] && c->graph_key[q] == key) slot = q;
+    if (slot < 0) {
+        slot = c->graph_next;
+        c->graph_next = (c->graph_next + 1) % kGraphSlots;
+        if (c->graph[slot]) cudaGraphExecDestroy(c->graph[slot]);
+        c->graph[slot] = nullptr;
         if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        c->captures++;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
@@ -848,13 +861,16 @@ int graph_steps(ens_ctx *c, int64_t n, int64_t *done) {
             return fail(c, ENS_ERR_CUDA, "time-loop graph capture: %s",
                         cudaGetErrorString(e != cudaSuccess ? e : e2));
         }
-        e = cudaGraphInstantiate(&c->graph, g, 0);
+        e = cudaGraphInstantiate(&c->graph[slot], g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return fail(c, ENS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-        c->graph_key = key;
+        if (e != cudaSuccess) {
+            c->graph[slot] = nullptr;
+            return fail(c, ENS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        c->graph_key[slot] = key;
     }
     while (n - *done >= K) {  // K is even: the parity is the same after every replay
-        CK(cudaGraphLaunch(c->graph, c->stream));
+        CK(cudaGraphLaunch(c->graph[slot], c->stream));
         *done += K;
     }
     return ENS_OK;

@@ -11,6 +11,7 @@
 namespace ens {
 constexpr int kVariants = 13;  // launch shapes the autotuner can time (see ens_info_t)
 constexpr int kGraphSteps = 32;  // steps per captured time-loop graph (even)
+constexpr int kGraphSlots = 4;   // time-loop graphs kept per context
 }
 
 struct ens_ctx {
@@ -26,6 +27,13 @@ struct ens_ctx {
     std::string err;
     size_t held_bytes = 0;
     std::vector<std::pair<void *, size_t>> bufs;
+    // Kept time-loop graphs bake buffer addresses. buf_epoch[k] is the number of graph
+    // captures made before bufs[k] was allocated; releasing a buffer that some capture may
+    // have baked (one allocated before the latest capture) advances buf_generation, which
+    // is part of every graph key, so no kept graph can name a released buffer.
+    std::vector<uint64_t> buf_epoch;
+    uint64_t captures = 0;
+    uint64_t buf_generation = 0;
 
     // device data
     int32_t *rowptr = nullptr;
@@ -51,10 +59,13 @@ struct ens_ctx {
     int32_t variant = 0;
     float variant_us[ens::kVariants] = {};
     int32_t flags_in = 0;
-    // time-loop graph of kGraphSteps launches + counter advance (see ens_step)
+    // time-loop graphs of kGraphSteps launches + counter advance (see ens_step), the most
+    // recent kGraphSlots of them with their keys; a geometry update alternates between two
+    // block buffers, so it keeps two graphs in use
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    std::vector<uintptr_t> graph_key;
+    cudaGraphExec_t graph[ens::kGraphSlots] = {};
+    std::vector<uintptr_t> graph_key[ens::kGraphSlots];
+    int32_t graph_next = 0;  // slot replaced by the next capture
     // output statistics: element-mean modulus [E][Sp], stress operators [E][6][9] (after
     // ens_set_centerline), the quantity buffer, and the probe histories
     double *ebar = nullptr;

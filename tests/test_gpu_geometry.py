@@ -102,3 +102,29 @@ def test_geometry_update_on_the_paper_cylinder_sampled():
         err = _rel(u[s], ref[k])
         print(f"cylinder geometry update sample {s}: rel-L2 {err:.2e}")
         assert err < TOL["kahan32"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "kahan32"])
+def test_geometry_update_graph_replays_equal_direct_launches(precision):
+    """Re-assembly every 80 steps: each segment replays captured 32-step graphs, and the
+    segments alternate between the two per-realisation block buffers (two kept graphs).
+    The run equals the one launched step by step, bit for bit, and so do the runs after
+    a reset, after the peak tracking adds a launch, and after the update is switched off."""
+    case = _case()
+    runs = []
+    for flags in (0, ens.FLAG_NO_GRAPH):
+        e = ens.Ensemble.from_case(case, precision=precision, flags=flags)
+        e.set_geometry_update(80)
+        e.step(400)
+        u = [e.displacement()]
+        e.reset()
+        e.set_peak(1)
+        e.step(330)
+        u.append(e.displacement())
+        e.set_geometry_update(0)
+        e.step(130)
+        u.append(e.displacement())
+        runs.append(u)
+        e.close()
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
