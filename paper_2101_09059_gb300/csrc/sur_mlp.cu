@@ -26,19 +26,19 @@ namespace {
 
 // ---- tensor-core product (tcgen05) ----------------------------------------------------
 // One CTA of 128 threads computes a 128 x 32 tile of C (the network's products are a few
-// tiles wide, so narrow tiles give more CTAs). Per K stage of 32 the threads stage
+// tiles wide, so narrow tiles give more CTAs). Per K stage of 64 the threads stage
 // the FP32 operands as BF16 into shared memory in the canonical K-major layout without
-// swizzle: 8 x 16-byte core matrices (8 rows of 8 consecutive k), the four k-groups of a
-// row group 128 bytes apart (leading byte offset) and row groups 512 bytes apart (stride
-// byte offset). One thread then issues two tcgen05.mma (M = 128, N = 32, K = 16) into the
+// swizzle: 8 x 16-byte core matrices (8 rows of 8 consecutive k), the eight k-groups of a
+// row group 128 bytes apart (leading byte offset) and row groups 1024 bytes apart (stride
+// byte offset). One thread then issues four tcgen05.mma (M = 128, N = 32, K = 16) into the
 // CTA's 32 tensor-memory columns and commits them to an mbarrier that every thread waits
 // on (bounded) before the stage is overwritten. At the end warp w reads rows 32w .. 32w+31
 // of the accumulator with tcgen05.ld and applies the epilogue.
-constexpr int TM = 128, TN = 32, TK = 32;
+constexpr int TM = 128, TN = 32, TK = 64;
 constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 32;
-constexpr uint32_t kCoreK = 128;   // bytes between core matrices along k
-constexpr uint32_t kCoreMN = 512;  // bytes between 8-row groups
+constexpr uint32_t kCoreK = 128;                    // bytes between core matrices along k
+constexpr uint32_t kCoreMN = (uint32_t)TK * 16u;    // bytes between 8-row groups
 constexpr uint32_t kAsBytes = TM / 8 * kCoreMN, kBsBytes = TN / 8 * kCoreMN;
 // dynamic shared memory per CTA: at most 8 CTAs fit on an SM, so their 8 x 32 columns
 // never exceed the SM's 512 columns of tensor memory and tcgen05.alloc never waits
@@ -550,6 +550,9 @@ struct sur_ctx {
     long long off[6] = {0, 0, 0, 0, 0, 0};  // W1 b1 W2 b2 W3 b3 in the flat vectors
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream for graph capture
+    // the backward pass runs its weight gradients on a side branch (fork and join by events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::string err;
     float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     // device buffers
@@ -610,7 +613,10 @@ int forward(sur_ctx *c, cudaStream_t s, const float *x, int B) {
     return SUR_OK;
 }
 
-// Loss and gradients of B rows (x, t on device) into c->g; loss to *loss_dev.
+// Loss and gradients of B rows (x, t on device) into c->g; loss to *loss_dev. The chain
+// of activation gradients (d2, d1) stays on s; the weight gradients and bias sums that
+// branch off it run on c->side, forked and joined by events, so a captured graph holds
+// them as parallel branches. Every gradient is written when s continues after the call.
 int backward(sur_ctx *c, cudaStream_t s, const float *x, const float *t, int B, float *loss_dev) {
     const int H = c->H, no = c->nout, ni = c->nin;
     const float *W2 = c->p + c->off[2], *W3 = c->p + c->off[4];
@@ -620,17 +626,24 @@ int backward(sur_ctx *c, cudaStream_t s, const float *x, const float *t, int B, 
     if (rc != SUR_OK) return rc;
     mse_kernel<<<1, 256, 0, s>>>(c->y, t, (long long)B * no, c->dy, loss_dev, no, gb3);  // and db3
     SCK(cudaGetLastError());
-    // layer 3: dW3 = dy^T a2, db3 = colsum dy (above), d2 = (dy W3) * gelu'(z2)
-    SCK((gemm<kStore>(s, no, H, B, c->dy, 1, no, c->a2, H, 1, gW3, H)));
+    // layer 3: dW3 = dy^T a2 (side), db3 = colsum dy (above), d2 = (dy W3) * gelu'(z2)
+    SCK(cudaEventRecord(c->ev[0], s));
+    SCK(cudaStreamWaitEvent(c->side, c->ev[0], 0));
+    SCK((gemm<kStore>(c->side, no, H, B, c->dy, 1, no, c->a2, H, 1, gW3, H)));
     SCK((gemm<kGeluGrad>(s, B, H, no, c->dy, no, 1, W3, H, 1, c->d2, H, nullptr, c->z2)));
-    // layer 2
-    SCK((gemm<kStore>(s, H, H, B, c->d2, 1, H, c->a1, H, 1, gW2, H)));
-    colsum_kernel<<<cdiv(H, 128), 128, 0, s>>>(c->d2, B, H, gb2);
+    // layer 2: dW2 = d2^T a1 and db2 (side), d1 = (d2 W2) * gelu'(z1)
+    SCK(cudaEventRecord(c->ev[1], s));
+    SCK(cudaStreamWaitEvent(c->side, c->ev[1], 0));
+    SCK((gemm<kStore>(c->side, H, H, B, c->d2, 1, H, c->a1, H, 1, gW2, H)));
+    colsum_kernel<<<cdiv(H, 128), 128, 0, c->side>>>(c->d2, B, H, gb2);
+    SCK(cudaGetLastError());
     SCK((gemm<kGeluGrad>(s, B, H, H, c->d2, H, 1, W2, H, 1, c->d1, H, nullptr, c->z1)));
     // layer 1
     SCK((gemm<kStore>(s, H, ni, B, c->d1, 1, H, x, ni, 1, gW1, ni)));
     colsum_kernel<<<cdiv(H, 128), 128, 0, s>>>(c->d1, B, H, gb1);
     SCK(cudaGetLastError());
+    SCK(cudaEventRecord(c->ev[2], c->side));  // join
+    SCK(cudaStreamWaitEvent(s, c->ev[2], 0));
     return SUR_OK;
 }
 
@@ -656,6 +669,12 @@ void sur_destroy(sur_ctx *c) {
     if (c->epoch_graph) cudaGraphExecDestroy(c->epoch_graph);
     for (void *p : c->bufs) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -706,6 +725,8 @@ int sur_create(int32_t n_in, int32_t n_hidden, int32_t n_out, int32_t max_batch,
         SCK(cudaMemset(c->g, 0, sizeof(float) * c->np));
         SCK(cudaMemset(c->tstep, 0, sizeof(int)));
         SCK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+        SCK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->ev) SCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         SCK(gemm_setup());
         return SUR_OK;
     }();

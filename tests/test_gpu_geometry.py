@@ -19,6 +19,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2101_09059_gb300 as ens  # noqa: E402
+from paper_2101_09059_gb300.ensemble import FLAG_NO_GRAPH  # noqa: E402
 
 TOL = {"fp64": 1e-10, "fp32_force": 1e-5, "kahan32": 1e-5}
 
@@ -112,7 +113,7 @@ def test_geometry_update_graph_replays_equal_direct_launches(precision):
     a reset, after the peak tracking adds a launch, and after the update is switched off."""
     case = _case()
     runs = []
-    for flags in (0, ens.FLAG_NO_GRAPH):
+    for flags in (0, FLAG_NO_GRAPH):
         e = ens.Ensemble.from_case(case, precision=precision, flags=flags)
         e.set_geometry_update(80)
         e.step(400)
