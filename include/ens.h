@@ -228,8 +228,9 @@ int ens_reset(ens_ctx *ctx);
  * block read by the two corners it couples) instead of the shared ones, several times
  * the bytes of a linear step; a re-assembly
  * costs one binary64 pass over the elements and samples (the new blocks) and one over the
- * nodes and samples, which adds (K_old - K_new) u_m to the correction in binary64 from the
- * words the step gathers (so the binary32 forms' rounding does not accumulate in it).
+ * nodes and samples, which adds (K_old - K_new) u_m to the correction: coefficient
+ * differences first, in the form's precision, the running sum in binary64, so the binary32
+ * forms' rounding of full forces does not accumulate in it.
  * Selective re-assembly (k > 1) uses the stiffness of a segment's start for the whole
  * segment, a path error of order k. An element that degenerates on its deformed surface
  * ends ens_step with ENS_ERR_NONFINITE. Contexts with a geometry update cannot join a

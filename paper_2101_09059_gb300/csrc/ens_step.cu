@@ -608,50 +608,51 @@ __global__ void __launch_bounds__(kBlock) step_geom_kernel(const StepArgs<R> a) 
     node_update<FORM, R, V>(a, i, s0, ui, f, fe);
 }
 
-// (K_old - K_new) u at node i from the gathered words of u, in binary64 arithmetic:
-// K_old from the shared coupling blocks (scaled by (E h)) when kcs_old is null, else from
-// the per-realisation corner blocks [E][3][9][Sp] read as in node_force_geom; K_new from
-// kcs_new. Both stiffnesses scale by the same (E h), so the coefficient differences are
-// taken first (exact for binary32 coefficients), then one product per coefficient.
+// (K_old - K_new) u at node i from the gathered words of u: K_old from the shared
+// coupling blocks (scaled by (E h)) when kcs_old is null, else from the per-realisation
+// corner blocks [E][3][9][Sp] read as in node_force_geom; K_new from kcs_new. Both
+// stiffnesses scale by the same (E h), so the coefficient differences are taken first:
+// the old and new coefficients are close, so their difference is exact or nearly so in
+// the form's precision, and the result carries the rounding of the small difference
+// force only, not the cancellation of two full forces.
 template <typename R, int V>
 __device__ __forceinline__ void node_force_delta(const ForceView<R> &w, const R *__restrict__ kcs_old,
                                                  const R *__restrict__ kcs_new, const R *__restrict__ ug, int32_t i,
-                                                 int32_t s0, const R (&ui)[3][V], double (&f)[3][V]) {
+                                                 int32_t s0, const R (&ui)[3][V], R (&f)[3][V]) {
     const int64_t Sp = w.Sp;
 #pragma unroll
     for (int d = 0; d < 3; d++)
 #pragma unroll
-        for (int v = 0; v < V; v++) f[d][v] = 0.0;
+        for (int v = 0; v < V; v++) f[d][v] = R(0);
     const GatherBase<R> g(ug, w.eh, (int32_t)Sp, s0);
     const int32_t p0 = __ldg(w.rowptr + i);
     const int32_t p1 = __ldg(w.rowptr + i + 1);
     for (int32_t p = p0; p < p1; ++p) {
         const int4 en = __ldg(w.ent + p);
-        R ua[3][V], ub[3][V], e[V];
+        R da[3][V], db[3][V], e[V];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            ld_nc(g.row(en.y, d), ua[d]);
-            ld_nc(g.row(en.z, d), ub[d]);
+            ld_nc(g.row(en.y, d), da[d]);
+            ld_nc(g.row(en.z, d), db[d]);
         }
         ld_nc(g.ehrow(en.x), e);
-        double da[3][V], db[3][V];
 #pragma unroll
         for (int d = 0; d < 3; d++)
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                da[d][v] = (double)ua[d][v] - (double)ui[d][v];
-                db[d][v] = (double)ub[d][v] - (double)ui[d][v];
+                da[d][v] -= ui[d][v];
+                db[d][v] -= ui[d][v];
             }
         const int cz = en.w == 0 ? 2 : en.w - 1;
         const int64_t oy = ((int64_t)en.x * 3 + en.w) * 9 * Sp + s0;  // K_c,c+1, row d
         const int64_t oz = ((int64_t)en.x * 3 + cz) * 9 * Sp + s0;     // K_c+2,c, column d
-        const R *ks = w.kc + (int64_t)p * Kc<R>::stride;  // shared blocks of this incidence
+        const R *ks = w.kc + (int64_t)p * Kc<R>::stride;              // shared blocks of this incidence
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             // coefficient q of row d: q < 3 couples to corner y, q >= 3 to corner z
             const int64_t off[6] = {oy + (3 * d) * Sp, oy + (3 * d + 1) * Sp, oy + (3 * d + 2) * Sp,
                                     oz + d * Sp,       oz + (3 + d) * Sp,     oz + (6 + d) * Sp};
-            double dk[6][V];
+            R dk[6][V];
 #pragma unroll
             for (int q = 0; q < 6; q++) {
                 R kn[V];
@@ -659,35 +660,35 @@ __device__ __forceinline__ void node_force_delta(const ForceView<R> &w, const R 
                 if (kcs_old == nullptr) {
                     const R ko = __ldg(ks + (q < 3 ? 3 * d + q : 9 + 3 * d + (q - 3)));
 #pragma unroll
-                    for (int v = 0; v < V; v++) dk[q][v] = (double)ko - (double)kn[v];
+                    for (int v = 0; v < V; v++) dk[q][v] = ko - kn[v];
                 } else {
                     R ko[V];
                     ld_nc(kcs_old + off[q], ko);
 #pragma unroll
-                    for (int v = 0; v < V; v++) dk[q][v] = (double)ko[v] - (double)kn[v];
+                    for (int v = 0; v < V; v++) dk[q][v] = ko[v] - kn[v];
                 }
             }
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                double t = dk[0][v] * da[0][v];
+                R t = dk[0][v] * da[0][v];
                 t = fma(dk[1][v], da[1][v], t);
                 t = fma(dk[2][v], da[2][v], t);
                 t = fma(dk[3][v], db[0][v], t);
                 t = fma(dk[4][v], db[1][v], t);
                 t = fma(dk[5][v], db[2][v], t);
-                f[d][v] = fma((double)e[v], t, f[d][v]);
+                f[d][v] = fma(e[v], t, f[d][v]);
             }
         }
     }
 }
 
-// Geometry update, at a re-assembly on the state u = a.ug_cur: c64 += K_old u - K_new u
-// (shared blocks for K_old when kcs_old is null), in binary64 from the words the step
-// gathers. c64 then holds the exact running sum of the corrections, so the rounding of a
-// binary32 form does not accumulate over re-assemblies; the step adds its rounding to
-// binary32, cR.
+// Geometry update, at a re-assembly on the state u = a.ug_cur: c64 += (K_old - K_new) u
+// (shared blocks for K_old when kcs_old is null), from the words the step gathers. The
+// increment is small next to the force, and its rounding with it, so the running sum in
+// binary64 does not accumulate the binary32 forms' rounding of full forces; the step adds
+// its rounding to binary32, cR.
 template <typename R, int V>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) geo_correct_kernel(const StepArgs<R> a, const R *__restrict__ kcs_old,
+__global__ void __launch_bounds__(kBlock) geo_correct_kernel(const StepArgs<R> a, const R *__restrict__ kcs_old,
                                                              const R *__restrict__ kcs_new, double *__restrict__ c64,
                                                              R *__restrict__ cR) {
     const int32_t Q = a.fv.Q;
@@ -699,14 +700,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 3 : 2) geo_correct_ke
     R ui[3][V];
 #pragma unroll
     for (int d = 0; d < 3; d++) ld_nc(a.ug_cur + ((int64_t)i * 3 + d) * Sp + s0, ui[d]);
-    double df[3][V];
+    R df[3][V];
     node_force_delta<R, V>(a.fv, kcs_old, kcs_new, a.ug_cur, i, s0, ui, df);
 #pragma unroll
     for (int d = 0; d < 3; d++)
 #pragma unroll
         for (int v = 0; v < V; v++) {
             const int64_t idx = ((int64_t)i * 3 + d) * Sp + s0 + v;
-            const double c = c64[idx] + df[d][v];
+            const double c = c64[idx] + (double)df[d][v];
             c64[idx] = c;
             cR[idx] = (R)c;
         }
@@ -1378,10 +1379,10 @@ template <typename R>
 cudaError_t launch_geo_correct(const StepArgs<R> &a0, const R *kcs_old, const R *kcs_new, double *c64, R *cR,
                                cudaStream_t s) {
     StepArgs<R> a = a0;
-    a.fv.Q = a.fv.Sp;  // one sample per thread: the binary64 sums need the registers
+    a.fv.Q = a.fv.Sp / 2;  // two samples per thread, as the updated step
     const int64_t threads = (int64_t)a.fv.N * a.fv.Q;
     if (threads == 0) return cudaSuccess;
-    geo_correct_kernel<R, 1><<<blocks_for(threads, kBlock), kBlock, 0, s>>>(a, kcs_old, kcs_new, c64, cR);
+    geo_correct_kernel<R, 2><<<blocks_for(threads, kBlock), kBlock, 0, s>>>(a, kcs_old, kcs_new, c64, cR);
     return cudaGetLastError();
 }
 template cudaError_t launch_geo_correct<double>(const StepArgs<double> &, const double *, const double *, double *,
