@@ -315,9 +315,9 @@ __device__ __forceinline__ double sum_run(const double *src, int n) {
     return a;
 }
 
-// The scalar part of an inner iteration, run by the block that completed the reduction,
-// one thread per sample s: the totals of r.z, z.w, r.r from the group sums, then (state
-// act_s: 0 inactive, 1 first iteration, 2 later ones)
+// The scalar part of an inner iteration, run by the block that completed the reduction:
+// the totals of r.z, z.w, r.r from the group sums (one thread per quantity and sample),
+// then, one thread per sample s (state act_s: 0 inactive, 1 first iteration, 2 later ones),
 //   convergence: r.r <= tol^2 ||r_0||^2 ends the inner solve of s (alpha = beta = 0 from
 //   then on, so its d, r stay as they are);
 //   beta = gamma / gamma_prev (0 on the first iteration), alpha = gamma / (delta - beta
