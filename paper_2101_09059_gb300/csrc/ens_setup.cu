@@ -37,6 +37,9 @@ struct ElemFrame {
     double area;
 };
 
+// RECIP: scale by the reciprocals of |n| and |X_2 - X_0| (two binary64 divisions instead
+// of six, results within a few ulp of the quotients); the set-up kernel divides.
+template <bool RECIP = false>
 __device__ __forceinline__ bool element_frame(const double X[3][3], ElemFrame &f) {
     double a[3], c[3], nn[3];
     for (int d = 0; d < 3; d++) {
@@ -47,9 +50,17 @@ __device__ __forceinline__ bool element_frame(const double X[3][3], ElemFrame &f
     double twoA = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
     double lc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
     if (!(twoA > 0.0) || !(lc > 0.0) || !isfinite(twoA)) return false;
-    for (int d = 0; d < 3; d++) {
-        f.n[d] = nn[d] / twoA;
-        f.t1[d] = c[d] / lc;
+    if constexpr (RECIP) {
+        const double in = 1.0 / twoA, ic = 1.0 / lc;
+        for (int d = 0; d < 3; d++) {
+            f.n[d] = nn[d] * in;
+            f.t1[d] = c[d] * ic;
+        }
+    } else {
+        for (int d = 0; d < 3; d++) {
+            f.n[d] = nn[d] / twoA;
+            f.t1[d] = c[d] / lc;
+        }
     }
     cross(f.n, f.t1, f.t2);
     double x[3], y[3];
@@ -193,10 +204,17 @@ __device__ __forceinline__ void coupling_block_f32(const float (&t1)[3], const f
 // K_01, K_12, K_20 determine the rest (K_ab = K_ba^T); they go to kcs [E][3][9][Sp]
 // (sample index innermost). u is read as binary64 from the state of any form. An element
 // whose deformed area is zero or not finite sets bit 3 of *flags.
+// C / E of the binary32 block arithmetic (C11, C12, C33, C44 as in coupling_block),
+// formed once on the host in binary64 and rounded.
+struct CoeffsF32 {
+    float c11, c12, c33, c44;
+};
+
 template <int FORM>
 __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t *__restrict__ tri,
-                                  int32_t E, int32_t Sp, double nu, double ks, const void *__restrict__ u_main,
-                                  const void *__restrict__ aux, void *__restrict__ kcs, int *flags) {
+                                  int32_t E, int32_t Sp, double nu, double ks, const CoeffsF32 cf,
+                                  const void *__restrict__ u_main, const void *__restrict__ aux,
+                                  void *__restrict__ kcs, int *flags) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)E * Sp) return;
     const int32_t e = (int32_t)(t / Sp);
@@ -217,7 +235,7 @@ __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t 
         }
     }
     ElemFrame f;
-    if (!element_frame(X, f)) {
+    if (!element_frame<true>(X, f)) {
         atomicOr(flags, 8);
         return;
     }
@@ -230,9 +248,7 @@ __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t 
                     ((double *)kcs)[(((int64_t)e * 3 + c) * 9 + 3 * r + q) * Sp + s] = G[r][q];
         }
     } else {
-        const double C11 = 1.0 / (1.0 - nu * nu);
-        const float c11 = (float)C11, c12 = (float)(nu * C11), c33 = (float)(0.5 * (1.0 - nu) * C11),
-                    c44 = (float)(0.5 * ks * (1.0 - nu) * C11), sc = (float)(1.0 / (4.0 * f.area));
+        const float sc = 0.25f / (float)f.area;
         float t1[3], t2[3], n[3], b[3], g[3];
         for (int d = 0; d < 3; d++) {
             t1[d] = (float)f.t1[d];
@@ -244,7 +260,7 @@ __global__ void reassemble_kernel(const double *__restrict__ xyz, const int32_t 
         for (int c = 0; c < 3; c++) {  // block c couples corner c to corner (c + 1) mod 3
             const int k = (c + 1) % 3;
             float G[3][3];
-            coupling_block_f32(t1, t2, n, b[c], g[c], b[k], g[k], sc, c11, c12, c33, c44, G);
+            coupling_block_f32(t1, t2, n, b[c], g[c], b[k], g[k], sc, cf.c11, cf.c12, cf.c33, cf.c44, G);
             for (int r = 0; r < 3; r++)
                 for (int q = 0; q < 3; q++) ((float *)kcs)[(((int64_t)e * 3 + c) * 9 + 3 * r + q) * Sp + s] = G[r][q];
         }
@@ -434,12 +450,15 @@ cudaError_t launch_reassemble(int form, const double *xyz, const int32_t *tri, i
     const int64_t n = (int64_t)E * Sp;
     if (n == 0) return cudaSuccess;
     const unsigned g = blocks_for(n, 128);
+    const double C11 = 1.0 / (1.0 - nu * nu);
+    const CoeffsF32 cf{(float)C11, (float)(nu * C11), (float)(0.5 * (1.0 - nu) * C11),
+                       (float)(0.5 * kshear * (1.0 - nu) * C11)};
     if (form == kFP64)
-        reassemble_kernel<kFP64><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, flags);
+        reassemble_kernel<kFP64><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, cf, u_main, aux, kcs, flags);
     else if (form == kFP32Force)
-        reassemble_kernel<kFP32Force><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, flags);
+        reassemble_kernel<kFP32Force><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, cf, u_main, aux, kcs, flags);
     else
-        reassemble_kernel<kKahan32><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, u_main, aux, kcs, flags);
+        reassemble_kernel<kKahan32><<<g, 128, 0, s>>>(xyz, tri, E, Sp, nu, kshear, cf, u_main, aux, kcs, flags);
     return cudaGetLastError();
 }
 
