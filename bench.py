@@ -192,6 +192,28 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+def measure_dgemm_tflops(stream, n=4096, reps=3):
+    """binary64 GEMM rate of the installed cuBLAS (torch.matmul of two n x n binary64
+    matrices), timed with CUDA events after a warm-up: a measured binary64 figure beside
+    the derived pipe peak. Whether cuBLAS reaches it on the binary64 pipe or by another
+    route is its own; the step kernel's binary64 FMAs can only use the pipe."""
+    import torch
+    g = torch.Generator(device=stream.device).manual_seed(7)
+    a = torch.rand((n, n), dtype=torch.float64, device=stream.device, generator=g)
+    b = torch.rand((n, n), dtype=torch.float64, device=stream.device, generator=g)
+    with torch.cuda.stream(stream):
+        c = a @ b
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            c = a @ b
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    del a, b, c
+    return 2.0 * n ** 3 * reps / t / 1e12
+
+
 def step_kernel_traffic(form, variant):
     """DRAM bytes per step-kernel launch of `form` in launch shape `variant`, from a
     committed ncu capture, if the kernel source it was taken on is unchanged (else None)."""
@@ -930,6 +952,8 @@ def main():
             flops = N * S * (48.0 * nnz / N + 3 * (2 * case["modes"].shape[0] + 7))
             res["achieved_tflops"] = flops / per_launch_s / 1e12
             res["fp64_frac"] = res["achieved_tflops"] / FP64_PEAK_TFLOPS
+            res["dgemm_tflops_measured"] = measure_dgemm_tflops(stream)
+            res["frac_of_measured_dgemm"] = res["achieved_tflops"] / res["dgemm_tflops_measured"]
         finals[form] = e.displacement()
         if form == (HEADLINE if HEADLINE in forms else forms[0]):
             shard_stats = e.stats()      # this rank's per-dof mean and variance
