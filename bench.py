@@ -415,6 +415,7 @@ def bench_outputs(args, local, stream, hbm_peak):
            "stress_kernel": {"achieved_gbs": alg / t_stress / 1e9, "hbm_frac": alg / t_stress / 1e9 / hbm_peak,
                              "fp64_tflops": flops / t_stress / 1e12,
                              "fp64_frac": flops / t_stress / 1e12 / FP64_PEAK_TFLOPS,
+                             "frac_of_measured_dgemm": flops / t_stress / 1e12 / measure_dgemm_tflops(stream),
                              "algorithmic_bytes": alg}}
     if not args.no_cpu_baseline:
         import oracle.outputs as oo
