@@ -46,7 +46,8 @@ int gmrf_create(int32_t n_nodes, int32_t n_elems, const double *xyz, const int32
  * 1 / (4 pi kappa^2) for nu = 1 on a 2-D surface, Section 2.1); sigma <= 0 means c = 1
  * (x itself). The solve is iterative refinement from x = 0: the
  * residual b - K x (b = C~^(1/2) z) is formed in binary64, a Jacobi-preconditioned
- * conjugate-gradient solve in binary32 reduces it by max(rtol, 1e-4), and x takes the
+ * conjugate-gradient solve in binary32 reduces it by a quarter of the factor still needed
+ * to reach rtol, clamped to [1e-4, 0.1], and x takes the
  * correction in binary64, until every sample has ||K x - b|| <= rtol ||b|| in binary64,
  * or max_iter binary32 iterations in all (then GMRF_ERR_NOT_CONVERGED, with out still
  * written). Each sample stops updating once it converges, so the result is

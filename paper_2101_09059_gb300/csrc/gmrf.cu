@@ -7,10 +7,12 @@
 // iteration is bound by that pipe (13 binary64 FMAs per row and sample), so the solve is
 // mixed-precision iterative refinement:
 //   outer, binary64:  r = b - K x (true residual), stop per sample at ||r|| <= rtol ||b||;
-//   inner, binary32:  Jacobi-preconditioned CG on K d = r / ||r|| to relative tolerance
-//                     max(rtol, 1e-4), then x += ||r|| d.
-// Each refinement gains about four digits (K has condition ~1e3 on the workloads, so the
-// binary32 solve is accurate to ~1e-4), and the final residual is the binary64 one.
+//   inner, binary32:  Jacobi-preconditioned CG on K d = r / ||r|| to a relative tolerance
+//                     per sample, a quarter of the reduction still needed to reach rtol,
+//                     within [1e-4, 0.1]; then x += ||r|| d.
+// A refinement gains up to about four digits (K has condition ~1e3 on the workloads, so
+// the binary32 solve is accurate to ~1e-4), the last one only what is left, and the
+// final residual is the binary64 one.
 // The inner solve takes Chronopoulos and Gear's form of preconditioned CG (one reduction
 // per iteration): with z = M^-1 r and w = K z, gamma = r.z and delta = z.w give
 // beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev), and the
@@ -42,7 +44,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 4096;  // upper bound of the row kernels' grid (see gmrf_ctx::grid)
 constexpr int kGraphIters = 8;
-constexpr double kInnerTol = 1e-4;
+constexpr double kInnerTol = 1e-4;     // smallest inner reduction asked of binary32 CG
+constexpr double kInnerMax = 0.1;      // largest inner tolerance
+constexpr double kInnerSafety = 0.25;  // inner target against the reduction still needed
 constexpr int kMaxRefinements = 16;
 
 thread_local char g_create_err[256] = "";
@@ -81,7 +85,6 @@ struct gmrf_ctx {
     int *h_active = nullptr;  // pinned
     cudaGraphExec_t graph = nullptr;
     int32_t graph_sp = -1;
-    double graph_tol = -1.0;
     gmrf_info_t info{};
     char err[256] = "";
 };
@@ -89,9 +92,9 @@ struct gmrf_ctx {
 namespace {
 
 // rows of scal
-// (kGam: r.z of the last inner iteration, kAlp: its alpha, kTot..kTot+2: this
-// iteration's totals of r.z, z.w, r.r)
-enum { kGam = 0, kBbIn, kActIn, kBb, kRr, kScale, kActOut, kAlp, kTot, kScal = kTot + 3 };
+// (kGam: r.z of the last inner iteration, kAlp: its alpha, kTolIn: the square of the
+// sample's inner tolerance, kTot..kTot+2: this iteration's totals of r.z, z.w, r.r)
+enum { kGam = 0, kBbIn, kActIn, kBb, kRr, kScale, kActOut, kAlp, kTolIn, kTot, kScal = kTot + 3 };
 #define SCS(row) scal[(size_t)(row) * Sp + s]
 
 int fail(gmrf_ctx *g, int code, const char *fmt, ...) {
@@ -318,7 +321,7 @@ __device__ __forceinline__ double sum_run(const double *src, int n) {
 // The scalar part of an inner iteration, run by the block that completed the reduction:
 // the totals of r.z, z.w, r.r from the group sums (one thread per quantity and sample),
 // then, one thread per sample s (state act_s: 0 inactive, 1 first iteration, 2 later ones),
-//   convergence: r.r <= tol^2 ||r_0||^2 ends the inner solve of s (alpha = beta = 0 from
+//   convergence: r.r <= tol_s^2 ||r_0||^2 ends the inner solve of s (alpha = beta = 0 from
 //   then on, so its d, r stay as they are);
 //   beta = gamma / gamma_prev (0 on the first iteration), alpha = gamma / (delta - beta
 //   gamma / alpha_prev) (gamma / delta on the first), rounded toward zero to binary32; a
@@ -327,7 +330,7 @@ __device__ __forceinline__ double sum_run(const double *src, int n) {
 // Kept out of line: it runs once per launch, and its binary64 arithmetic would otherwise
 // set the register budget of the product loop.
 __device__ __noinline__ void finish_iteration(const double *gpart, double *scal, float *alpha32, float *beta32,
-                                              int *n_active, int32_t Sp, double tol2) {
+                                              int *n_active, int32_t Sp) {
     __shared__ int s_count;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
     const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
@@ -342,7 +345,7 @@ __device__ __noinline__ void finish_iteration(const double *gpart, double *scal,
         double alpha = 0.0, beta = 0.0;
         if (act != 0.0) {
             if (act == 1.0) SCS(kBbIn) = rrs;
-            bool done = rrs <= tol2 * SCS(kBbIn);
+            bool done = rrs <= SCS(kTolIn) * SCS(kBbIn);
             if (!done) {
                 double den = del;
                 if (act == 2.0) {
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_matvec_kernel(
     const int32_t *__restrict__ ell_col, const float *__restrict__ ell_valz, const int32_t *__restrict__ rowptr,
     const int32_t *__restrict__ col, const float *__restrict__ valz, const float *__restrict__ minv,
     const float *__restrict__ ri, float *__restrict__ w, int32_t N, int32_t Sp, int64_t tiles, double *part,
-    double *gpart, unsigned *ctr, double *scal, float *alpha32, float *beta32, int *n_active, double tol2) {
+    double *gpart, unsigned *ctr, double *scal, float *alpha32, float *beta32, int *n_active) {
     // dynamic shared memory: the staged rows (int32 indices, then binary32 values,
     // max(kStageEntries, WP R) each), later the block's partial tree
     extern __shared__ double smd[];
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_matvec_kernel(
             for (int k = 0; k < V; k++)
                 part[((size_t)q * Sp + s0 + k) * gridDim.x + blockIdx.x] = smd[(q * V + k) * nt + xq];
     if (reduce_arrive(part, gpart, ctr, gridDim.x, Sp))
-        finish_iteration(gpart, scal, alpha32, beta32, n_active, Sp, tol2);
+        finish_iteration(gpart, scal, alpha32, beta32, n_active, Sp);
 }
 
 // Dynamic shared memory of cg_matvec_kernel<WP, V> for a block of (Qt, R).
@@ -586,7 +589,10 @@ __device__ __forceinline__ double block_total(const double *part, int w, int G, 
 #define SC(row) scal[(size_t)(row) * Sp + s]
 
 // Outer test after a residual: rr = ||r||^2 (first: also ||b||^2); a sample stays active
-// while rr > rtol^2 bb; the inner right-hand side is r / ||r||.
+// while rr > rtol^2 bb; the inner right-hand side is r / ||r||, and the inner solve of an
+// active sample stops at a relative residual of tol_s = kInnerSafety rtol sqrt(bb / rr),
+// the reduction still needed with a margin, clamped to [kInnerTol, kInnerMax]: the last
+// refinement does not go four digits past rtol.
 __global__ void fin_outer_kernel(const double *part, int G, int32_t Sp, double rtol2, int first, double *scal,
                                  double *inv_scale, int *n_active) {
     FIN_SAMPLE
@@ -599,6 +605,9 @@ __global__ void fin_outer_kernel(const double *part, int G, int32_t Sp, double r
         SC(kActOut) = act ? 1.0 : 0.0;
         SC(kScale) = act ? sqrt(rr) : 0.0;
         inv_scale[s] = act ? 1.0 / sqrt(rr) : 0.0;
+        const double need = act ? kInnerSafety * sqrt(rtol2 * bb / rr) : kInnerMax;
+        const double tin = fmin(kInnerMax, fmax(kInnerTol, need));
+        SC(kTolIn) = tin * tin;
         if (act) atomicAdd(n_active, 1);
     }
 }
@@ -650,7 +659,7 @@ int alloc_work(gmrf_ctx *g, int32_t Sp) {
 }
 
 // One inner (binary32) CG iteration: two launches on g's stream.
-cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double tol2) {
+cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp) {
     constexpr int V = kMatvecV;
     const Geo o = geometry(g->N, Sp, g->grid, V);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
@@ -658,8 +667,7 @@ cudaError_t launch_iteration(gmrf_ctx *g, int32_t Sp, double tol2) {
 #define CG_MATVEC(WP)                                                                                           \
     cg_matvec_kernel<WP, V><<<grid, block, matvec_smem(WP, V, o.Qt, o.R), g->stream>>>(g->ell_col, g->ell_valz, g->rowptr, g->col, g->valz, \
                                                             g->minv32, g->ri, g->w, g->N, Sp, o.tiles, g->part,  \
-                                                            g->gpart, g->ctr, g->scal, alpha, beta, g->n_active, \
-                                                            tol2)
+                                                            g->gpart, g->ctr, g->scal, alpha, beta, g->n_active)
     if (g->ell_w == 8)
         CG_MATVEC(8);
     else if (g->ell_w == 16)
@@ -875,7 +883,6 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
     const Geo o = geometry(g->N, Sp, g->grid);
     const dim3 grid(o.G, o.chunks), block(o.Qt, o.R);
     const size_t sm = sizeof(double2) * o.Qt * o.R;
-    const double tol = std::max(rtol, kInnerTol);
     double *inv_scale = g->scal + (size_t)kScal * Sp;
     // binary64 right-hand side and residual
     CKG(cudaMemsetAsync(g->n_active, 0, sizeof(int), g->stream));
@@ -884,7 +891,7 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
                                                         g->n_active);
     CKG(cudaGetLastError());
     if ((rc = read_active(g)) != GMRF_OK) return rc;
-    if (g->graph && (g->graph_sp != Sp || g->graph_tol != tol)) {
+    if (g->graph && g->graph_sp != Sp) {
         cudaGraphExecDestroy(g->graph);
         g->graph = nullptr;
     }
@@ -905,7 +912,7 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
                     g->stream = cap;
                     cudaGraph_t gr = nullptr;
                     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-                    for (int it = 0; it < kGraphIters && e == cudaSuccess; it++) e = launch_iteration(g, Sp, tol * tol);
+                    for (int it = 0; it < kGraphIters && e == cudaSuccess; it++) e = launch_iteration(g, Sp);
                     cudaError_t e2 = cudaStreamEndCapture(cap, &gr);
                     g->stream = keep;
                     cudaStreamDestroy(cap);
@@ -917,11 +924,10 @@ int gmrf_sample(gmrf_ctx *g, int32_t S, const double *z, double *out, double sig
                         return fail(g, GMRF_ERR_CUDA, "iteration graph: %s", cudaGetErrorString(e));
                     }
                     g->graph_sp = Sp;
-                    g->graph_tol = tol;
                 }
                 CKG(cudaGraphLaunch(g->graph, g->stream));
             } else {
-                for (int it = 0; it < k; it++) CKG(launch_iteration(g, Sp, tol * tol));
+                for (int it = 0; it < k; it++) CKG(launch_iteration(g, Sp));
             }
             iters += k;
             if ((rc = read_active(g)) != GMRF_OK) return rc;
